@@ -1,0 +1,269 @@
+"""ctypes front end of the FP64 CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the package smoke check and by
+the benchmark's CPU-baseline leg; never by the library product.  The oracle is a
+plain, slow FP64 restatement of the paper's method (Appendix Eqs. A1-A13, Eq. (1),
+Sec. 2.1 Tasks 1-5, Sec. 2.6, Fig. 5); see oracle.c for what each function follows.
+
+Parity status of each oracle function (what pins it, in tests/test_oracle_*.py):
+  potential functions f, Phi, phi, F, M ... closed forms A6-A9, finite differences,
+                                            Hermite error bound, special cases
+  neighbour sets ........................ brute force == cell list; symmetry
+  energies and forces .................... -grad E by central differences per term;
+                                            Newton's third law; BCC closed form
+                                            (E = -E_c, dE/da = 0, F = 0); dimer
+  time loop .............................. time reversibility, NVE conservation,
+                                            momentum conservation, indenter travel
+The physical outputs of Sec. 4.3 (load, modulus, hardness) stay unpinned: the
+potential parameters of the paper's refs. [42] and [34] are not printed.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+import subprocess
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "oracle.c")
+LIB = os.path.join(HERE, "liboracle.so")
+
+_lock = threading.Lock()
+_lib = None
+
+OR_F, OR_PHI, OR_MORSE, OR_EMBED, OR_MTERM, OR_F_RAW, OR_PHI_AN, OR_MORSE_RAW = range(8)
+
+
+class OrParams(C.Structure):
+    _fields_ = [(n, C.c_double) for n in
+                ("r_e", "f_e", "beta", "F_o", "n", "rho_e", "alpha", "P_e",
+                 "a0", "a1", "a2", "a3", "d", "D_o", "alpha_x", "y_eq", "rc", "rc_m")] + \
+               [("shifted", C.c_int32), ("tabulated", C.c_int32), ("r_min", C.c_double), ("h", C.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, FP64, no FMA contraction, OpenMP if available)."""
+    with _lock:
+        if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+            return LIB
+        base = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", SRC, "-o", LIB + ".tmp", "-lm"]
+        try:
+            subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+        except subprocess.CalledProcessError:
+            subprocess.run(base, check=True, capture_output=True)
+        os.replace(LIB + ".tmp", LIB)
+        return LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(LIB)
+        dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+        ip = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+        lp = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+        up = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+        L.or_pot_new.restype = C.c_void_p
+        L.or_pot_new.argtypes = [C.POINTER(OrParams)]
+        L.or_pot_free.argtypes = [C.c_void_p]
+        L.or_eval.restype = C.c_int
+        L.or_eval.argtypes = [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.or_neumaier.restype = C.c_double
+        L.or_neumaier.argtypes = [dp, C.c_int64]
+        L.or_grid.restype = C.c_int
+        L.or_grid.argtypes = [dp, dp, ip, C.c_double, ip, dp]
+        L.or_cell_coords.restype = C.c_int
+        L.or_cell_coords.argtypes = [C.c_int32, dp, dp, dp, ip, C.c_double, ip]
+        L.or_neighbors.restype = C.c_int64
+        L.or_neighbors.argtypes = [C.c_int32, dp, dp, dp, ip, C.c_double, C.c_int32, lp, ip, C.c_int64,
+                                   C.POINTER(C.c_int64)]
+        L.or_cneighbors.restype = C.c_int64
+        L.or_cneighbors.argtypes = [C.c_int32, dp, C.c_int32, dp, dp, dp, ip, C.c_double, lp, ip, C.c_int64,
+                                    C.POINTER(C.c_int64)]
+        L.or_forces.restype = C.c_int
+        L.or_forces.argtypes = [C.c_void_p, C.c_int32, dp, dp, dp, ip, C.c_int32, dp, C.c_int32,
+                                dp, dp, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.or_sim_new.restype = C.c_void_p
+        L.or_sim_new.argtypes = [C.c_void_p, C.c_int32, dp, dp, up, C.c_int32, dp, dp, dp, ip,
+                                 C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, C.c_int32]
+        L.or_sim_free.argtypes = [C.c_void_p]
+        L.or_sim_step.restype = C.c_int
+        L.or_sim_step.argtypes = [C.c_void_p, C.c_int64]
+        L.or_sim_get.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.or_sim_list.restype = C.c_int64
+        L.or_sim_list.argtypes = [C.c_void_p, C.c_int32, lp, ip, C.c_int64]
+        L.or_set_threads.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int32]
+        _lib = L
+    return _lib
+
+
+def set_threads(n: int) -> int:
+    """Set the OpenMP thread count (0 = leave); returns the count in use."""
+    return int(lib().or_set_threads(int(n)))
+
+
+def _arr(a, dt=np.float64):
+    return np.ascontiguousarray(np.asarray(a, dtype=dt))
+
+
+def load_params(path: Optional[str] = None) -> dict:
+    """The derived parameter set shipped with the package (a JSON file written by derive_params.py)."""
+    if path is None:
+        path = os.path.join(os.path.dirname(HERE), "paper_1507_07068_gb300", "cr_c_params.json")
+    with open(path) as fh:
+        return json.load(fh)
+
+
+class Potential:
+    """The oracle's potential functions with a given parameter dict."""
+
+    def __init__(self, params: dict, **override):
+        p = dict(params)
+        p.update(override)
+        self.params = p
+        st = OrParams()
+        for name, _ in OrParams._fields_:
+            setattr(st, name, int(p[name]) if name in ("shifted", "tabulated") else float(p[name]))
+        self._st = st
+        self.h = lib().or_pot_new(C.byref(st))
+        if not self.h:
+            raise MemoryError("or_pot_new failed")
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().or_pot_free(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def eval(self, which: int, x: float):
+        v = C.c_double(); d = C.c_double()
+        if lib().or_eval(self.h, int(which), float(x), C.byref(v), C.byref(d)):
+            raise ValueError(which)
+        return v.value, d.value
+
+    def evalv(self, which: int, xs: Sequence[float]):
+        out = np.array([self.eval(which, float(x)) for x in xs])
+        return out[:, 0], out[:, 1]
+
+
+def neumaier(x) -> float:
+    x = _arr(x)
+    return float(lib().or_neumaier(x, x.size))
+
+
+def grid(lo, hi, periodic, cut):
+    n = np.zeros(3, np.int32); w = np.zeros(3)
+    err = lib().or_grid(_arr(lo), _arr(hi), _arr(periodic, np.int32), float(cut), n, w)
+    if err:
+        raise ValueError(f"or_grid: {err}")
+    return n, w
+
+
+def cell_coords(x, lo, hi, periodic, cut) -> np.ndarray:
+    x = _arr(x).reshape(-1, 3)
+    out = np.zeros((len(x), 3), np.int32)
+    if lib().or_cell_coords(len(x), x, _arr(lo), _arr(hi), _arr(periodic, np.int32), float(cut), out):
+        raise ValueError("or_cell_coords")
+    return out
+
+
+def _csr_call(fn, n, *args):
+    cap = 64 * max(n, 1)
+    while True:
+        off = np.zeros(n + 1, np.int64); idx = np.zeros(max(cap, 1), np.int32); need = C.c_int64()
+        tot = fn(*args, off, idx, cap, C.byref(need))
+        if tot >= 0:
+            return off, idx[:tot].copy()
+        if need.value <= cap:
+            raise RuntimeError("oracle neighbour build failed")
+        cap = int(need.value)
+
+
+def neighbors(x, lo, hi, periodic, cut, method: int = 1):
+    """CSR (off, idx) of all j != i within `cut` (method 0 brute force, 1 cell list)."""
+    x = _arr(x).reshape(-1, 3)
+    return _csr_call(lib().or_neighbors, len(x), len(x), x, _arr(lo), _arr(hi), _arr(periodic, np.int32),
+                     float(cut), int(method))
+
+
+def cneighbors(x, xc, lo, hi, periodic, cut):
+    x = _arr(x).reshape(-1, 3); xc = _arr(xc).reshape(-1, 3)
+    return _csr_call(lib().or_cneighbors, len(x), len(x), x, len(xc), xc if len(xc) else np.zeros(3),
+                     _arr(lo), _arr(hi), _arr(periodic, np.int32), float(cut))
+
+
+def forces(pot: Potential, x, lo, hi, periodic, xc=None, method: int = 1, want_atoms: bool = False):
+    """Stateless evaluation: returns dict with F (n,3), energy components, load (and rho, P, e_atom)."""
+    x = _arr(x).reshape(-1, 3)
+    xc = np.zeros((0, 3)) if xc is None else _arr(xc).reshape(-1, 3)
+    n = len(x)
+    F = np.zeros((n, 3)); ep = np.zeros(5)
+    rho = np.zeros(n) if want_atoms else None
+    P = np.zeros(n) if want_atoms else None
+    ea = np.zeros(n) if want_atoms else None
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p) if a is not None else None
+    err = lib().or_forces(pot.h, n, x, _arr(lo), _arr(hi), _arr(periodic, np.int32), len(xc),
+                          xc if len(xc) else np.zeros(3), int(method), F, ep, ptr(rho), ptr(P), ptr(ea))
+    if err:
+        raise RuntimeError(f"or_forces: {err}")
+    out = dict(F=F, embed=ep[0], pair=ep[1], mterm=ep[2], morse=ep[3], load=ep[4],
+               potential=ep[0] + ep[1] + ep[2] + ep[3])
+    if want_atoms:
+        out.update(rho=rho, P=P, e_atom=ea)
+    return out
+
+
+class Sim:
+    """Oracle time loop (Fig. 5): Verlet lists with skin, Tasks 1-5 per step."""
+
+    def __init__(self, pot: Potential, rep, skin: float = 0.3, rebuild_every: int = 0, method: int = 1,
+                 x=None, v=None):
+        self.pot = pot
+        self.n = rep.n_cr
+        self.nc = rep.n_c
+        self._keep = [pot]
+        x = _arr(rep.x_cr if x is None else x).reshape(-1, 3)
+        v = _arr(rep.v_cr if v is None else v).reshape(-1, 3)
+        xc = _arr(rep.x_c).reshape(-1, 3) if rep.n_c else np.zeros((1, 3))
+        self.h = lib().or_sim_new(pot.h, self.n, x, v, _arr(rep.fixed, np.uint8), self.nc, xc,
+                                  _arr(rep.box_lo), _arr(rep.box_hi), _arr(rep.periodic, np.int32),
+                                  float(rep.z_indenter0), float(rep.v_indenter), float(rep.dt),
+                                  float(rep.mass_cr), float(skin), int(rebuild_every), int(method))
+        if not self.h:
+            raise RuntimeError("or_sim_new failed")
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().or_sim_free(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        if lib().or_sim_step(self.h, int(n)):
+            raise RuntimeError("or_sim_step failed")
+
+    def state(self):
+        x = np.zeros((self.n, 3)); v = np.zeros((self.n, 3)); F = np.zeros((self.n, 3))
+        e = np.zeros(8); z = np.zeros(1); cnt = np.zeros(2, np.int64)
+        p = lambda a: a.ctypes.data_as(C.c_void_p)
+        lib().or_sim_get(self.h, p(x), p(v), p(F), p(e), p(z), p(cnt))
+        return dict(x=x, v=v, F=F, embed=e[0], pair=e[1], mterm=e[2], morse=e[3], kinetic=e[4],
+                    potential=e[5], total=e[6], load=e[7], z_ind=z[0], step=int(cnt[0]), rebuilds=int(cnt[1]))
+
+    def verlet_list(self, which: int = 0):
+        cap = 128 * max(self.n, 1)
+        off = np.zeros(self.n + 1, np.int64); idx = np.zeros(cap, np.int32)
+        tot = lib().or_sim_list(self.h, int(which), off, idx, cap)
+        if tot < 0:
+            raise RuntimeError("list capacity")
+        return off, idx[:tot].copy()
