@@ -1,0 +1,413 @@
+#!/usr/bin/env python3
+"""Benchmark of the per-timestep short-range force evaluation (EAM Cr-Cr + Morse Cr-C +
+velocity Verlet) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 1M] [--impl reference]
+
+Metric: Cr atom-timesteps/s of md_step on the named workload (whole job over all ranks;
+replicas shard across ranks with no data-path collective: "scaling": "weak").  Prints ONE
+JSON line on rank 0.  --impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import md_inputs as mi  # noqa: E402
+
+METRIC = "atom-timesteps/s (Cr), md_step on one GB300"
+UNIT = "atom-steps/s"
+
+WORKLOAD_TEXT = {
+    "tiny": "tiny: Cr film 8x8x8 cells (1,024 atoms) + C hemisphere R=0.6 nm, 300 K, 20 m/s, dt=1 fs",
+    "64k": "64k: Cr film 40x40x20 cells (64,000 atoms) + C hemisphere R=1.5 nm, 3 fixed planes, 300 K",
+    "1M": "1M: Cr film 100x100x50 cells (1,000,000 atoms) + C hemisphere R=3 nm, 300 K, 20 m/s, dt=1 fs",
+    "8M": "8M: Cr film 200x200x100 cells (8,000,000 atoms) + C hemisphere R=6 nm, 300 K, 20 m/s, dt=1 fs",
+    "batched": "batched: 256 uneven replicas (6..24 x 6..24 x 6..12 cells, R 0.5-1.5 nm, 100-500 K)",
+}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 50):
+        self.gpu = gpu_index
+        self.period = period_ms
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", str(self.period)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self._t:
+                self._t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [t.strip() for t in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(name: str, rank: int):
+    wl = mi.make_workload(name)
+    reps = wl.replicas
+    if rank and name != "batched":
+        # weak scaling: each rank runs its own replica of the workload (fresh velocity draw)
+        nx, ny, nz, R, nf, _ = mi.PRESETS[name]
+        reps = [mi.make_replica(name, nx, ny, nz, R, 300.0, seed=1507 * 1000 + 97 * rank, n_fixed_planes=nf)]
+    return wl, reps
+
+
+def algorithmic_bytes(kernel: str, kmean: float, precision: str) -> float:
+    """Bytes per Cr atom that the kernel must move (int32 list, neighbour data counted once)."""
+    if precision == "mixed":
+        if kernel == "density":
+            return 4 * kmean + 28      # cnt 4 + list 4K + float4 position 16 + (F', M') write 8
+        return 4 * kmean + 44          # cnt 4 + list 4K + position 16 + (F', M') 8 + force write 16
+    if kernel == "density":
+        return 4 * kmean + 44          # cnt + list + 3 FP64 coordinates 24 + (F', M') 16
+    return 4 * kmean + 68              # cnt + list + coordinates 24 + (F', M') 16 + force write 24
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("md_kernels.cu", "md_internal.h"):
+        with open(os.path.join(ROOT, "paper_1507_07068_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic(workload: str, precision: str, kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled to this
+    workload; None when absent or taken from a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as fh:
+            tr = json.load(fh)
+        rec = tr.get(f"{workload}:{precision}:k_{kernel}")
+        if not rec or rec.get("source_hash") != kernel_source_hash():
+            return None
+        return rec.get("bytes_per_launch")
+    except (OSError, ValueError):
+        return None
+
+
+def run_gpu(args):
+    import torch
+    from paper_1507_07068_gb300 import md
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    params = md.load_params()
+    wl, reps = make_workload(args.workload, rank)
+    n_cr = sum(r.n_cr for r in reps)
+    n_c = sum(r.n_c for r in reps)
+    stream = torch.cuda.current_stream()
+    sim = md.MD(reps, params, precision=args.precision, skin=0.3, tpa=args.tpa, block=args.block)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region (graph replay)
+    sim.step(args.warmup)
+    e0 = sim.energy(0)
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True); ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    e1 = sim.energy(0)
+    rebuilds = e1["rebuilds"] - e0["rebuilds"]
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = n_cr * ws * args.steps / (t_max * 1e-3)
+
+    # ---- per-kernel device time (direct launches with CUDA events around each phase)
+    prof = sim.step_profiled(args.profile_steps)
+    _, cnt, _ = sim.neighbors(0, 0, kmax=1)
+    kmean = float(cnt.mean())
+    phases = {k: prof[k] / prof["steps"] for k in ("skin", "rebuild", "verlet1", "density", "force", "reduce")}
+    dom = "force" if phases["force"] >= phases["density"] else "density"
+    peak, peak_kind = load_peaks()
+    bytes_per_launch = algorithmic_bytes(dom, kmean, args.precision) * n_cr
+    achieved = bytes_per_launch / (phases[dom] * 1e-3) / 1e9
+    traffic = dram_traffic(args.workload, args.precision, dom)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timing
+    e2e = None
+    if not args.no_e2e and len(reps) >= 1:
+        r0 = reps[0]
+        n0 = r0.n_cr
+        hx = torch.empty((n0, 3), dtype=torch.float64, pin_memory=True).numpy()
+        hv = torch.empty((n0, 3), dtype=torch.float64, pin_memory=True).numpy()
+        x, v, z, st = sim.state(0)
+        hx[:] = x; hv[:] = v
+        for _ in range(2):
+            sim.set_state(0, hx, hv, z, st)
+            sim.step(1)
+            md.md_get_state(sim.h, 0, n0, hx, hv)
+            z = sim.energy(0)["z_indenter"]; st += 1
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            sim.set_state(0, hx, hv, z, st)        # H2D of this step's inputs
+            sim.step(1)
+            md.md_get_state(sim.h, 0, n0, hx, hv)  # D2H of the step's result
+            en = sim.energy(0)
+            z = en["z_indenter"]; st += 1
+        dt_e2e = time.perf_counter() - t0
+        e2e = {"value": n0 * args.e2e_steps / dt_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(hx.nbytes + hv.nbytes + 16),
+               "d2h_bytes_per_step": int(hx.nbytes + hv.nbytes + md.C.sizeof(md.md_energy)),
+               "path": "md_set_state (H2D) + md_step(1) + md_get_state (D2H) + md_get_energy, replica 0"}
+
+    # ---- variants on the same GPU: plain FP64 form on this workload, batched replicas
+    variants = {}
+    if not args.no_variants and rank == 0:
+        if args.precision != "fp64":
+            s64 = md.MD(reps, params, precision="fp64", skin=0.3)
+            s64.step(3)
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+            k64 = max(5, min(args.steps, args.fp64_steps))
+            a0.record(stream); s64.step(k64); a1.record(stream); torch.cuda.synchronize()
+            variants["fp64"] = {"value": n_cr * k64 / (a0.elapsed_time(a1) * 1e-3), "steps": k64,
+                                "ms_per_step": a0.elapsed_time(a1) / k64}
+            s64.close()
+        if args.workload != "batched":
+            bw = mi.make_workload("batched")
+            sb = md.MD(bw.replicas, params, precision="mixed", skin=0.3)
+            sb.step(10)
+            torch.cuda.synchronize()
+            b0 = torch.cuda.Event(enable_timing=True); b1 = torch.cuda.Event(enable_timing=True)
+            kb = max(10, min(args.steps, args.batched_steps))
+            b0.record(stream); sb.step(kb); b1.record(stream); torch.cuda.synchronize()
+            variants["batched_mixed"] = {"value": bw.n_cr * kb / (b0.elapsed_time(b1) * 1e-3), "steps": kb,
+                                         "replicas": len(bw.replicas), "n_cr": bw.n_cr,
+                                         "ms_per_step": b0.elapsed_time(b1) / kb}
+            sb.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, params, args.cpu_seconds)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic (seeded BCC film + diamond hemisphere, Maxwell-Boltzmann velocities)",
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "n_cr": n_cr * ws, "n_c": n_c * ws,
+                   "precision": args.precision, "potential": "cubic Hermite tables, shifted-force cut-offs",
+                   "skin_A": 0.3, "rebuild": "skin/2 rule (conditional graph node)",
+                   "rebuilds_in_timed_region": rebuilds, "tpa": args.tpa or 4, "block": args.block or 128,
+                   "l2": "working set larger than L2 (neighbour list alone %.0f MB)" % (n_cr * kmean * 4 / 1e6),
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                     "algorithmic_bytes_per_atom": algorithmic_bytes(dom, kmean, args.precision),
+                     "mean_list_length": kmean, "launch_ms": phases[dom]},
+        "phases_ms_per_step": phases,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": int(6 * args.steps + 13 * rebuilds),
+        "variants": variants,
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    sim.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample_replica(workload: str, target_atoms: int):
+    """A film of the workload's kind, thinned in z to about target_atoms (same lateral size)."""
+    if workload == "batched":
+        return mi.batched_replicas(1)[0], "one replica of the batched set"
+    nx, ny, nz, R, nf, _ = mi.PRESETS[workload]
+    full = 2 * nx * ny * nz
+    if target_atoms >= full:
+        rep = mi.make_workload(workload).replicas[0]
+        return rep, f"the full {workload} film ({full} Cr)"
+    nz_s = max(4, int(target_atoms / (2 * nx * ny)))
+    while 2 * nx * ny * nz_s > target_atoms and nz_s > 4:
+        nz_s -= 1
+    if 2 * nx * ny * nz_s > target_atoms * 2:
+        # lateral thinning too (keeps the film periodic and the indenter inside)
+        s = max(0.2, (target_atoms / (2 * nx * ny * nz_s)) ** 0.5)
+        nx = max(int(2 * R / mi.A_CR) + 6, int(nx * s)); ny = nx
+    rep = mi.make_replica(workload, nx, ny, nz_s, R, 300.0, seed=1507 + 7, n_fixed_planes=nf)
+    return rep, f"{nx}x{ny}x{nz_s}-cell slab of the {workload} film ({rep.n_cr} Cr), same indenter"
+
+
+def oracle_rate(params, rep, steps: int):
+    import oracle
+    pot = oracle.Potential(params)
+    sim = oracle.Sim(pot, rep, skin=0.3)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    return rep.n_cr * steps / (time.perf_counter() - t0)
+
+
+def cpu_baseline(workload: str, params, seconds: float):
+    import oracle
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    probe = mi.make_replica("probe", 24, 24, 10, 6.0, 300.0, seed=3)
+    rate = oracle_rate(params, probe, 2)
+    target = int(rate * seconds / 6)
+    rep, desc = oracle_sample_replica(workload, max(target, 20000))
+    n = max(2, min(6, int(rate * seconds / max(rep.n_cr, 1))))
+    v = oracle_rate(params, rep, n)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} FP64 oracle time steps (list build excluded) on {desc}, OpenMP over {cores} threads"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    sys.path.insert(0, ROOT)
+    import oracle
+    oracle.build()
+    params = oracle.load_params()
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    probe = mi.make_replica("probe", 24, 24, 10, 6.0, 300.0, seed=3)
+    rate = oracle_rate(params, probe, 2)
+    budget = args.ref_seconds
+    per_step = budget / max(args.steps + args.warmup, 1)
+    rep, desc = oracle_sample_replica(args.workload, max(int(rate * per_step), 5000))
+    pot = oracle.Potential(params)
+    sim = oracle.Sim(pot, rep, skin=0.3)
+    sim.step(args.warmup)
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = rep.n_cr * args.steps / dt
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD_TEXT[args.workload], "precision": "fp64 (oracle)",
+                      "sample": desc},
+           "impl": "reference",
+           "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
+                            "sample": f"each step one FP64 oracle time step on {desc}"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--workload", default="1M", choices=list(WORKLOAD_TEXT))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--tpa", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--fp64-steps", type=int, default=40)
+    ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=120.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

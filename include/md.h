@@ -1,0 +1,230 @@
+/*
+ * md.h -- C ABI of libmd: the per-timestep short-range force evaluation of a Cr film
+ * indented by a rigid carbon hemisphere (Pal, Agarwala, Raha & Bhattacharya,
+ * arXiv:1507.07068), on one NVIDIA GB300 (sm_103a).
+ *
+ * One call of md_step advances every replica by whole time steps in the order of the
+ * paper's time loop (Fig. 5, Table 1):
+ *   Task 1  neighbour-list check and rebuild (Sec. 2.6: rebuild when an atom has moved
+ *           more than half the skin; cell binning + Verlet list),
+ *   Task 2  rigid indenter moved at constant velocity (Sec. 2.1, 2.5),
+ *   Task 3  velocity-Verlet half kick and drift (Appendix Eqs. A11-A12),
+ *   Task 4  electron densities, embedding derivatives, EAM + Morse forces and energies
+ *           (Eq. (1), Appendix Eqs. A1-A10, A13),
+ *   Task 5  closing half kick.
+ *
+ * Conventions for every function below:
+ *   - Units: Angstrom, eV, fs, atomic mass units (u).  Accelerations use
+ *     1 eV/(A u) = 9.6485332e-3 A/fs^2.
+ *   - Arrays of vectors are AoS x0,y0,z0,x1,... in the caller's own atom order; the
+ *     library keeps atoms in its own cell order internally and never exposes it.
+ *   - Host pointers are read during the call only (md_init copies everything); output
+ *     buffers are caller-owned and must hold the stated number of elements.
+ *   - Every function returns MD_OK (0) or an MD_ERR_* code; md_last_error() gives a
+ *     one-line description.  No C++ exception crosses this interface.
+ *   - A handle is used from one host thread at a time.  All device work runs on the
+ *     CUDA stream given to md_init; getters synchronise that stream.
+ *   - The library owns all device memory it allocates (cudaMalloc at md_init, freed by
+ *     md_free); no allocation happens in md_step.
+ */
+#ifndef MD_H
+#define MD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+enum {
+    MD_OK = 0,
+    MD_ERR_ARG = 1,             /* invalid argument (sizes, box too small for the cell grid, ...) */
+    MD_ERR_CUDA = 2,            /* a CUDA runtime call failed; the handle should be freed */
+    MD_ERR_NBR_OVERFLOW = 3,    /* an atom had more neighbours than kmax / kcmax at a rebuild */
+    MD_ERR_SKIN_VIOLATION = 4,  /* fixed rebuild interval: an atom moved more than skin/2 */
+    MD_ERR_LOST_ATOM = 5,       /* an atom left the cell-grid domain along a non-periodic axis (or became NaN) */
+    MD_ERR_STATE = 6            /* call not valid in the handle's current state */
+};
+
+/* arithmetic of the force kernels */
+enum {
+    MD_FP64 = 0,    /* everything in FP64 */
+    MD_MIXED = 1    /* pair and EAM arithmetic in FP32 on cell-relative positions; FP64
+                       integration, skin test, list build and energy/load reductions */
+};
+
+/*
+ * Potential parameters (Appendix Eqs. A2-A5).  The paper prints the forms but not the
+ * values (they come from its refs. [42] and [34]); any consistent set may be passed.
+ *   f(r)   = f_e (r_e / r)^beta                                   Eq. A2
+ *   F(rho) = -F_o [1 - n ln(rho/rho_e)] (rho/rho_e)^n              Eq. A3 (ln(.)^n read as n ln(.))
+ *   M(P)   = alpha u^2 exp(-u^2),  u = P/P_e - 1                   Eq. A3
+ *   Phi(x) = (x - d)^2 (a3 x^3 + a2 x^2 + a1 x + a0), x = r/r_e <= d; 0 beyond   Eq. A4
+ *   phi(y) = D_o [exp(-alpha_x (y/y_eq - 1)) - 2 exp(-(alpha_x/2)(y/y_eq - 1))] Eq. A5
+ * f, f^2 and Phi are cut at rc, phi at rc_morse.  shifted = 1 replaces f and phi below
+ * their cut-offs by the shifted-force forms g(r) - g(rc) - (r - rc) g'(rc) (continuous
+ * forces; needed for energy conservation); shifted = 0 truncates.  tabulated = 1
+ * evaluates f, Phi and phi from cubic Hermite tables on a uniform grid from r_min to the
+ * cut-off with spacing <= h (knot values and slopes from the forms above, forces the
+ * exact derivative of the interpolant); tabulated = 0 evaluates the forms directly.
+ */
+typedef struct md_params {
+    double r_e, f_e, beta;
+    double F_o, n, rho_e;
+    double alpha, P_e;
+    double a[4];                /* a0, a1, a2, a3 */
+    double d;
+    double D_o, alpha_x, y_eq;
+    double rc, rc_morse;
+    int32_t shifted, tabulated;
+    double r_min, h;
+} md_params;
+
+/*
+ * One independent indentation system (a "replica").
+ *   x_cr, v_cr : 3*n_cr doubles, film positions (A) and velocities (A/fs)
+ *   fixed      : n_cr bytes, nonzero = atom held fixed (v = 0, never moved, still exerts
+ *                and feels forces), or NULL for none
+ *   x_c        : 3*n_c doubles, indenter atom positions at t = 0 (rigid; at time t they are
+ *                x_c + (0, 0, z_indenter(t) - z_indenter0)); NULL when n_c = 0
+ *   box_lo/hi  : the cell-grid domain.  A periodic axis has period hi - lo (minimum image);
+ *                along a non-periodic axis an atom outside [lo, hi] is reported as lost.
+ *   z_indenter0, v_indenter : indenter displacement at t = 0 and its rate (A/fs; negative
+ *                moves the indenter down into the film)
+ *   dt (fs), mass_cr (u)
+ */
+typedef struct md_system {
+    int32_t n_cr, n_c;
+    const double *x_cr, *v_cr, *x_c;
+    const uint8_t *fixed;
+    double box_lo[3], box_hi[3];
+    int32_t periodic[3];
+    double z_indenter0, v_indenter, dt, mass_cr;
+} md_system;
+
+/*
+ * Options shared by all replicas of a handle.
+ *   pot           : potential parameters (copied)
+ *   precision     : MD_FP64 or MD_MIXED
+ *   skin          : Verlet skin (A); lists hold pairs within rc + skin (Cr-Cr) and
+ *                   rc_morse + skin (Cr-C)
+ *   rebuild_every : 0 = rebuild when max displacement since the last build exceeds skin/2
+ *                   (or, with an indenter, when that plus the indenter's travel exceeds the
+ *                   skin); k > 0 = rebuild every k steps (a larger displacement is then
+ *                   reported as MD_ERR_SKIN_VIOLATION)
+ *   kmax, kcmax   : neighbour capacity per atom for Cr-Cr and Cr-C (0 = defaults 80, 160)
+ *   tpa           : threads per atom in the force kernels, 1, 2, 4 or 8 (0 = default)
+ *   block         : threads per block in the force kernels (0 = default)
+ *   use_graph     : nonzero = md_step replays a captured CUDA graph
+ */
+typedef struct md_options {
+    const md_params *pot;
+    int32_t precision;
+    double skin;
+    int32_t rebuild_every;
+    int32_t kmax, kcmax;
+    int32_t tpa, block;
+    int32_t use_graph;
+} md_options;
+
+/* Energies of one replica after the last force evaluation (eV); FP64 sums. */
+typedef struct md_energy {
+    double embed;       /* sum_i F(rho_i)                    (Eq. A1)            */
+    double pair;        /* 1/2 sum_{i != j} Phi(r_ij)        (Eq. A1)            */
+    double mterm;       /* sum_i M(P_i)                      (Eq. A1)            */
+    double morse;       /* sum_{i in Cr, c in C} phi(y_ic)   (Eq. A5)            */
+    double kinetic;     /* sum_i m v_i^2 / 2                                     */
+    double potential;   /* embed + pair + mterm + morse                          */
+    double total;       /* potential + kinetic                                   */
+    double temperature; /* 2 kinetic / (3 k_B N_mobile)                          */
+    double load;        /* z force on the indenter = -sum_i F^Morse_{i,z} (eV/A) */
+    double depth;       /* top Cr plane at t = 0 minus the indenter's lowest atom (A) */
+    double z_indenter;  /* current indenter displacement (A)                     */
+    int64_t step;       /* steps taken                                           */
+    int64_t rebuilds;   /* neighbour-list rebuilds after md_init                 */
+} md_energy;
+
+/* Per-phase device time of md_step_profiled, milliseconds summed over its steps. */
+typedef struct md_phase_times {
+    double skin, rebuild, verlet1, density, force, reduce;
+    int64_t steps, rebuilds;
+} md_phase_times;
+
+typedef struct md_handle md_t;
+
+/*
+ * Copy n_replicas systems to the device, bin the indenter, build the potential tables,
+ * build the neighbour lists and evaluate forces and energies at t = 0 (the accelerations
+ * Task 3 needs at the first step).  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream).  On success *out receives a handle to be released with md_free.
+ * Errors: MD_ERR_ARG (bad sizes or options, a periodic axis shorter than 3 cells of
+ * rc + skin, or an indenter wider than the periodic box allows), MD_ERR_CUDA,
+ * MD_ERR_NBR_OVERFLOW.  On error *out is set to NULL and nothing is leaked.
+ */
+int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, void *cuda_stream, md_t **out);
+
+/* Task 1 now: wrap positions into periodic boxes, bin all atoms into cells (counting
+ * sort of cell keys, ascending caller id within a cell) and rebuild both Verlet lists
+ * (Sec. 2.6).  Errors: MD_ERR_NBR_OVERFLOW, MD_ERR_LOST_ATOM, MD_ERR_CUDA. */
+int md_build_neighbors(md_t *h);
+
+/* Task 4 at the current positions without integrating: densities, F'(rho), M'(P),
+ * forces, energies and load (Eq. (1), Eqs. A1-A10).  Uses the current lists. */
+int md_compute_forces(md_t *h);
+
+/* Advance every replica by n >= 0 time steps (Fig. 5: Tasks 1-5 per step).  Device-side
+ * errors raised during the n steps (overflow, lost atom, skin violation) are returned
+ * when the call ends; the state after such an error is not meaningful. */
+int md_step(md_t *h, int64_t n);
+
+/* As md_step, launching every kernel directly with CUDA events around each phase, and
+ * returning the summed device time per phase in *out (for measurement). */
+int md_step_profiled(md_t *h, int64_t n, md_phase_times *out);
+
+/* Energies of replica `replica` (0-based). */
+int md_get_energy(md_t *h, int32_t replica, md_energy *out);
+
+/* Forces (eV/A) of the last force evaluation, 3*n_cr doubles in caller order. */
+int md_get_forces(md_t *h, int32_t replica, double *out3n);
+
+/* Indenter load (eV/A, positive when the film pushes the indenter up) and depth (A). */
+int md_get_indenter_load(md_t *h, int32_t replica, double *load_z, double *depth);
+
+/* Positions (3*n_cr), velocities (3*n_cr) at the current integer time, indenter
+ * displacement and step count; any pointer may be NULL. */
+int md_get_state(md_t *h, int32_t replica, double *x3n, double *v3n, double *z_ind, int64_t *step);
+
+/* Replace positions and velocities (caller order; x3n or v3n may be NULL to keep), the
+ * indenter displacement and the step count of one replica.  The next md_step first
+ * re-checks the lists and re-evaluates forces at the new positions. */
+int md_set_state(md_t *h, int32_t replica, const double *x3n, const double *v3n, double z_ind, int64_t step);
+
+/* Test hook.  which = 0: Cr-Cr list, which = 1: Cr-C list, as built at the last rebuild.
+ * cell_xyz (3*n_cr, may be NULL): cell coordinates of each atom in the Cr cell grid;
+ * cnt (n_cr): list lengths (capped at the capacity); nbr (n_cr*kmax, may be NULL): entries
+ * in caller ids (film ids for which = 0, indenter ids for which = 1), row i holding atom
+ * i's first min(cnt[i], kmax) entries in unspecified order. */
+int md_get_neighbors(md_t *h, int32_t replica, int32_t which, int32_t *cell_xyz, int32_t *cnt,
+                     int32_t *nbr, int32_t kmax);
+
+/* Counts of one handle: out[0] = replicas, out[1] = film atoms, out[2] = indenter atoms,
+ * out[3] = atom slots (incl. tile padding), out[4] = cells, out[5] = kmax, out[6] = kcmax,
+ * out[7] = largest Cr-Cr list length seen at the last rebuild, out[8] = largest Cr-C. */
+int md_get_info(md_t *h, int64_t *out9);
+
+/* The last error message of the handle (never NULL; "" when none).  h may be NULL, then
+ * the message of the last failed md_init on this thread is returned. */
+const char *md_last_error(const md_t *h);
+
+/* Release all device and host memory of the handle (NULL is ignored). */
+void md_free(md_t *h);
+
+/* ABI version of this header (incremented on incompatible change). */
+int md_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MD_H */

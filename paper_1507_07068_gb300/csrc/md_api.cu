@@ -1,0 +1,772 @@
+// md_api.cu -- the C ABI of libmd (declared in include/md.h): handle life cycle, device
+// layout, CUDA-graph capture of the time step, state transfer and getters.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "md_internal.h"
+
+#define MD_ABI_VERSION 1
+
+namespace {
+
+thread_local std::string g_init_error;
+
+// device-side state transfer between the caller's AoS order and the slot order
+__global__ void k_state_in(const double *stage, double *dst, const int32_t *orig, int slot_off, int n, size_t S)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = slot_off + i;
+    int o = orig[s];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dst[k * S + s] = stage[3 * (size_t)o + k];
+}
+
+__global__ void k_state_out(const double *src, double *stage, const int32_t *orig, int slot_off, int n, size_t S)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = slot_off + i;
+    int o = orig[s];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) stage[3 * (size_t)o + k] = src[k * S + s];
+}
+
+__global__ void k_set_scalars(RepState *rs, int r, double z_ind, DevStatus *st, long long step, int set_step)
+{
+    rs[r].z_ind = z_ind;
+    rs[r].z_build = z_ind;
+    if (set_step) st->step = step;
+}
+
+}  // namespace
+
+struct md_handle {
+    cudaStream_t stream = nullptr;       // caller's stream
+    cudaStream_t cap = nullptr;          // private stream used only for graph capture
+    md_options opt{};
+    md_params pot_h{};
+    PotDev pot{};
+    LaunchCfg cfg{1, 128};
+    DevArgs a{};
+    std::vector<RepDev> rep;
+    std::vector<int32_t> c_orig;          // indenter slot -> caller indenter id (within replica)
+    int n_rep = 0;
+    int64_t n_cr = 0, n_c = 0;
+    Cf64 *tab64 = nullptr;
+    float4 *tab32 = nullptr;
+    double *stage = nullptr;              // 3 * max replica atoms doubles
+    std::vector<void *> allocs;
+    cudaGraphExec_t exec1 = nullptr, execU = nullptr;
+    int unroll = 1;
+    bool forces_valid = false;
+    std::vector<cudaEvent_t> ev;
+    std::string err;
+};
+
+namespace {
+
+int fail(md_t *h, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_init_error = buf;
+    return code;
+}
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(h, MD_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+template <class T>
+int dalloc(md_t *h, T **p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e != cudaSuccess) return fail(h, MD_ERR_CUDA, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+    h->allocs.push_back(*p);
+    e = cudaMemset(*p, 0, n * sizeof(T));
+    if (e != cudaSuccess) return fail(h, MD_ERR_CUDA, "cudaMemset: %s", cudaGetErrorString(e));
+    return MD_OK;
+}
+
+int cu_check(md_t *h, cudaError_t e, const char *what)
+{
+    if (e != cudaSuccess) return fail(h, MD_ERR_CUDA, "%s failed: %s", what, cudaGetErrorString(e));
+    return MD_OK;
+}
+
+int read_status(md_t *h, DevStatus *st)
+{
+    CU(cudaMemcpyAsync(st, h->a.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return MD_OK;
+}
+
+int status_to_code(md_t *h, const DevStatus &st)
+{
+    if (st.err & MDE_LOST) return fail(h, MD_ERR_LOST_ATOM, "an atom left the cell-grid domain along a non-periodic axis or became NaN");
+    if (st.err & MDE_OVERFLOW) return fail(h, MD_ERR_NBR_OVERFLOW, "Cr-Cr neighbour list overflow: %d > kmax %d", st.max_cnt, h->a.kmax);
+    if (st.err & MDE_COVERFLOW) return fail(h, MD_ERR_NBR_OVERFLOW, "Cr-C neighbour list overflow: %d > kcmax %d", st.max_cntc, h->a.kcmax);
+    if (st.err & MDE_SKIN) return fail(h, MD_ERR_SKIN_VIOLATION, "an atom moved more than skin/2 between fixed-interval rebuilds");
+    return MD_OK;
+}
+
+int clear_err(md_t *h)
+{
+    CU(cudaMemsetAsync(&h->a.st->err, 0, sizeof(int32_t), h->stream));
+    return MD_OK;
+}
+
+int forces_now(md_t *h, cudaStream_t s)
+{
+    CU(launch_density(h->a, h->pot, h->cfg, s));
+    CU(launch_force(h->a, h->pot, h->cfg, 0, s));
+    CU(launch_reduce(h->a, h->cfg, 0, s));
+    return MD_OK;
+}
+
+int rebuild_now(md_t *h)
+{
+    CU(launch_skin(h->a, h->stream));
+    CU(launch_decide(h->a, 1, 0, 0, h->stream));
+    CU(launch_rebuild(h->a, h->stream));
+    return MD_OK;
+}
+
+// grow the list capacities when the last build overflowed (outside md_step only)
+int rebuild_growing(md_t *h)
+{
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        int rc = clear_err(h);
+        if (rc) return rc;
+        if ((rc = rebuild_now(h))) return rc;
+        DevStatus st;
+        if ((rc = read_status(h, &st))) return rc;
+        bool grow = false;
+        if ((st.err & MDE_OVERFLOW) && st.max_cnt > h->a.kmax) {
+            int k = st.max_cnt + 16;
+            int32_t *p;
+            if ((rc = dalloc(h, &p, (size_t)k * h->a.S))) return rc;
+            h->a.nbr = p; h->a.kmax = k; grow = true;
+        }
+        if ((st.err & MDE_COVERFLOW) && st.max_cntc > h->a.kcmax) {
+            int k = st.max_cntc + 32;
+            int32_t *p;
+            if ((rc = dalloc(h, &p, (size_t)k * h->a.S))) return rc;
+            h->a.nbrc = p; h->a.kcmax = k; grow = true;
+        }
+        if (!grow) return status_to_code(h, st);
+    }
+    return fail(h, MD_ERR_NBR_OVERFLOW, "neighbour capacity kept growing");
+}
+
+void destroy_graphs(md_t *h)
+{
+    if (h->exec1) cudaGraphExecDestroy(h->exec1);
+    if (h->execU) cudaGraphExecDestroy(h->execU);
+    h->exec1 = h->execU = nullptr;
+}
+
+// One graph of `nsteps` whole time steps: per step [k_skin -> k_decide] -> IF(rebuild) ->
+// [k_verlet1 -> k_density -> k_force -> k_reduce].  k_decide sets the step's conditional.
+int capture(md_t *h, int nsteps, cudaGraphExec_t *out)
+{
+    cudaGraph_t g = nullptr;
+    CU(cudaGraphCreate(&g, 0));
+    std::vector<cudaGraphNode_t> deps;
+    const cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+    for (int k = 0; k < nsteps; ++k) {
+        cudaGraphConditionalHandle hc;
+        CU(cudaGraphConditionalHandleCreate(&hc, g, 0, cudaGraphCondAssignDefault));
+        CU(cudaStreamBeginCaptureToGraph(h->cap, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), mode));
+        CU(launch_skin(h->a, h->cap));
+        CU(launch_decide(h->a, 0, 1, hc, h->cap));
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *d = nullptr;
+        size_t nd = 0;
+        CU(cudaStreamGetCaptureInfo(h->cap, &cs, nullptr, nullptr, &d, nullptr, &nd));
+        std::vector<cudaGraphNode_t> cur(d, d + nd);
+        CU(cudaStreamEndCapture(h->cap, &g));
+        alignas(cudaGraphNodeParams) unsigned char cpbuf[sizeof(cudaGraphNodeParams)];
+        memset(cpbuf, 0, sizeof cpbuf);
+        cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cpbuf);
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hc;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cn;
+        CU(cudaGraphAddNode(&cn, g, cur.data(), nullptr, cur.size(), &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        CU(cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, mode));
+        CU(launch_rebuild(h->a, h->cap));
+        CU(cudaStreamEndCapture(h->cap, &body));
+        CU(cudaStreamBeginCaptureToGraph(h->cap, g, &cn, nullptr, 1, mode));
+        CU(launch_verlet1(h->a, h->cap));
+        CU(launch_density(h->a, h->pot, h->cfg, h->cap));
+        CU(launch_force(h->a, h->pot, h->cfg, 1, h->cap));
+        CU(launch_reduce(h->a, h->cfg, 1, h->cap));
+        CU(cudaStreamGetCaptureInfo(h->cap, &cs, nullptr, nullptr, &d, nullptr, &nd));
+        deps.assign(d, d + nd);
+        CU(cudaStreamEndCapture(h->cap, &g));
+    }
+    cudaError_t e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, MD_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    return MD_OK;
+}
+
+int build_graphs(md_t *h)
+{
+    destroy_graphs(h);
+    if (!h->opt.use_graph) return MD_OK;
+    int rc = capture(h, 1, &h->exec1);
+    if (rc) return rc;
+    if (h->unroll > 1) rc = capture(h, h->unroll, &h->execU);
+    return rc;
+}
+
+// the per-step sequence with direct launches (no graph); the host reads the rebuild flag
+int step_direct(md_t *h, cudaEvent_t *ev, bool *rebuilt)
+{
+    cudaStream_t s = h->stream;
+    if (ev) CU(cudaEventRecord(ev[0], s));
+    CU(launch_skin(h->a, s));
+    CU(launch_decide(h->a, 0, 0, 0, s));
+    if (ev) CU(cudaEventRecord(ev[1], s));
+    int32_t flag = 0;
+    CU(cudaMemcpyAsync(&flag, &h->a.st->any_rebuild, sizeof flag, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (ev) CU(cudaEventRecord(ev[2], s));
+    if (flag) CU(launch_rebuild(h->a, s));
+    if (ev) CU(cudaEventRecord(ev[3], s));
+    CU(launch_verlet1(h->a, s));
+    if (ev) CU(cudaEventRecord(ev[4], s));
+    CU(launch_density(h->a, h->pot, h->cfg, s));
+    if (ev) CU(cudaEventRecord(ev[5], s));
+    CU(launch_force(h->a, h->pot, h->cfg, 1, s));
+    if (ev) CU(cudaEventRecord(ev[6], s));
+    CU(launch_reduce(h->a, h->cfg, 1, s));
+    if (ev) CU(cudaEventRecord(ev[7], s));
+    if (rebuilt) *rebuilt = flag != 0;
+    return MD_OK;
+}
+
+int check_replica(md_t *h, int32_t r)
+{
+    if (!h) return MD_ERR_ARG;
+    if (r < 0 || r >= h->n_rep) return fail(h, MD_ERR_ARG, "replica %d out of range [0, %d)", r, h->n_rep);
+    return MD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int md_version(void) { return MD_ABI_VERSION; }
+
+const char *md_last_error(const md_t *h)
+{
+    if (!h) return g_init_error.c_str();
+    return h->err.c_str();
+}
+
+void md_free(md_t *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    destroy_graphs(h);
+    for (auto e : h->ev) cudaEventDestroy(e);
+    for (void *p : h->allocs) cudaFree(p);
+    if (h->tab64) cudaFree(h->tab64);
+    if (h->tab32) cudaFree(h->tab32);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    delete h;
+}
+
+int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, void *cuda_stream, md_t **out)
+{
+    md_t *h = nullptr;
+    if (out) *out = nullptr;
+    if (!sys || !opt || !out || n_replicas < 1 || !opt->pot)
+        return fail(nullptr, MD_ERR_ARG, "md_init: null argument or n_replicas < 1");
+    if (opt->precision != MD_FP64 && opt->precision != MD_MIXED)
+        return fail(nullptr, MD_ERR_ARG, "md_init: precision must be MD_FP64 or MD_MIXED");
+    if (!(opt->skin >= 0.0) || opt->rebuild_every < 0)
+        return fail(nullptr, MD_ERR_ARG, "md_init: skin must be >= 0 and rebuild_every >= 0");
+    int tpa = opt->tpa ? opt->tpa : (opt->precision == MD_MIXED ? 4 : 4);
+    int block = opt->block ? opt->block : 128;
+    if (!(tpa == 1 || tpa == 2 || tpa == 4 || tpa == 8) || block < 32 || block > 256 || block % 32 ||
+        MD_TILE % (block / tpa) != 0)
+        return fail(nullptr, MD_ERR_ARG, "md_init: tpa must be 1, 2, 4 or 8 and block a multiple of 32 in [32, 256] with %d %% (block/tpa) == 0", MD_TILE);
+    h = new md_t();
+    h->stream = (cudaStream_t)cuda_stream;
+    h->opt = *opt;
+    h->pot_h = *opt->pot;
+    h->opt.pot = &h->pot_h;
+    h->cfg.tpa = tpa;
+    h->cfg.block = block;
+    h->n_rep = n_replicas;
+    int rc = MD_OK;
+#define INIT_FAIL(code_expr)                    \
+    do {                                        \
+        int c_ = (code_expr);                   \
+        if (c_) {                               \
+            g_init_error = h->err;              \
+            md_free(h);                         \
+            return c_;                          \
+        }                                       \
+    } while (0)
+
+#define CUI(call) INIT_FAIL(cu_check(h, (call), #call))
+    char ebuf[256] = {0};
+    rc = md_build_pot(&h->pot_h, &h->pot, &h->tab64, &h->tab32, ebuf, sizeof ebuf);
+    if (rc) { h->err = ebuf; INIT_FAIL(rc); }
+
+    const double cut = h->pot_h.rc + opt->skin, cutc = h->pot_h.rc_morse + opt->skin;
+    // ---- layout
+    int64_t slots = 0, cells = 0, ccells = 0, real = 0, cslots = 0;
+    size_t max_n = 1;
+    h->rep.resize(n_replicas);
+    for (int r = 0; r < n_replicas; ++r) {
+        const md_system &y = sys[r];
+        RepDev &R = h->rep[r];
+        memset(&R, 0, sizeof R);
+        if (y.n_cr < 1 || y.n_c < 0 || !y.x_cr || !y.v_cr || (y.n_c > 0 && !y.x_c) || !(y.dt > 0) || !(y.mass_cr > 0))
+            INIT_FAIL(fail(h, MD_ERR_ARG, "replica %d: need n_cr >= 1, positions, velocities, dt > 0, mass > 0", r));
+        for (int k = 0; k < 3; ++k) {
+            R.lo[k] = y.box_lo[k]; R.hi[k] = y.box_hi[k]; R.L[k] = y.box_hi[k] - y.box_lo[k];
+            R.per[k] = y.periodic[k] ? 1 : 0;
+            if (!(R.L[k] > 0)) INIT_FAIL(fail(h, MD_ERR_ARG, "replica %d: box_hi must exceed box_lo", r));
+            int n = (int)floor(R.L[k] / cut);
+            if (n < 1) n = 1;
+            if (R.per[k] && n < 3)
+                INIT_FAIL(fail(h, MD_ERR_ARG, "replica %d: periodic axis %d is %.3f A, shorter than 3 cells of rc + skin = %.3f A", r, k, R.L[k], cut));
+            if (n > (1 << MD_CELL_BITS) - 1)
+                INIT_FAIL(fail(h, MD_ERR_ARG, "replica %d: axis %d needs %d cells, more than %d", r, k, n, (1 << MD_CELL_BITS) - 1));
+            R.nc[k] = n;
+            R.w[k] = R.L[k] / n;
+            R.w32[k] = (float)R.w[k];
+        }
+        R.cell_off = (int32_t)cells;
+        R.n_cells = R.nc[0] * R.nc[1] * R.nc[2];
+        cells += R.n_cells;
+        R.slot_off = (int32_t)slots;
+        R.n_atoms = y.n_cr;
+        R.n_slots = (y.n_cr + MD_TILE - 1) / MD_TILE * MD_TILE;
+        R.real_off = (int32_t)real;
+        slots += R.n_slots;
+        real += y.n_cr;
+        max_n = std::max(max_n, (size_t)y.n_cr);
+        int nmob = 0;
+        for (int i = 0; i < y.n_cr; ++i) nmob += (y.fixed && y.fixed[i]) ? 0 : 1;
+        R.n_mobile = nmob;
+        R.v_ind = y.v_indenter; R.dt = y.dt; R.mass = y.mass_cr; R.acc_per_f = MD_ACC / y.mass_cr;
+        double ztop = -1e300;
+        for (int i = 0; i < y.n_cr; ++i) ztop = std::max(ztop, y.x_cr[3 * i + 2]);
+        R.z_surface0 = ztop;
+        // indenter grid over the bounding box of x_c
+        R.c_off = (int32_t)cslots;
+        R.n_c = y.n_c;
+        R.ccell_off = (int32_t)ccells;
+        if (y.n_c > 0) {
+            double bl[3], bh[3];
+            for (int k = 0; k < 3; ++k) { bl[k] = 1e300; bh[k] = -1e300; }
+            for (int c = 0; c < y.n_c; ++c)
+                for (int k = 0; k < 3; ++k) { bl[k] = std::min(bl[k], y.x_c[3 * c + k]); bh[k] = std::max(bh[k], y.x_c[3 * c + k]); }
+            R.zc_min0 = bl[2];
+            for (int k = 0; k < 3; ++k) {
+                double ext = (bh[k] - bl[k]) + 1e-6;
+                int n = (int)floor(ext / cutc);
+                if (n < 1) n = 1;
+                R.cg_n[k] = n; R.cg_w[k] = ext / n; R.cg_lo[k] = bl[k] - 0.5e-6;
+                if (R.per[k] && (bh[k] - bl[k]) + 2.0 * cutc > R.L[k])
+                    INIT_FAIL(fail(h, MD_ERR_ARG, "replica %d: indenter (%.2f A) plus twice the Morse reach exceeds the periodic length %.2f A on axis %d", r, bh[k] - bl[k], R.L[k], k));
+            }
+            ccells += R.cg_n[0] * R.cg_n[1] * R.cg_n[2];
+        }
+        cslots += y.n_c;
+    }
+    if (slots >= (int64_t)1 << 31 || cells >= (int64_t)1 << 31)
+        INIT_FAIL(fail(h, MD_ERR_ARG, "too many atoms or cells for 32-bit slot indices"));
+    h->n_cr = real; h->n_c = cslots;
+    const int S = (int)slots;
+    DevArgs &a = h->a;
+    a.S = S; a.n_rep = n_replicas; a.total_cells = (int)cells;
+    a.kmax = opt->kmax > 0 ? opt->kmax : 80;
+    a.kcmax = opt->kcmax > 0 ? opt->kcmax : 160;
+    a.mixed = opt->precision == MD_MIXED;
+    a.rebuild_every = opt->rebuild_every;
+    a.skin = opt->skin; a.cut = cut; a.cutc = cutc; a.cut2 = cut * cut; a.cutc2 = cutc * cutc;
+    a.C = (int)cslots;
+    a.max_blocks = S / (block / tpa) + 1;
+
+    // ---- device memory
+    RepDev *d_rep; RepState *d_rs; RepEnergy *d_en; DevStatus *d_st;
+    int32_t *d_tile_rep, *d_cell_rep;
+    INIT_FAIL(dalloc(h, &d_rep, n_replicas));
+    INIT_FAIL(dalloc(h, &d_rs, n_replicas));
+    INIT_FAIL(dalloc(h, &d_en, n_replicas));
+    INIT_FAIL(dalloc(h, &d_st, 1));
+    INIT_FAIL(dalloc(h, &d_tile_rep, S / MD_TILE));
+    INIT_FAIL(dalloc(h, &d_cell_rep, cells));
+    a.rep = d_rep; a.rs = d_rs; a.en = d_en; a.st = d_st; a.tile_rep = d_tile_rep; a.cell_rep = d_cell_rep;
+    INIT_FAIL(dalloc(h, &a.x, 3 * (size_t)S));
+    INIT_FAIL(dalloc(h, &a.v, 3 * (size_t)S));
+    INIT_FAIL(dalloc(h, &a.F, 3 * (size_t)S));
+    INIT_FAIL(dalloc(h, &a.xb, 3 * (size_t)S));
+    INIT_FAIL(dalloc(h, &a.pos4, S));
+    INIT_FAIL(dalloc(h, &a.fm64, S));
+    INIT_FAIL(dalloc(h, &a.fm32, S));
+    INIT_FAIL(dalloc(h, &a.cellc, S));
+    INIT_FAIL(dalloc(h, &a.orig, S));
+    INIT_FAIL(dalloc(h, &a.fixed, S));
+    INIT_FAIL(dalloc(h, &a.nbr, (size_t)a.kmax * S));
+    INIT_FAIL(dalloc(h, &a.cnt, S));
+    INIT_FAIL(dalloc(h, &a.nbrc, (size_t)a.kcmax * S));
+    INIT_FAIL(dalloc(h, &a.cntc, S));
+    INIT_FAIL(dalloc(h, &a.key, S));
+    INIT_FAIL(dalloc(h, &a.perm, S));
+    INIT_FAIL(dalloc(h, &a.cell_count, cells));
+    INIT_FAIL(dalloc(h, &a.cell_start, cells));
+    INIT_FAIL(dalloc(h, &a.cell_fill, cells));
+    INIT_FAIL(dalloc(h, &a.scan_blk, cells / 1024 + 2));
+    INIT_FAIL(dalloc(h, &a.sx, 3 * (size_t)S));
+    INIT_FAIL(dalloc(h, &a.sv, 3 * (size_t)S));
+    INIT_FAIL(dalloc(h, &a.sF, 3 * (size_t)S));
+    INIT_FAIL(dalloc(h, &a.sorig, S));
+    INIT_FAIL(dalloc(h, &a.sfixed, S));
+    INIT_FAIL(dalloc(h, &a.part, 6 * (size_t)a.max_blocks));
+    double *d_xc0; int32_t *d_ccs, *d_ccc;
+    INIT_FAIL(dalloc(h, &d_xc0, 3 * (size_t)(cslots > 0 ? cslots : 1)));
+    INIT_FAIL(dalloc(h, &d_ccs, ccells > 0 ? ccells : 1));
+    INIT_FAIL(dalloc(h, &d_ccc, ccells > 0 ? ccells : 1));
+    a.xc0 = d_xc0; a.ccell_start = d_ccs; a.ccell_count = d_ccc;
+    INIT_FAIL(dalloc(h, &h->stage, 6 * max_n));
+
+    // ---- host staging in slot order (initial slot order = caller order)
+    {
+        std::vector<double> hx(3 * (size_t)S, 0.0), hv(3 * (size_t)S, 0.0);
+        std::vector<int32_t> horig(S, 0), htile(S / MD_TILE), hcell(cells);
+        std::vector<uint8_t> hfix(S, 1);
+        std::vector<double> hxc(3 * (size_t)(cslots > 0 ? cslots : 1), 0.0);
+        std::vector<int32_t> hccs(ccells > 0 ? ccells : 1, 0), hccc(ccells > 0 ? ccells : 1, 0);
+        h->c_orig.assign(cslots > 0 ? cslots : 1, 0);
+        std::vector<RepState> hrs(n_replicas);
+        for (int r = 0; r < n_replicas; ++r) {
+            const md_system &y = sys[r];
+            const RepDev &R = h->rep[r];
+            for (int t = R.slot_off / MD_TILE; t < (R.slot_off + R.n_slots) / MD_TILE; ++t) htile[t] = r;
+            for (int c = R.cell_off; c < R.cell_off + R.n_cells; ++c) hcell[c] = r;
+            for (int i = 0; i < y.n_cr; ++i) {
+                int s = R.slot_off + i;
+                for (int k = 0; k < 3; ++k) {
+                    hx[(size_t)k * S + s] = y.x_cr[3 * i + k];
+                    hv[(size_t)k * S + s] = y.v_cr[3 * i + k];
+                }
+                horig[s] = i;
+                hfix[s] = (y.fixed && y.fixed[i]) ? 1 : 0;
+                if (hfix[s]) for (int k = 0; k < 3; ++k) hv[(size_t)k * S + s] = 0.0;
+            }
+            // indenter: counting sort by indenter cell (static, once)
+            if (y.n_c > 0) {
+                int nc3 = R.cg_n[0] * R.cg_n[1] * R.cg_n[2];
+                std::vector<int32_t> key(y.n_c), cnt(nc3, 0), start(nc3 + 1, 0);
+                for (int c = 0; c < y.n_c; ++c) {
+                    int q[3];
+                    for (int k = 0; k < 3; ++k) {
+                        int t = (int)floor((y.x_c[3 * c + k] - R.cg_lo[k]) / R.cg_w[k]);
+                        q[k] = std::min(std::max(t, 0), R.cg_n[k] - 1);
+                    }
+                    key[c] = (q[2] * R.cg_n[1] + q[1]) * R.cg_n[0] + q[0];
+                    cnt[key[c]]++;
+                }
+                for (int k = 0; k < nc3; ++k) start[k + 1] = start[k] + cnt[k];
+                std::vector<int32_t> fill(start.begin(), start.end() - 1);
+                for (int c = 0; c < y.n_c; ++c) {
+                    int t = R.c_off + fill[key[c]]++;
+                    for (int k = 0; k < 3; ++k) hxc[(size_t)k * cslots + t] = y.x_c[3 * c + k];
+                    h->c_orig[t] = c;
+                }
+                for (int k = 0; k < nc3; ++k) { hccs[R.ccell_off + k] = R.c_off + start[k]; hccc[R.ccell_off + k] = cnt[k]; }
+            }
+            hrs[r].z_ind = y.z_indenter0;
+            hrs[r].z_build = y.z_indenter0;
+        }
+        CUI(cudaMemcpy(a.x, hx.data(), hx.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CUI(cudaMemcpy(a.v, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CUI(cudaMemcpy(a.orig, horig.data(), S * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CUI(cudaMemcpy(a.fixed, hfix.data(), S, cudaMemcpyHostToDevice));
+        CUI(cudaMemcpy(d_tile_rep, htile.data(), htile.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CUI(cudaMemcpy(d_cell_rep, hcell.data(), hcell.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CUI(cudaMemcpy(d_rep, h->rep.data(), n_replicas * sizeof(RepDev), cudaMemcpyHostToDevice));
+        CUI(cudaMemcpy(d_rs, hrs.data(), n_replicas * sizeof(RepState), cudaMemcpyHostToDevice));
+        if (cslots > 0) {
+            CUI(cudaMemcpy(d_xc0, hxc.data(), 3 * (size_t)cslots * sizeof(double), cudaMemcpyHostToDevice));
+            CUI(cudaMemcpy(d_ccs, hccs.data(), ccells * sizeof(int32_t), cudaMemcpyHostToDevice));
+            CUI(cudaMemcpy(d_ccc, hccc.data(), ccells * sizeof(int32_t), cudaMemcpyHostToDevice));
+        }
+    }
+    CUI(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    h->ev.resize(8);
+    for (auto &e : h->ev) CUI(cudaEventCreate(&e));
+    h->unroll = real < 200000 ? 8 : 1;
+
+    // ---- first list build and forces at t = 0
+    INIT_FAIL(rebuild_growing(h));
+    INIT_FAIL(forces_now(h, h->stream));
+    {
+        DevStatus st;
+        INIT_FAIL(read_status(h, &st));
+        INIT_FAIL(status_to_code(h, st));
+        st.rebuilds = 0; st.step = 0; st.since_build = 0;
+        CUI(cudaMemcpy(a.st, &st, sizeof st, cudaMemcpyHostToDevice));
+    }
+    h->forces_valid = true;
+    INIT_FAIL(build_graphs(h));
+    CUI(cudaStreamSynchronize(h->stream));
+    *out = h;
+    return MD_OK;
+#undef INIT_FAIL
+#undef CUI
+}
+
+int md_build_neighbors(md_t *h)
+{
+    if (!h) return MD_ERR_ARG;
+    size_t kmax0 = h->a.kmax, kc0 = h->a.kcmax;
+    int rc = rebuild_growing(h);
+    if (rc) return rc;
+    if ((size_t)h->a.kmax != kmax0 || (size_t)h->a.kcmax != kc0) {
+        if ((rc = build_graphs(h))) return rc;
+    }
+    CU(cudaStreamSynchronize(h->stream));
+    return MD_OK;
+}
+
+int md_compute_forces(md_t *h)
+{
+    if (!h) return MD_ERR_ARG;
+    int rc = forces_now(h, h->stream);
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(h->stream));
+    h->forces_valid = true;
+    return MD_OK;
+}
+
+static int ensure_forces(md_t *h)
+{
+    if (h->forces_valid) return MD_OK;
+    int rc = md_build_neighbors(h);
+    if (rc) return rc;
+    rc = forces_now(h, h->stream);
+    if (rc) return rc;
+    h->forces_valid = true;
+    return MD_OK;
+}
+
+int md_step(md_t *h, int64_t n)
+{
+    if (!h) return MD_ERR_ARG;
+    if (n < 0) return fail(h, MD_ERR_ARG, "md_step: n < 0");
+    int rc = ensure_forces(h);
+    if (rc) return rc;
+    if ((rc = clear_err(h))) return rc;
+    if (h->opt.use_graph && h->exec1) {
+        int64_t k = 0;
+        if (h->execU)
+            for (; k + h->unroll <= n; k += h->unroll) CU(cudaGraphLaunch(h->execU, h->stream));
+        for (; k < n; ++k) CU(cudaGraphLaunch(h->exec1, h->stream));
+    } else {
+        for (int64_t k = 0; k < n; ++k)
+            if ((rc = step_direct(h, nullptr, nullptr))) return rc;
+    }
+    DevStatus st;
+    if ((rc = read_status(h, &st))) return rc;
+    return status_to_code(h, st);
+}
+
+int md_step_profiled(md_t *h, int64_t n, md_phase_times *out)
+{
+    if (!h || !out) return MD_ERR_ARG;
+    int rc = ensure_forces(h);
+    if (rc) return rc;
+    if ((rc = clear_err(h))) return rc;
+    memset(out, 0, sizeof *out);
+    for (int64_t k = 0; k < n; ++k) {
+        bool rebuilt = false;
+        if ((rc = step_direct(h, h->ev.data(), &rebuilt))) return rc;
+        CU(cudaEventSynchronize(h->ev[7]));
+        float ms[7];
+        for (int p = 0; p < 7; ++p) CU(cudaEventElapsedTime(&ms[p], h->ev[p], h->ev[p + 1]));
+        out->skin += ms[0];
+        out->rebuild += ms[2];
+        out->verlet1 += ms[3];
+        out->density += ms[4];
+        out->force += ms[5];
+        out->reduce += ms[6];
+        out->steps += 1;
+        out->rebuilds += rebuilt ? 1 : 0;
+    }
+    DevStatus st;
+    if ((rc = read_status(h, &st))) return rc;
+    return status_to_code(h, st);
+}
+
+int md_get_energy(md_t *h, int32_t r, md_energy *out)
+{
+    int rc = check_replica(h, r);
+    if (rc) return rc;
+    if (!out) return fail(h, MD_ERR_ARG, "md_get_energy: null output");
+    RepEnergy E; DevStatus st; RepState rs;
+    CU(cudaMemcpyAsync(&E, h->a.en + r, sizeof E, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&rs, h->a.rs + r, sizeof rs, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&st, h->a.st, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    const RepDev &R = h->rep[r];
+    out->embed = E.embed; out->pair = E.pair; out->mterm = E.mterm; out->morse = E.morse;
+    out->kinetic = E.kinetic;
+    out->potential = E.embed + E.pair + E.mterm + E.morse;
+    out->total = out->potential + E.kinetic;
+    out->temperature = R.n_mobile > 0 ? 2.0 * E.kinetic / (3.0 * MD_KB * R.n_mobile) : 0.0;
+    out->load = E.load;
+    out->z_indenter = rs.z_ind;
+    out->depth = R.n_c > 0 ? R.z_surface0 - (R.zc_min0 + rs.z_ind) : 0.0;
+    out->step = st.step;
+    out->rebuilds = st.rebuilds;
+    return MD_OK;
+}
+
+static int fetch(md_t *h, int32_t r, const double *src, double *out3n)
+{
+    const RepDev &R = h->rep[r];
+    int n = R.n_atoms;
+    k_state_out<<<(n + 255) / 256, 256, 0, h->stream>>>(src, h->stage, h->a.orig, R.slot_off, n, h->a.S);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(out3n, h->stage, 3 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return MD_OK;
+}
+
+int md_get_forces(md_t *h, int32_t r, double *out3n)
+{
+    int rc = check_replica(h, r);
+    if (rc) return rc;
+    if (!out3n) return fail(h, MD_ERR_ARG, "md_get_forces: null output");
+    return fetch(h, r, h->a.F, out3n);
+}
+
+int md_get_indenter_load(md_t *h, int32_t r, double *load_z, double *depth)
+{
+    md_energy e;
+    int rc = md_get_energy(h, r, &e);
+    if (rc) return rc;
+    if (load_z) *load_z = e.load;
+    if (depth) *depth = e.depth;
+    return MD_OK;
+}
+
+int md_get_state(md_t *h, int32_t r, double *x3n, double *v3n, double *z_ind, int64_t *step)
+{
+    int rc = check_replica(h, r);
+    if (rc) return rc;
+    if (x3n && (rc = fetch(h, r, h->a.x, x3n))) return rc;
+    if (v3n && (rc = fetch(h, r, h->a.v, v3n))) return rc;
+    if (z_ind || step) {
+        RepState rs; DevStatus st;
+        CU(cudaMemcpyAsync(&rs, h->a.rs + r, sizeof rs, cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaMemcpyAsync(&st, h->a.st, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        if (z_ind) *z_ind = rs.z_ind;
+        if (step) *step = st.step;
+    }
+    return MD_OK;
+}
+
+int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, double z_ind, int64_t step)
+{
+    int rc = check_replica(h, r);
+    if (rc) return rc;
+    const RepDev &R = h->rep[r];
+    int n = R.n_atoms;
+    if (x3n) {
+        CU(cudaMemcpyAsync(h->stage, x3n, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        k_state_in<<<(n + 255) / 256, 256, 0, h->stream>>>(h->stage, h->a.x, h->a.orig, R.slot_off, n, h->a.S);
+        CU(cudaGetLastError());
+    }
+    if (v3n) {
+        double *st2 = h->stage + 3 * (size_t)n;
+        CU(cudaMemcpyAsync(st2, v3n, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        k_state_in<<<(n + 255) / 256, 256, 0, h->stream>>>(st2, h->a.v, h->a.orig, R.slot_off, n, h->a.S);
+        CU(cudaGetLastError());
+    }
+    k_set_scalars<<<1, 1, 0, h->stream>>>(h->a.rs, r, z_ind, h->a.st, (long long)step, 1);
+    CU(cudaGetLastError());
+    h->forces_valid = false;
+    return ensure_forces(h);
+}
+
+int md_get_neighbors(md_t *h, int32_t r, int32_t which, int32_t *cell_xyz, int32_t *cnt, int32_t *nbr, int32_t kmax)
+{
+    int rc = check_replica(h, r);
+    if (rc) return rc;
+    if (!cnt || (nbr && kmax < 1)) return fail(h, MD_ERR_ARG, "md_get_neighbors: cnt required, kmax >= 1 with nbr");
+    const RepDev &R = h->rep[r];
+    int n = R.n_atoms, S = h->a.S;
+    int K = which ? h->a.kcmax : h->a.kmax;
+    std::vector<int32_t> orig(n), c(n), cellc(n), list;
+    CU(cudaMemcpy(orig.data(), h->a.orig + R.slot_off, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(c.data(), (which ? h->a.cntc : h->a.cnt) + R.slot_off, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(cellc.data(), h->a.cellc + R.slot_off, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (nbr) {
+        list.resize((size_t)K * n);
+        for (int k = 0; k < K; ++k)
+            CU(cudaMemcpy(list.data() + (size_t)k * n, (which ? h->a.nbrc : h->a.nbr) + (size_t)k * S + R.slot_off,
+                          n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    }
+    const int M = (1 << MD_CELL_BITS) - 1;
+    for (int i = 0; i < n; ++i) {
+        int o = orig[i];
+        cnt[o] = c[i];
+        if (cell_xyz) {
+            cell_xyz[3 * o] = cellc[i] & M;
+            cell_xyz[3 * o + 1] = (cellc[i] >> MD_CELL_BITS) & M;
+            cell_xyz[3 * o + 2] = (cellc[i] >> (2 * MD_CELL_BITS)) & M;
+        }
+        if (nbr) {
+            int m = std::min(c[i], kmax);
+            for (int k = 0; k < m; ++k) {
+                int e = list[(size_t)k * n + i];
+                nbr[(size_t)o * kmax + k] = which ? h->c_orig[e] : orig[e - R.slot_off];
+            }
+        }
+    }
+    return MD_OK;
+}
+
+int md_get_info(md_t *h, int64_t *out9)
+{
+    if (!h || !out9) return MD_ERR_ARG;
+    DevStatus st;
+    int rc = read_status(h, &st);
+    if (rc) return rc;
+    out9[0] = h->n_rep; out9[1] = h->n_cr; out9[2] = h->n_c; out9[3] = h->a.S; out9[4] = h->a.total_cells;
+    out9[5] = h->a.kmax; out9[6] = h->a.kcmax; out9[7] = st.max_cnt; out9[8] = st.max_cntc;
+    return MD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// md_internal.h -- device data layout and kernel launchers of libmd (sm_103a).
+//
+// Layout in HBM (all replicas concatenated; "slots" are atom places in cell order):
+//   - every replica's slot range starts on a TILE-aligned boundary (tiles never span two
+//     replicas, so a CTA's atoms belong to one replica and per-replica sums are plain
+//     per-CTA partials); slots past a replica's last atom are padding (never binned,
+//     never listed, never integrated);
+//   - per-atom SoA arrays: x[3][S], v[3][S], F[3][S], x_build[3][S] (FP64),
+//     pos4[S] (float4: position relative to the atom's cell centre in FP32, and the
+//     atom's cell coordinates packed in .w), fm (F'(rho), M'(P) per atom: double2 in FP64
+//     mode, float2 in mixed mode), cellc[S] (packed cell coordinates), orig[S] (caller id),
+//     fixed[S] (uint8);
+//   - Verlet lists in SoA form nbr[k * S + i] (slot of the k-th neighbour of slot i), so a
+//     warp reading its 32 atoms' k-th entries reads 128 consecutive bytes, and cnt[S];
+//     the Cr-C list the same with indenter slots;
+//   - the Cr cell grid: cell_start/cell_count per cell (replica cell ranges concatenated);
+//   - the indenter: FP64 SoA positions at t = 0 sorted by their own cell grid (built once),
+//     with per-replica displacement z_ind held on the device.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/md.h"
+
+#define MD_TILE 128          // slots per tile; a CTA of the per-atom kernels covers <= one tile
+#define MD_ACC 9.6485332e-3  // 1 eV/(A u) in A/fs^2
+#define MD_KB 8.617333262e-5 // Boltzmann constant, eV/K
+#define MD_CELL_BITS 10      // bits per packed cell coordinate (grids up to 1024 cells per axis)
+
+// error bits raised by kernels (device word, read by the host after md_step)
+enum { MDE_OVERFLOW = 1, MDE_LOST = 2, MDE_SKIN = 4, MDE_COVERFLOW = 8 };
+
+// Hermite cubic coefficients of one table interval, c0 + c1 t + c2 t^2 + c3 t^3
+struct alignas(32) Cf64 {
+    double x, y, z, w;
+};
+
+// potential, passed by value to kernels (lives in the constant bank)
+struct PotDev {
+    // Eq. A2: f = f_e (r_e/r)^beta = exp2(lf0 - beta log2 r)
+    double f_e, r_e, beta, lf0;
+    // Eq. A3
+    double F_o, n, rho_e, alpha, P_e;
+    // Eq. A4 about the double root x = d: with t = r/r_e - d <= 0,
+    // Phi = t^2 (b0 + b1 t + b2 t^2 + b3 t^3)   (no cancellation near the cut-off)
+    double b[4], d;
+    // Eq. A5 with E = exp(-(alpha_x/2)(y/y_eq - 1)): phi = D_o (E^2 - 2E)
+    double D_o, half_ax, inv_yeq;
+    double rc, rc_m, rc2, rcm2;
+    double f_rc, df_rc, m_rc, dm_rc;   // shifted-force constants, 0 when truncating
+    int32_t shifted, tabulated;
+    // tables: interval k covers [r_min + k h, r_min + (k+1) h]; coefficients c0..c3 of
+    // the Hermite cubic in t in [0, 1); forces are d/dr of the same cubic
+    double r_min, inv_hf, inv_hm;
+    int32_t nf, nm;
+    const Cf64 *tf, *tp, *tm;
+    const float4 *tf32, *tp32, *tm32;
+};
+
+// static per-replica description (read-only on the device)
+struct RepDev {
+    double lo[3], hi[3], L[3], w[3];  // Cr cell grid; L = hi - lo; w = L / nc
+    int32_t per[3], nc[3];
+    float w32[3];
+    int32_t cell_off, n_cells;
+    int32_t slot_off, n_atoms, n_slots;  // first slot (TILE aligned), real atoms, slots incl. padding
+    int32_t real_off;                    // atoms of the replicas before (unpadded)
+    int32_t n_mobile;
+    // indenter
+    int32_t c_off, n_c;                  // indenter slots
+    double cg_lo[3], cg_w[3];            // indenter cell grid in its own frame (t = 0)
+    int32_t cg_n[3], ccell_off;
+    // dynamics
+    double v_ind, dt, mass, acc_per_f;   // acc_per_f = MD_ACC / mass
+    double z_surface0, zc_min0;
+};
+
+// mutable per-replica scalars
+struct RepState {
+    double z_ind, z_build;
+    unsigned long long d2max_bits;       // max |x - x_build|^2 since last decision (bits of a double)
+    int32_t need;                        // rebuild decided for this step
+    int32_t pad;
+};
+
+// energies of one replica (device copy of md_energy's sums)
+struct RepEnergy {
+    double embed, pair, mterm, morse, kinetic, load;
+};
+
+// global counters and flags
+struct DevStatus {
+    int32_t err;            // MDE_* bits
+    int32_t any_rebuild;    // rebuild decided this step (host-readable)
+    int32_t max_cnt, max_cntc;
+    int64_t step, rebuilds, since_build;
+};
+
+// everything the kernels need, by value
+struct DevArgs {
+    int32_t S;               // slots
+    int32_t n_rep;
+    int32_t total_cells;
+    int32_t kmax, kcmax;
+    int32_t mixed;
+    int32_t rebuild_every;
+    double skin, cut2, cutc2, cut, cutc;
+    const RepDev *rep;
+    RepState *rs;
+    RepEnergy *en;
+    DevStatus *st;
+    const int32_t *tile_rep;     // replica of each tile
+    const int32_t *cell_rep;     // replica of each cell
+    // per-atom
+    double *x, *v, *F, *xb;      // [3][S]
+    float4 *pos4;
+    double2 *fm64;
+    float2 *fm32;
+    int32_t *cellc, *orig;
+    uint8_t *fixed;
+    int32_t *nbr, *cnt, *nbrc, *cntc;
+    // rebuild scratch
+    int32_t *key, *perm, *cell_count, *cell_start, *cell_fill, *scan_blk;
+    double *sx, *sv, *sF;        // [3][S] gather scratch
+    int32_t *sorig;
+    uint8_t *sfixed;
+    // indenter (sorted by indenter cell)
+    const double *xc0;           // [3][C]
+    const int32_t *ccell_start, *ccell_count;
+    int32_t C;
+    // block partial sums: [6][max_blocks]
+    double *part;
+    int32_t max_blocks;
+};
+
+struct LaunchCfg {
+    int32_t tpa;      // threads per atom
+    int32_t block;    // threads per block
+};
+
+// ---- host-side helpers implemented in md_kernels.cu
+int md_build_pot(const md_params *p, PotDev *out, Cf64 **d_tabs64, float4 **d_tabs32, char *err, size_t errlen);
+
+// ---- launchers (all enqueue on `s`; return cudaError_t of the launch)
+cudaError_t launch_skin(const DevArgs &a, cudaStream_t s);
+cudaError_t launch_decide(const DevArgs &a, int force, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s);
+cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s);
+cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, cudaStream_t s);
+cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, int advance, cudaStream_t s);
+cudaError_t launch_refresh_pos4(const DevArgs &a, cudaStream_t s);

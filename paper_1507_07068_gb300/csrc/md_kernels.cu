@@ -1,0 +1,1105 @@
+// md_kernels.cu -- the sm_103a kernels of libmd and their launchers.
+//
+// Per time step (Fig. 5 / Table 1 of Pal et al., arXiv:1507.07068):
+//   k_skin      Task 1 test: max_i |x_i - x_build,i|^2 per replica (FP64)
+//   k_decide    Task 1 decision (Sec. 2.6 skin/2 rule) -> device flag + graph conditional
+//   [rebuild]   Task 1 rebuild: k_bin (wrap, FP64 cell keys, histogram), scan, k_scatter,
+//               k_cellsort (ascending caller id within a cell), k_gather/k_copyback
+//               (permute every per-atom array), k_nbr (full Cr-Cr Verlet list), k_nbrc
+//               (Cr-C list through the indenter's own cell grid), k_build_done
+//   k_verlet1   Tasks 2+3: indenter move, half kick + drift (Eqs. A11-A12), refresh of the
+//               FP32 cell-relative positions
+//   k_density   Task 4a: rho_i, P_i (Eq. A2) -> F'(rho_i), M'(P_i), F(rho_i), M(P_i) (Eq. A3)
+//   k_force     Task 4b,c + 5: Eq. (1) with the M term (A6-A8, A10), Morse (A5, A9),
+//               indenter load; epilogue: closing half kick (Task 5), kinetic energy
+//   k_reduce    per-replica FP64 sums of the CTA partials in a fixed order
+// Every per-atom kernel writes only its own atom (full neighbour list: no atomics in
+// the force path); energy and load sums are warp-shuffle -> CTA partial -> fixed-order
+// final pass, so results do not depend on scheduling.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "md_internal.h"
+
+// ============================================================================ host:
+// potential forms used to fill the tables (FP64), restated from the Appendix.
+
+namespace {
+
+struct HostPot {
+    md_params p;
+    double f_rc = 0, df_rc = 0, m_rc = 0, dm_rc = 0;
+    double e[4];   // Eq. A4 about x = d: Phi = t^2 (e0 + e1 t + e2 t^2 + e3 t^3), t = r/r_e - d
+
+    double f_raw(double r) const { return p.f_e * pow(p.r_e / r, p.beta); }
+    double df_raw(double r) const { return -p.beta * f_raw(r) / r; }
+    void morse_raw(double y, double &v, double &dv) const {
+        double E = exp(-0.5 * p.alpha_x * (y / p.y_eq - 1.0));
+        v = p.D_o * E * (E - 2.0);
+        dv = -p.D_o * p.alpha_x / p.y_eq * E * (E - 1.0);
+    }
+    void f(double r, double &v, double &dv) const {   // r < rc branch
+        v = f_raw(r) - f_rc - (r - p.rc) * df_rc;
+        dv = df_raw(r) - df_rc;
+    }
+    void phi(double r, double &v, double &dv) const {
+        double t = r / p.r_e - p.d;
+        if (t > 0.0) { v = dv = 0.0; return; }
+        v = t * t * (e[0] + t * (e[1] + t * (e[2] + t * e[3])));
+        dv = t * (2.0 * e[0] + t * (3.0 * e[1] + t * (4.0 * e[2] + t * 5.0 * e[3]))) / p.r_e;
+    }
+    void morse(double y, double &v, double &dv) const {
+        morse_raw(y, v, dv);
+        v -= m_rc + (y - p.rc_morse) * dm_rc;
+        dv -= dm_rc;
+    }
+};
+
+// cubic on [0,1) from end values g0, g1 and end slopes (per unit t) m0, m1
+void hermite_coeffs(double g0, double g1, double m0, double m1, Cf64 &c)
+{
+    c.x = g0;
+    c.y = m0;
+    c.z = 3.0 * (g1 - g0) - 2.0 * m0 - m1;
+    c.w = 2.0 * (g0 - g1) + m0 + m1;
+}
+
+template <class Fn>
+void fill_table(int n, double r0, double r1, Fn g, std::vector<Cf64> &out)
+{
+    out.resize(n);
+    double h = (r1 - r0) / n;
+    std::vector<double> v(n + 1), d(n + 1);
+    for (int k = 0; k <= n; ++k) {
+        double r = (k == n) ? r1 : r0 + k * h;
+        g(r, v[k], d[k]);
+    }
+    for (int k = 0; k < n; ++k) hermite_coeffs(v[k], v[k + 1], d[k] * h, d[k + 1] * h, out[k]);
+}
+
+}  // namespace
+
+int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs32, char *err, size_t errlen)
+{
+    memset(P, 0, sizeof(*P));
+    if (!(p->r_e > 0 && p->f_e > 0 && p->rho_e > 0 && p->P_e > 0 && p->y_eq > 0 && p->rc > 0 &&
+          p->rc_morse > 0 && p->r_min > 0 && p->r_min < p->rc && p->r_min < p->rc_morse && p->h > 0)) {
+        snprintf(err, errlen, "md_params: r_e, f_e, rho_e, P_e, y_eq, rc, rc_morse, h must be > 0 and r_min < both cut-offs");
+        return MD_ERR_ARG;
+    }
+    HostPot H;
+    H.p = *p;
+    // Taylor coefficients of the cubic of Eq. A4 about x = d
+    const double *a = p->a, d = p->d;
+    H.e[0] = ((a[3] * d + a[2]) * d + a[1]) * d + a[0];
+    H.e[1] = (3.0 * a[3] * d + 2.0 * a[2]) * d + a[1];
+    H.e[2] = 3.0 * a[3] * d + a[2];
+    H.e[3] = a[3];
+    if (p->shifted) {
+        H.f_rc = H.f_raw(p->rc);
+        H.df_rc = H.df_raw(p->rc);
+        H.morse_raw(p->rc_morse, H.m_rc, H.dm_rc);
+    }
+    P->f_e = p->f_e; P->r_e = p->r_e; P->beta = p->beta;
+    P->lf0 = log2(p->f_e) + p->beta * log2(p->r_e);
+    P->F_o = p->F_o; P->n = p->n; P->rho_e = p->rho_e; P->alpha = p->alpha; P->P_e = p->P_e;
+    for (int k = 0; k < 4; ++k) P->b[k] = H.e[k];
+    P->d = d;
+    P->D_o = p->D_o; P->half_ax = 0.5 * p->alpha_x; P->inv_yeq = 1.0 / p->y_eq;
+    P->rc = p->rc; P->rc_m = p->rc_morse; P->rc2 = p->rc * p->rc; P->rcm2 = p->rc_morse * p->rc_morse;
+    P->f_rc = H.f_rc; P->df_rc = H.df_rc; P->m_rc = H.m_rc; P->dm_rc = H.dm_rc;
+    P->shifted = p->shifted; P->tabulated = p->tabulated;
+    P->r_min = p->r_min;
+    int nf = (int)ceil((p->rc - p->r_min) / p->h - 1e-9);
+    int nm = (int)ceil((p->rc_morse - p->r_min) / p->h - 1e-9);
+    if (nf < 1) nf = 1;
+    if (nm < 1) nm = 1;
+    if (nf > (1 << 24) || nm > (1 << 24)) { snprintf(err, errlen, "md_params: table spacing h too small"); return MD_ERR_ARG; }
+    P->nf = nf; P->nm = nm;
+    P->inv_hf = nf / (p->rc - p->r_min);
+    P->inv_hm = nm / (p->rc_morse - p->r_min);
+    *d_tabs64 = nullptr; *d_tabs32 = nullptr;
+    std::vector<Cf64> tf, tp, tm;
+    fill_table(nf, p->r_min, p->rc, [&](double r, double &v, double &dv) { H.f(r, v, dv); }, tf);
+    fill_table(nf, p->r_min, p->rc, [&](double r, double &v, double &dv) { H.phi(r, v, dv); }, tp);
+    fill_table(nm, p->r_min, p->rc_morse, [&](double r, double &v, double &dv) { H.morse(r, v, dv); }, tm);
+    size_t ntot = (size_t)2 * nf + nm;
+    std::vector<Cf64> all;
+    all.reserve(ntot);
+    all.insert(all.end(), tf.begin(), tf.end());
+    all.insert(all.end(), tp.begin(), tp.end());
+    all.insert(all.end(), tm.begin(), tm.end());
+    std::vector<float4> all32(ntot);
+    for (size_t k = 0; k < ntot; ++k)
+        all32[k] = make_float4((float)all[k].x, (float)all[k].y, (float)all[k].z, (float)all[k].w);
+    if (cudaMalloc(d_tabs64, ntot * sizeof(Cf64)) != cudaSuccess ||
+        cudaMalloc(d_tabs32, ntot * sizeof(float4)) != cudaSuccess) {
+        snprintf(err, errlen, "cudaMalloc of potential tables failed");
+        if (*d_tabs64) cudaFree(*d_tabs64);
+        *d_tabs64 = nullptr;
+        return MD_ERR_CUDA;
+    }
+    if (cudaMemcpy(*d_tabs64, all.data(), ntot * sizeof(Cf64), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(*d_tabs32, all32.data(), ntot * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess) {
+        snprintf(err, errlen, "copy of potential tables failed");
+        return MD_ERR_CUDA;
+    }
+    P->tf = *d_tabs64; P->tp = *d_tabs64 + nf; P->tm = *d_tabs64 + 2 * nf;
+    P->tf32 = *d_tabs32; P->tp32 = *d_tabs32 + nf; P->tm32 = *d_tabs32 + 2 * nf;
+    return MD_OK;
+}
+
+// ============================================================================ device helpers
+
+namespace {
+
+__device__ __forceinline__ int pack_cell(int c0, int c1, int c2)
+{
+    return c0 | (c1 << MD_CELL_BITS) | (c2 << (2 * MD_CELL_BITS));
+}
+__device__ __forceinline__ int cell_x(int p) { return p & ((1 << MD_CELL_BITS) - 1); }
+__device__ __forceinline__ int cell_y(int p) { return (p >> MD_CELL_BITS) & ((1 << MD_CELL_BITS) - 1); }
+__device__ __forceinline__ int cell_z(int p) { return (p >> (2 * MD_CELL_BITS)) & ((1 << MD_CELL_BITS) - 1); }
+
+// ---- exact FP64 geometry of the list build and the skin test: every operation is a
+// separately rounded IEEE operation (no FMA contraction), so cell keys and neighbour
+// sets are reproducible on any IEEE machine from the same positions.
+__device__ __forceinline__ double wrap_exact(double x, double lo, double L)
+{
+    double m = floor(__ddiv_rn(__dsub_rn(x, lo), L));
+    return __dsub_rn(x, __dmul_rn(m, L));
+}
+__device__ __forceinline__ int cell_exact(double x, double lo, double w, int n)
+{
+    double t = floor(__ddiv_rn(__dsub_rn(x, lo), w));
+    if (!(t >= 0.0)) return 0;
+    if (t > (double)(n - 1)) return n - 1;
+    return (int)t;
+}
+__device__ __forceinline__ double mi_exact(double d, int per, double L)
+{
+    if (per) {
+        double half = 0.5 * L;
+        if (d > half) d = __dsub_rn(d, L);
+        else if (d < -half) d = __dadd_rn(d, L);
+    }
+    return d;
+}
+__device__ __forceinline__ double norm2_exact(double dx, double dy, double dz)
+{
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// ---- potential, FP64
+__device__ __forceinline__ void cubic64(const Cf64 *T, int n, double s, double inv_h, double &v, double &dv)
+{
+    double kf = fmin(fmax(floor(s), 0.0), (double)(n - 1));
+    double t = s - kf;
+    Cf64 c = T[(int)kf];
+    v = fma(fma(fma(c.w, t, c.z), t, c.y), t, c.x);
+    dv = fma(fma(3.0 * c.w, t, 2.0 * c.z), t, c.y) * inv_h;
+}
+__device__ __forceinline__ void f_64(const PotDev &P, double r, double &v, double &dv)
+{
+    if (P.tabulated) { cubic64(P.tf, P.nf, (r - P.r_min) * P.inv_hf, P.inv_hf, v, dv); return; }
+    double fr = exp2(P.lf0 - P.beta * log2(r));
+    v = fr - P.f_rc - (r - P.rc) * P.df_rc;
+    dv = -P.beta * fr / r - P.df_rc;
+}
+__device__ __forceinline__ void phi_64(const PotDev &P, double r, double &v, double &dv)
+{
+    if (P.tabulated) { cubic64(P.tp, P.nf, (r - P.r_min) * P.inv_hf, P.inv_hf, v, dv); return; }
+    double t = r / P.r_e - P.d;
+    if (t > 0.0) { v = dv = 0.0; return; }
+    v = t * t * fma(fma(fma(P.b[3], t, P.b[2]), t, P.b[1]), t, P.b[0]);
+    dv = t * fma(fma(fma(5.0 * P.b[3], t, 4.0 * P.b[2]), t, 3.0 * P.b[1]), t, 2.0 * P.b[0]) / P.r_e;
+}
+__device__ __forceinline__ void morse_64(const PotDev &P, double y, double &v, double &dv)
+{
+    if (P.tabulated) { cubic64(P.tm, P.nm, (y - P.r_min) * P.inv_hm, P.inv_hm, v, dv); return; }
+    double E = exp(-P.half_ax * (y * P.inv_yeq - 1.0));
+    v = P.D_o * E * (E - 2.0) - P.m_rc - (y - P.rc_m) * P.dm_rc;
+    dv = -2.0 * P.D_o * P.half_ax * P.inv_yeq * E * (E - 1.0) - P.dm_rc;
+}
+// Eq. A3: F and F' (F' = F_o n^2 s^n ln s / rho), M and M' (M' = (2 alpha/P_e) u (1-u^2) e^{-u^2})
+__device__ __forceinline__ void embed_64(const PotDev &P, double rho, double &F, double &Fp)
+{
+    if (!(rho > 0.0)) { F = Fp = 0.0; return; }
+    double L = log(rho / P.rho_e);
+    double sn = exp(P.n * L);
+    F = -P.F_o * (1.0 - P.n * L) * sn;
+    Fp = P.F_o * P.n * P.n * sn * L / rho;
+}
+__device__ __forceinline__ void mterm_64(const PotDev &P, double Ps, double &M, double &Mp)
+{
+    if (!(Ps > 0.0)) { M = Mp = 0.0; return; }
+    double u = Ps / P.P_e - 1.0;
+    double e = exp(-u * u);
+    M = P.alpha * u * u * e;
+    Mp = 2.0 * P.alpha / P.P_e * u * (1.0 - u * u) * e;
+}
+
+// ---- potential, FP32 (mixed precision)
+__device__ __forceinline__ void cubic32(const float4 *T, int n, float s, float inv_h, float &v, float &dv)
+{
+    float kf = fminf(fmaxf(floorf(s), 0.0f), (float)(n - 1));
+    float t = s - kf;
+    float4 c = __ldg(&T[(int)kf]);
+    v = fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
+    dv = fmaf(fmaf(3.0f * c.w, t, 2.0f * c.z), t, c.y) * inv_h;
+}
+
+struct Pot32 {   // FP32 constants, derived once per thread from PotDev
+    float rmin_s_f, inv_hf, rmin_s_m, inv_hm, lf0, beta, f_rc, df_rc, rc;
+    float inv_re, d, b0, b1, b2, b3;
+    float D_o, half_ax, inv_yeq, m_rc, dm_rc, rc_m;
+    float F_o, n, inv_rho_e, alpha, inv_P_e, rc2;
+    int tabulated, nf, nm;
+    const float4 *tf, *tp, *tm;
+    __device__ __forceinline__ void init(const PotDev &P)
+    {
+        inv_hf = (float)P.inv_hf; rmin_s_f = (float)(P.r_min * P.inv_hf);
+        inv_hm = (float)P.inv_hm; rmin_s_m = (float)(P.r_min * P.inv_hm);
+        lf0 = (float)P.lf0; beta = (float)P.beta; f_rc = (float)P.f_rc; df_rc = (float)P.df_rc; rc = (float)P.rc;
+        inv_re = (float)(1.0 / P.r_e); d = (float)P.d;
+        b0 = (float)P.b[0]; b1 = (float)P.b[1]; b2 = (float)P.b[2]; b3 = (float)P.b[3];
+        D_o = (float)P.D_o; half_ax = (float)P.half_ax; inv_yeq = (float)P.inv_yeq;
+        m_rc = (float)P.m_rc; dm_rc = (float)P.dm_rc; rc_m = (float)P.rc_m;
+        F_o = (float)P.F_o; n = (float)P.n; inv_rho_e = (float)(1.0 / P.rho_e); alpha = (float)P.alpha;
+        inv_P_e = (float)(1.0 / P.P_e); rc2 = (float)P.rc2;
+        tabulated = P.tabulated; nf = P.nf; nm = P.nm; tf = P.tf32; tp = P.tp32; tm = P.tm32;
+    }
+    __device__ __forceinline__ void f(float r, float &v, float &dv) const
+    {
+        if (tabulated) { cubic32(tf, nf, fmaf(r, inv_hf, -rmin_s_f), inv_hf, v, dv); return; }
+        float fr = exp2f(lf0 - beta * __log2f(r));
+        v = fr - f_rc - (r - rc) * df_rc;
+        dv = -beta * fr / r - df_rc;
+    }
+    __device__ __forceinline__ void phi(float r, float &v, float &dv) const
+    {
+        if (tabulated) { cubic32(tp, nf, fmaf(r, inv_hf, -rmin_s_f), inv_hf, v, dv); return; }
+        float t = fmaf(r, inv_re, -d);
+        if (t > 0.0f) { v = dv = 0.0f; return; }
+        v = t * t * fmaf(fmaf(fmaf(b3, t, b2), t, b1), t, b0);
+        dv = t * fmaf(fmaf(fmaf(5.0f * b3, t, 4.0f * b2), t, 3.0f * b1), t, 2.0f * b0) * inv_re;
+    }
+    __device__ __forceinline__ void morse(float y, float &v, float &dv) const
+    {
+        if (tabulated) { cubic32(tm, nm, fmaf(y, inv_hm, -rmin_s_m), inv_hm, v, dv); return; }
+        float E = expf(-half_ax * fmaf(y, inv_yeq, -1.0f));
+        v = D_o * E * (E - 2.0f) - m_rc - (y - rc_m) * dm_rc;
+        dv = -2.0f * D_o * half_ax * inv_yeq * E * (E - 1.0f) - dm_rc;
+    }
+    __device__ __forceinline__ void embed(float rho, float &F, float &Fp) const
+    {
+        if (!(rho > 0.0f)) { F = Fp = 0.0f; return; }
+        float L = logf(rho * inv_rho_e);
+        float sn = expf(n * L);
+        F = -F_o * (1.0f - n * L) * sn;
+        Fp = F_o * n * n * sn * L / rho;
+    }
+    __device__ __forceinline__ void mterm(float Ps, float &M, float &Mp) const
+    {
+        if (!(Ps > 0.0f)) { M = Mp = 0.0f; return; }
+        float u = fmaf(Ps, inv_P_e, -1.0f);
+        float e = expf(-u * u);
+        M = alpha * u * u * e;
+        Mp = 2.0f * alpha * inv_P_e * u * (1.0f - u * u) * e;
+    }
+};
+
+// per-thread copy of the replica fields the pair kernels use
+struct RepPair {
+    int per0, per1, per2, n0, n1, n2;
+    float w0, w1, w2;
+    double L0, L1, L2;
+    int slot_off, n_atoms;
+    __device__ __forceinline__ void load(const RepDev &R)
+    {
+        per0 = R.per[0]; per1 = R.per[1]; per2 = R.per[2];
+        n0 = R.nc[0]; n1 = R.nc[1]; n2 = R.nc[2];
+        w0 = R.w32[0]; w1 = R.w32[1]; w2 = R.w32[2];
+        L0 = R.L[0]; L1 = R.L[1]; L2 = R.L[2];
+        slot_off = R.slot_off; n_atoms = R.n_atoms;
+    }
+};
+
+__device__ __forceinline__ int wrap_shift(int s, int per, int n)
+{
+    if (per) {
+        if (s > 1) s -= n;
+        else if (s < -1) s += n;
+    }
+    return s;
+}
+
+// displacement x_j - x_i from cell-relative FP32 positions: the cell-centre offset of the
+// two cells is a whole number of cell widths (periodic wrap included), added in FP32
+__device__ __forceinline__ void rel_disp(const float4 &pi, int ci, const float4 &pj, const RepPair &R,
+                                         float &dx, float &dy, float &dz)
+{
+    int cj = __float_as_int(pj.w);
+    int sx = wrap_shift(cell_x(cj) - cell_x(ci), R.per0, R.n0);
+    int sy = wrap_shift(cell_y(cj) - cell_y(ci), R.per1, R.n1);
+    int sz = wrap_shift(cell_z(cj) - cell_z(ci), R.per2, R.n2);
+    dx = fmaf((float)sx, R.w0, pj.x - pi.x);
+    dy = fmaf((float)sy, R.w1, pj.y - pi.y);
+    dz = fmaf((float)sz, R.w2, pj.z - pi.z);
+}
+
+__device__ __forceinline__ double mi64(double d, int per, double L)
+{
+    if (per) {
+        double half = 0.5 * L;
+        if (d > half) d -= L;
+        else if (d < -half) d += L;
+    }
+    return d;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// CTA sum of up to 4 doubles; thread 0 writes part[t * stride + blk]
+template <int NV>
+__device__ __forceinline__ void cta_partials(double (&v)[NV], double *part, int stride, int blk)
+{
+    __shared__ double sm[32][4];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) v[t] = warp_sum(v[t]);
+    if (lane == 0) {
+#pragma unroll
+        for (int t = 0; t < NV; ++t) sm[wid][t] = v[t];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            double acc = 0.0;
+            for (int w = 0; w < nw; ++w) acc += sm[w][t];
+            part[t * stride + blk] = acc;
+        }
+    }
+}
+
+// ============================================================================ Task 1: skin test
+
+__global__ void __launch_bounds__(MD_TILE) k_skin(DevArgs a)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    int r = a.tile_rep[blockIdx.x];   // blockDim == MD_TILE
+    const RepDev &R = a.rep[r];
+    double d2 = 0.0;
+    if (s - R.slot_off < R.n_atoms) {
+        double dx = __dsub_rn(a.x[s], a.xb[s]);
+        double dy = __dsub_rn(a.x[(size_t)a.S + s], a.xb[(size_t)a.S + s]);
+        double dz = __dsub_rn(a.x[2 * (size_t)a.S + s], a.xb[2 * (size_t)a.S + s]);
+        d2 = norm2_exact(dx, dy, dz);
+        if (d2 != d2) d2 = 1e300;   // NaN position: force a rebuild, which reports it
+    }
+    for (int o = 16; o > 0; o >>= 1) d2 = fmax(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+    __shared__ double sm[MD_TILE / 32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = d2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sm[w]);
+        if (m > 0.0) atomicMax(&a.rs[r].d2max_bits, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+__global__ void k_decide(DevArgs a, int force, int use_cond, cudaGraphConditionalHandle h)
+{
+    int any = 0;
+    for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) {
+        RepState &S = a.rs[r];
+        double dmax = sqrt(__longlong_as_double((long long)S.d2max_bits));
+        S.d2max_bits = 0ull;
+        int need;
+        if (a.rebuild_every > 0) {
+            need = a.st->since_build >= a.rebuild_every;
+            if (!need && 2.0 * dmax > a.skin) atomicOr(&a.st->err, MDE_SKIN);
+        } else {
+            need = (2.0 * dmax > a.skin) ||
+                   (a.rep[r].n_c > 0 && __dadd_rn(dmax, fabs(__dsub_rn(S.z_ind, S.z_build))) > a.skin);
+        }
+        if (force) need = 1;
+        S.need = need;
+        any |= need;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        a.st->any_rebuild = any;
+        if (use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
+    }
+}
+
+// ============================================================================ Task 1: rebuild
+
+__global__ void k_zero_i32(int32_t *p, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 0;
+}
+
+// wrap into the periodic box, FP64 cell coordinates, cell key, histogram
+__global__ void k_bin(DevArgs a)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s == 0) { a.st->max_cnt = 0; a.st->max_cntc = 0; }
+    if (s >= a.S) return;
+    int r = a.tile_rep[s / MD_TILE];
+    const RepDev &R = a.rep[r];
+    if (s - R.slot_off >= R.n_atoms) return;
+    int c[3];
+    bool lost = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double xk = a.x[(size_t)k * a.S + s];
+        if (xk != xk) lost = true;
+        if (R.per[k]) {
+            xk = wrap_exact(xk, R.lo[k], R.L[k]);
+            a.x[(size_t)k * a.S + s] = xk;
+        } else if (xk < R.lo[k] || xk > R.hi[k]) {
+            lost = true;
+        }
+        c[k] = cell_exact(xk, R.lo[k], R.w[k], R.nc[k]);
+    }
+    if (lost) atomicOr(&a.st->err, MDE_LOST);
+    int key = R.cell_off + (c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0];
+    a.key[s] = key;
+    atomicAdd(&a.cell_count[key], 1);
+}
+
+// exclusive scan, phase 1: per-CTA scan of 2 * blockDim elements, CTA totals to blk
+__global__ void k_scan1(const int32_t *in, int32_t *out, int32_t *blk, int n)
+{
+    extern __shared__ int32_t sh[];
+    int t = threadIdx.x, base = blockIdx.x * 2 * blockDim.x;
+    int i0 = base + 2 * t, i1 = i0 + 1;
+    int v0 = i0 < n ? in[i0] : 0, v1 = i1 < n ? in[i1] : 0;
+    sh[t] = v0 + v1;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {   // Hillis-Steele inclusive scan of pair sums
+        int add = t >= off ? sh[t - off] : 0;
+        __syncthreads();
+        sh[t] += add;
+        __syncthreads();
+    }
+    int excl = sh[t] - (v0 + v1);
+    if (i0 < n) out[i0] = excl;
+    if (i1 < n) out[i1] = excl + v0;
+    if (t == blockDim.x - 1) blk[blockIdx.x] = sh[t];
+}
+
+// phase 2: one CTA scans the CTA totals (any count; chunks of blockDim)
+__global__ void k_scan2(int32_t *blk, int nb)
+{
+    extern __shared__ int32_t sh[];
+    int t = threadIdx.x;
+    int carry = 0;
+    for (int base = 0; base < nb; base += blockDim.x) {
+        int i = base + t;
+        int v = i < nb ? blk[i] : 0;
+        sh[t] = v;
+        __syncthreads();
+        for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+            int add = t >= off ? sh[t - off] : 0;
+            __syncthreads();
+            sh[t] += add;
+            __syncthreads();
+        }
+        if (i < nb) blk[i] = carry + sh[t] - v;
+        int tot = sh[blockDim.x - 1];
+        __syncthreads();
+        carry += tot;
+    }
+}
+
+// phase 3: add CTA offsets and move each replica's cells to its TILE-aligned slot range
+__global__ void k_scan3(DevArgs a, int per_block)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.total_cells) return;
+    const RepDev &R = a.rep[a.cell_rep[c]];
+    a.cell_start[c] += a.scan_blk[c / per_block] + (R.slot_off - R.real_off);
+}
+
+__global__ void k_scatter(DevArgs a)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.S) return;
+    const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
+    if (s - R.slot_off >= R.n_atoms) return;
+    int key = a.key[s];
+    int k = atomicAdd(&a.cell_fill[key], 1);
+    a.perm[a.cell_start[key] + k] = s;
+}
+
+// deterministic order within a cell: ascending caller id (insertion sort, ~10 atoms)
+__global__ void k_cellsort(DevArgs a)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.total_cells) return;
+    int b = a.cell_start[c], n = a.cell_count[c];
+    for (int i = 1; i < n; ++i) {
+        int p = a.perm[b + i];
+        int key = a.orig[p];
+        int j = i - 1;
+        while (j >= 0 && a.orig[a.perm[b + j]] > key) { a.perm[b + j + 1] = a.perm[b + j]; --j; }
+        a.perm[b + j + 1] = p;
+    }
+}
+
+__global__ void k_gather(DevArgs a)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.S) return;
+    const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
+    if (s - R.slot_off >= R.n_atoms) return;
+    int o = a.perm[s];
+    size_t S = a.S;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        a.sx[k * S + s] = a.x[k * S + o];
+        a.sv[k * S + s] = a.v[k * S + o];
+        a.sF[k * S + s] = a.F[k * S + o];
+    }
+    a.sorig[s] = a.orig[o];
+    a.sfixed[s] = a.fixed[o];
+    int loc = a.key[o] - R.cell_off;
+    int c0 = loc % R.nc[0], c1 = (loc / R.nc[0]) % R.nc[1], c2 = loc / (R.nc[0] * R.nc[1]);
+    a.cellc[s] = pack_cell(c0, c1, c2);
+}
+
+__device__ __forceinline__ float4 rel_pos(const DevArgs &a, const RepDev &R, int s)
+{
+    int pc = a.cellc[s];
+    size_t S = a.S;
+    double c0 = R.lo[0] + (cell_x(pc) + 0.5) * R.w[0];
+    double c1 = R.lo[1] + (cell_y(pc) + 0.5) * R.w[1];
+    double c2 = R.lo[2] + (cell_z(pc) + 0.5) * R.w[2];
+    return make_float4((float)(a.x[s] - c0), (float)(a.x[S + s] - c1), (float)(a.x[2 * S + s] - c2), __int_as_float(pc));
+}
+
+__global__ void k_copyback(DevArgs a)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.S) return;
+    const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
+    if (s - R.slot_off >= R.n_atoms) return;
+    size_t S = a.S;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double xk = a.sx[k * S + s];
+        a.x[k * S + s] = xk;
+        a.xb[k * S + s] = xk;
+        a.v[k * S + s] = a.sv[k * S + s];
+        a.F[k * S + s] = a.sF[k * S + s];
+    }
+    a.orig[s] = a.sorig[s];
+    a.fixed[s] = a.sfixed[s];
+    if (a.mixed) a.pos4[s] = rel_pos(a, R, s);
+}
+
+// full Cr-Cr Verlet list: every slot j != i in the 27-cell stencil with |x_j - x_i|^2 < (rc + skin)^2
+__global__ void __launch_bounds__(128) k_nbr(DevArgs a)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.S) return;
+    const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
+    if (s - R.slot_off >= R.n_atoms) return;
+    size_t S = a.S;
+    double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
+    int pc = a.cellc[s];
+    int c0 = cell_x(pc), c1 = cell_y(pc), c2 = cell_z(pc);
+    int m = 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+        int q2 = c2 + dz;
+        if (q2 < 0 || q2 >= R.nc[2]) { if (!R.per[2]) continue; q2 = (q2 + R.nc[2]) % R.nc[2]; }
+        for (int dy = -1; dy <= 1; ++dy) {
+            int q1 = c1 + dy;
+            if (q1 < 0 || q1 >= R.nc[1]) { if (!R.per[1]) continue; q1 = (q1 + R.nc[1]) % R.nc[1]; }
+            for (int dx = -1; dx <= 1; ++dx) {
+                int q0 = c0 + dx;
+                if (q0 < 0 || q0 >= R.nc[0]) { if (!R.per[0]) continue; q0 = (q0 + R.nc[0]) % R.nc[0]; }
+                int key = R.cell_off + (q2 * R.nc[1] + q1) * R.nc[0] + q0;
+                int b = a.cell_start[key], e = b + a.cell_count[key];
+                for (int t = b; t < e; ++t) {
+                    if (t == s) continue;
+                    double ddx = mi_exact(__dsub_rn(a.x[t], xi), R.per[0], R.L[0]);
+                    double ddy = mi_exact(__dsub_rn(a.x[S + t], yi), R.per[1], R.L[1]);
+                    double ddz = mi_exact(__dsub_rn(a.x[2 * S + t], zi), R.per[2], R.L[2]);
+                    if (norm2_exact(ddx, ddy, ddz) < a.cut2) {
+                        if (m < a.kmax) a.nbr[(size_t)m * S + s] = t;
+                        ++m;
+                    }
+                }
+            }
+        }
+    }
+    a.cnt[s] = m < a.kmax ? m : a.kmax;
+    if (m > a.kmax) atomicOr(&a.st->err, MDE_OVERFLOW);
+    atomicMax(&a.st->max_cnt, m);
+}
+
+// Cr-C list through the indenter's own cell grid (indenter frame = positions at z_ind = 0)
+__global__ void __launch_bounds__(128) k_nbrc(DevArgs a)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.S) return;
+    int r = a.tile_rep[s / MD_TILE];
+    const RepDev &R = a.rep[r];
+    if (s - R.slot_off >= R.n_atoms) return;
+    if (R.n_c == 0) { a.cntc[s] = 0; return; }
+    size_t S = a.S, C = a.C;
+    double z_ind = a.rs[r].z_ind;
+    double xi[3] = {a.x[s], a.x[S + s], a.x[2 * S + s]};
+    if (!(isfinite(xi[0]) && isfinite(xi[1]) && isfinite(xi[2]))) { a.cntc[s] = 0; return; }   // reported by k_bin
+    int lo[3], hi[3];
+    double reach = a.cutc * (1.0 + 1e-9) + 1e-9;
+    for (int k = 0; k < 3; ++k) {
+        double q = xi[k] - (k == 2 ? z_ind : 0.0);
+        double ctr = R.cg_lo[k] + 0.5 * R.cg_n[k] * R.cg_w[k];
+        q = ctr + mi64(q - ctr, R.per[k], R.L[k]);
+        double tl = floor((q - reach - R.cg_lo[k]) / R.cg_w[k]);
+        double th = floor((q + reach - R.cg_lo[k]) / R.cg_w[k]);
+        if (th < 0.0 || tl > (double)(R.cg_n[k] - 1)) { a.cntc[s] = 0; return; }
+        lo[k] = tl < 0.0 ? 0 : (int)tl;
+        hi[k] = th > (double)(R.cg_n[k] - 1) ? R.cg_n[k] - 1 : (int)th;
+    }
+    int m = 0;
+    for (int q2 = lo[2]; q2 <= hi[2]; ++q2)
+        for (int q1 = lo[1]; q1 <= hi[1]; ++q1)
+            for (int q0 = lo[0]; q0 <= hi[0]; ++q0) {
+                int key = R.ccell_off + (q2 * R.cg_n[1] + q1) * R.cg_n[0] + q0;
+                int b = a.ccell_start[key], e = b + a.ccell_count[key];
+                for (int c = b; c < e; ++c) {
+                    double ddx = mi_exact(__dsub_rn(a.xc0[c], xi[0]), R.per[0], R.L[0]);
+                    double ddy = mi_exact(__dsub_rn(a.xc0[C + c], xi[1]), R.per[1], R.L[1]);
+                    double zc = __dadd_rn(a.xc0[2 * C + c], z_ind);
+                    double ddz = mi_exact(__dsub_rn(zc, xi[2]), R.per[2], R.L[2]);
+                    if (norm2_exact(ddx, ddy, ddz) < a.cutc2) {
+                        if (m < a.kcmax) a.nbrc[(size_t)m * S + s] = c;
+                        ++m;
+                    }
+                }
+            }
+    a.cntc[s] = m < a.kcmax ? m : a.kcmax;
+    if (m > a.kcmax) atomicOr(&a.st->err, MDE_COVERFLOW);
+    atomicMax(&a.st->max_cntc, m);
+}
+
+__global__ void k_build_done(DevArgs a)
+{
+    for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) a.rs[r].z_build = a.rs[r].z_ind;
+    if (threadIdx.x == 0) { a.st->rebuilds += 1; a.st->since_build = 0; }
+}
+
+// ============================================================================ Tasks 2 + 3
+
+__global__ void k_verlet1(DevArgs a)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.S) return;
+    int r = a.tile_rep[s / MD_TILE];
+    const RepDev &R = a.rep[r];
+    if (s == R.slot_off) {   // Task 2: the rigid indenter moves by v_ind dt
+        RepState &st = a.rs[r];
+        st.z_ind = __dadd_rn(st.z_ind, __dmul_rn(R.v_ind, R.dt));
+    }
+    if (s - R.slot_off >= R.n_atoms) return;
+    size_t S = a.S;
+    if (!a.fixed[s]) {
+        double hk = 0.5 * R.dt * R.acc_per_f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double v = a.v[k * S + s] + hk * a.F[k * S + s];   // Eq. A12
+            a.v[k * S + s] = v;
+            a.x[k * S + s] += R.dt * v;                         // Eq. A11 with the half-step velocity
+        }
+    }
+    if (a.mixed) a.pos4[s] = rel_pos(a, R, s);
+}
+
+__global__ void k_refresh_pos4(DevArgs a)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.S) return;
+    const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
+    if (s - R.slot_off >= R.n_atoms) return;
+    a.pos4[s] = rel_pos(a, R, s);
+}
+
+// ============================================================================ Task 4a
+
+template <int TPA, bool MIXED>
+__global__ void __launch_bounds__(256) k_density(DevArgs a, PotDev P)
+{
+    const int A = blockDim.x / TPA;
+    const int g = threadIdx.x / TPA, lane = threadIdx.x % TPA;
+    const int s = blockIdx.x * A + g;
+    const int r = a.tile_rep[(blockIdx.x * A) / MD_TILE];
+    RepPair R;
+    R.load(a.rep[r]);
+    const bool real = s < a.S && (s - R.slot_off) < R.n_atoms;
+    double acc[2] = {0.0, 0.0};
+    const size_t S = a.S;
+    if (MIXED) {
+        Pot32 Q;
+        Q.init(P);
+        float rho = 0.f, Ps = 0.f;
+        if (real) {
+            const float4 pi = a.pos4[s];
+            const int ci = __float_as_int(pi.w);
+            const int n = a.cnt[s];
+            for (int k = lane; k < n; k += TPA) {
+                const int j = __ldg(&a.nbr[(size_t)k * S + s]);
+                const float4 pj = __ldg(&a.pos4[j]);
+                float dx, dy, dz;
+                rel_disp(pi, ci, pj, R, dx, dy, dz);
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (r2 < Q.rc2) {
+                    float f, df;
+                    Q.f(sqrtf(r2), f, df);
+                    rho += f;
+                    Ps = fmaf(f, f, Ps);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = TPA / 2; o > 0; o >>= 1) {
+            rho += __shfl_xor_sync(0xffffffffu, rho, o);
+            Ps += __shfl_xor_sync(0xffffffffu, Ps, o);
+        }
+        if (real && lane == 0) {
+            float F, Fp, M, Mp;
+            Q.embed(rho, F, Fp);
+            Q.mterm(Ps, M, Mp);
+            a.fm32[s] = make_float2(Fp, Mp);
+            acc[0] = F; acc[1] = M;
+        }
+    } else {
+        double rho = 0.0, Ps = 0.0;
+        if (real) {
+            const double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
+            const int n = a.cnt[s];
+            for (int k = lane; k < n; k += TPA) {
+                const int j = __ldg(&a.nbr[(size_t)k * S + s]);
+                const double dx = mi64(a.x[j] - xi, R.per0, R.L0);
+                const double dy = mi64(a.x[S + j] - yi, R.per1, R.L1);
+                const double dz = mi64(a.x[2 * S + j] - zi, R.per2, R.L2);
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < P.rc2) {
+                    double f, df;
+                    f_64(P, sqrt(r2), f, df);
+                    rho += f;
+                    Ps += f * f;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = TPA / 2; o > 0; o >>= 1) {
+            rho += __shfl_xor_sync(0xffffffffu, rho, o);
+            Ps += __shfl_xor_sync(0xffffffffu, Ps, o);
+        }
+        if (real && lane == 0) {
+            double F, Fp, M, Mp;
+            embed_64(P, rho, F, Fp);
+            mterm_64(P, Ps, M, Mp);
+            a.fm64[s] = make_double2(Fp, Mp);
+            acc[0] = F; acc[1] = M;
+        }
+    }
+    cta_partials<2>(acc, a.part, a.max_blocks, blockIdx.x);
+}
+
+// ============================================================================ Task 4b,c + Task 5
+
+template <int TPA, bool MIXED>
+__global__ void __launch_bounds__(256) k_force(DevArgs a, PotDev P, int integrate)
+{
+    const int A = blockDim.x / TPA;
+    const int g = threadIdx.x / TPA, lane = threadIdx.x % TPA;
+    const int s = blockIdx.x * A + g;
+    const int r = a.tile_rep[(blockIdx.x * A) / MD_TILE];
+    RepPair R;
+    R.load(a.rep[r]);
+    const bool real = s < a.S && (s - R.slot_off) < R.n_atoms;
+    const size_t S = a.S, C = a.C;
+    double fx = 0.0, fy = 0.0, fz = 0.0, e_pair = 0.0, e_mor = 0.0, load = 0.0;
+    if (MIXED) {
+        Pot32 Q;
+        Q.init(P);
+        float gx = 0.f, gy = 0.f, gz = 0.f, ep = 0.f;
+        if (real) {
+            const float4 pi = a.pos4[s];
+            const int ci = __float_as_int(pi.w);
+            const float2 fmi = a.fm32[s];
+            const int n = a.cnt[s];
+            for (int k = lane; k < n; k += TPA) {
+                const int j = __ldg(&a.nbr[(size_t)k * S + s]);
+                const float4 pj = __ldg(&a.pos4[j]);
+                float dx, dy, dz;
+                rel_disp(pi, ci, pj, R, dx, dy, dz);
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (r2 < Q.rc2) {
+                    const float2 fmj = __ldg(&a.fm32[j]);
+                    const float rinv = rsqrtf(r2);
+                    const float rr = r2 * rinv;
+                    float f, df, ph, dph;
+                    Q.f(rr, f, df);
+                    Q.phi(rr, ph, dph);
+                    // Eq. (1) with the M term: coef * (x_j - x_i)/r is the force on i
+                    const float coef = fmaf(fmi.x + fmj.x, df, fmaf((fmi.y + fmj.y) * 2.0f * f, df, dph)) * rinv;
+                    gx = fmaf(coef, dx, gx);
+                    gy = fmaf(coef, dy, gy);
+                    gz = fmaf(coef, dz, gz);
+                    ep = fmaf(0.5f, ph, ep);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = TPA / 2; o > 0; o >>= 1) {
+            gx += __shfl_xor_sync(0xffffffffu, gx, o);
+            gy += __shfl_xor_sync(0xffffffffu, gy, o);
+            gz += __shfl_xor_sync(0xffffffffu, gz, o);
+            ep += __shfl_xor_sync(0xffffffffu, ep, o);
+        }
+        fx = gx; fy = gy; fz = gz; e_pair = ep;
+        // Cr-C (Morse): FP64 geometry, FP32 potential
+        float mx = 0.f, my = 0.f, mz = 0.f, em = 0.f;
+        if (real) {
+            const int nc = a.cntc[s];
+            if (nc > 0) {
+                const double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
+                const double z_ind = a.rs[r].z_ind;
+                for (int k = lane; k < nc; k += TPA) {
+                    const int c = __ldg(&a.nbrc[(size_t)k * S + s]);
+                    const double ddx = mi64(a.xc0[c] - xi, R.per0, R.L0);
+                    const double ddy = mi64(a.xc0[C + c] - yi, R.per1, R.L1);
+                    const double ddz = mi64(a.xc0[2 * C + c] + z_ind - zi, R.per2, R.L2);
+                    const double y2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                    if (y2 < P.rcm2) {
+                        const float yinv = rsqrtf((float)y2);
+                        const float y = (float)y2 * yinv;
+                        float v, dv;
+                        Q.morse(y, v, dv);
+                        const float c1 = dv * yinv;
+                        mx = fmaf(c1, (float)ddx, mx);
+                        my = fmaf(c1, (float)ddy, my);
+                        mz = fmaf(c1, (float)ddz, mz);
+                        em += v;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int o = TPA / 2; o > 0; o >>= 1) {
+            mx += __shfl_xor_sync(0xffffffffu, mx, o);
+            my += __shfl_xor_sync(0xffffffffu, my, o);
+            mz += __shfl_xor_sync(0xffffffffu, mz, o);
+            em += __shfl_xor_sync(0xffffffffu, em, o);
+        }
+        fx += mx; fy += my; fz += mz; e_mor = em; load = -(double)mz;
+    } else {
+        double gx = 0.0, gy = 0.0, gz = 0.0, ep = 0.0;
+        double mx = 0.0, my = 0.0, mz = 0.0, em = 0.0;
+        if (real) {
+            const double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
+            const double2 fmi = a.fm64[s];
+            const int n = a.cnt[s];
+            for (int k = lane; k < n; k += TPA) {
+                const int j = __ldg(&a.nbr[(size_t)k * S + s]);
+                const double dx = mi64(a.x[j] - xi, R.per0, R.L0);
+                const double dy = mi64(a.x[S + j] - yi, R.per1, R.L1);
+                const double dz = mi64(a.x[2 * S + j] - zi, R.per2, R.L2);
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < P.rc2) {
+                    const double2 fmj = a.fm64[j];
+                    const double rr = sqrt(r2);
+                    double f, df, ph, dph;
+                    f_64(P, rr, f, df);
+                    phi_64(P, rr, ph, dph);
+                    const double coef = ((fmi.x + fmj.x) * df + (fmi.y + fmj.y) * 2.0 * f * df + dph) / rr;
+                    gx += coef * dx; gy += coef * dy; gz += coef * dz;
+                    ep += 0.5 * ph;
+                }
+            }
+            const int nc = a.cntc[s];
+            if (nc > 0) {
+                const double z_ind = a.rs[r].z_ind;
+                for (int k = lane; k < nc; k += TPA) {
+                    const int c = __ldg(&a.nbrc[(size_t)k * S + s]);
+                    const double ddx = mi64(a.xc0[c] - xi, R.per0, R.L0);
+                    const double ddy = mi64(a.xc0[C + c] - yi, R.per1, R.L1);
+                    const double ddz = mi64(a.xc0[2 * C + c] + z_ind - zi, R.per2, R.L2);
+                    const double y2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                    if (y2 < P.rcm2) {
+                        const double y = sqrt(y2);
+                        double v, dv;
+                        morse_64(P, y, v, dv);
+                        mx += dv * ddx / y; my += dv * ddy / y; mz += dv * ddz / y;
+                        em += v;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int o = TPA / 2; o > 0; o >>= 1) {
+            gx += __shfl_xor_sync(0xffffffffu, gx, o);
+            gy += __shfl_xor_sync(0xffffffffu, gy, o);
+            gz += __shfl_xor_sync(0xffffffffu, gz, o);
+            ep += __shfl_xor_sync(0xffffffffu, ep, o);
+            mx += __shfl_xor_sync(0xffffffffu, mx, o);
+            my += __shfl_xor_sync(0xffffffffu, my, o);
+            mz += __shfl_xor_sync(0xffffffffu, mz, o);
+            em += __shfl_xor_sync(0xffffffffu, em, o);
+        }
+        fx = gx + mx; fy = gy + my; fz = gz + mz; e_pair = ep; e_mor = em; load = -mz;
+    }
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (real && lane == 0) {
+        a.F[s] = fx; a.F[S + s] = fy; a.F[2 * S + s] = fz;
+        double vx = a.v[s], vy = a.v[S + s], vz = a.v[2 * S + s];
+        const RepDev &RD = a.rep[r];
+        if (integrate && !a.fixed[s]) {   // Task 5: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2
+            const double hk = 0.5 * RD.dt * RD.acc_per_f;
+            vx += hk * fx; vy += hk * fy; vz += hk * fz;
+            a.v[s] = vx; a.v[S + s] = vy; a.v[2 * S + s] = vz;
+        }
+        acc[0] = e_pair; acc[1] = e_mor; acc[2] = load;
+        acc[3] = 0.5 * RD.mass * (vx * vx + vy * vy + vz * vz) / MD_ACC;
+    }
+    cta_partials<4>(acc, a.part + 2 * (size_t)a.max_blocks, a.max_blocks, blockIdx.x);
+}
+
+// per-replica sums of the CTA partials, fixed order: thread t adds blocks t, t+B, ...;
+// then a fixed tree over threads
+__global__ void k_reduce(DevArgs a, int atoms_per_block, int advance)
+{
+    int r = blockIdx.x;
+    const RepDev &R = a.rep[r];
+    int b0 = R.slot_off / atoms_per_block, b1 = (R.slot_off + R.n_slots) / atoms_per_block;
+    __shared__ double sm[6][128];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x)
+        for (int t = 0; t < 6; ++t) acc[t] += a.part[(size_t)t * a.max_blocks + b];
+    for (int t = 0; t < 6; ++t) sm[t][threadIdx.x] = acc[t];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int t = 0; t < 6; ++t) sm[t][threadIdx.x] += sm[t][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        RepEnergy &E = a.en[r];
+        E.embed = sm[0][0]; E.mterm = sm[1][0]; E.pair = sm[2][0]; E.morse = sm[3][0];
+        E.load = sm[4][0]; E.kinetic = sm[5][0];
+        if (advance && r == 0) { a.st->step += 1; a.st->since_build += 1; }
+    }
+}
+
+inline unsigned nblk(long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+// ============================================================================ launchers
+
+cudaError_t launch_skin(const DevArgs &a, cudaStream_t s)
+{
+    k_skin<<<a.S / MD_TILE, MD_TILE, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decide(const DevArgs &a, int force, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s)
+{
+    k_decide<<<1, 256, 0, s>>>(a, force, use_cond, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s)
+{
+    const int B = 256;
+    k_zero_i32<<<nblk(a.total_cells, B), B, 0, s>>>(a.cell_count, a.total_cells);
+    k_zero_i32<<<nblk(a.total_cells, B), B, 0, s>>>(a.cell_fill, a.total_cells);
+    k_bin<<<nblk(a.S, B), B, 0, s>>>(a);
+    const int SB = 512, per_block = 2 * SB;
+    int nb = (int)nblk(a.total_cells, per_block);
+    k_scan1<<<nb, SB, SB * sizeof(int32_t), s>>>(a.cell_count, a.cell_start, a.scan_blk, a.total_cells);
+    k_scan2<<<1, 1024, 1024 * sizeof(int32_t), s>>>(a.scan_blk, nb);
+    k_scan3<<<nblk(a.total_cells, B), B, 0, s>>>(a, per_block);
+    k_scatter<<<nblk(a.S, B), B, 0, s>>>(a);
+    k_cellsort<<<nblk(a.total_cells, B), B, 0, s>>>(a);
+    k_gather<<<nblk(a.S, B), B, 0, s>>>(a);
+    k_copyback<<<nblk(a.S, B), B, 0, s>>>(a);
+    k_nbr<<<nblk(a.S, 128), 128, 0, s>>>(a);
+    k_nbrc<<<nblk(a.S, 128), 128, 0, s>>>(a);
+    k_build_done<<<1, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s)
+{
+    k_verlet1<<<nblk(a.S, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refresh_pos4(const DevArgs &a, cudaStream_t s)
+{
+    k_refresh_pos4<<<nblk(a.S, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int TPA>
+static void dens_t(const DevArgs &a, const PotDev &p, int block, cudaStream_t s)
+{
+    int A = block / TPA;
+    if (a.mixed) k_density<TPA, true><<<a.S / A, block, 0, s>>>(a, p);
+    else k_density<TPA, false><<<a.S / A, block, 0, s>>>(a, p);
+}
+
+template <int TPA>
+static void force_t(const DevArgs &a, const PotDev &p, int block, int integ, cudaStream_t s)
+{
+    int A = block / TPA;
+    if (a.mixed) k_force<TPA, true><<<a.S / A, block, 0, s>>>(a, p, integ);
+    else k_force<TPA, false><<<a.S / A, block, 0, s>>>(a, p, integ);
+}
+
+cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c, cudaStream_t s)
+{
+    switch (c.tpa) {
+    case 1: dens_t<1>(a, p, c.block, s); break;
+    case 2: dens_t<2>(a, p, c.block, s); break;
+    case 4: dens_t<4>(a, p, c.block, s); break;
+    default: dens_t<8>(a, p, c.block, s); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, cudaStream_t s)
+{
+    switch (c.tpa) {
+    case 1: force_t<1>(a, p, c.block, integrate, s); break;
+    case 2: force_t<2>(a, p, c.block, integrate, s); break;
+    case 4: force_t<4>(a, p, c.block, integrate, s); break;
+    default: force_t<8>(a, p, c.block, integrate, s); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, int advance, cudaStream_t s)
+{
+    k_reduce<<<a.n_rep, 128, 0, s>>>(a, c.block / c.tpa, advance);
+    return cudaGetLastError();
+}

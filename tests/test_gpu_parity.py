@@ -1,0 +1,278 @@
+"""CUDA path (through the C ABI) against the FP64 CPU oracle, element by element.
+
+Bars: cell coordinates and neighbour sets built in FP64 bit-exact (pairs within 1e-12 A of
+the list cut-off excluded); per-atom forces within 1e-12 (FP64 mode) and 1e-5 (mixed mode)
+of the metric ||dF_i|| / max(||F_i||, F_rms); energies likewise.
+"""
+import numpy as np
+import pytest
+
+import md_inputs as mi
+import oracle
+from gpu_helpers import compare_sets, jitter, min_image_r, rel_force_err, tiny
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def md():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1507_07068_gb300 import md as mdmod
+    mdmod.lib()
+    return mdmod
+
+
+def oracle_eval(params, rep, z_ind=0.0, **ov):
+    pot = oracle.Potential(params, **ov)
+    xc = rep.x_c + np.array([0.0, 0.0, z_ind]) if rep.n_c else None
+    return oracle.forces(pot, rep.x_cr, rep.box_lo, rep.box_hi, rep.periodic, xc)
+
+
+def energy_close(e, o, rtol, atol):
+    for k in ("embed", "pair", "mterm", "morse", "load"):
+        assert e[k] == pytest.approx(o[k], rel=rtol, abs=atol), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cells_and_lists_bit_exact(md, params, precision):
+    rep = tiny(amp=0.12, gap=1.0)
+    skin = 0.3
+    sim = md.MD([rep], params, precision=precision, skin=skin)
+    cut = params["rc"] + skin
+    cell, cnt, nbr = sim.neighbors(0, 0)
+    ocell = oracle.cell_coords(rep.x_cr, rep.box_lo, rep.box_hi, rep.periodic, cut)
+    assert np.array_equal(cell, ocell)
+    off, idx = oracle.neighbors(rep.x_cr, rep.box_lo, rep.box_hi, rep.periodic, cut, method=0)
+    near = lambda i, j: abs(min_image_r(rep.x_cr, i, j, rep.box_lo, rep.box_hi, rep.periodic) - cut) < 1e-12
+    assert compare_sets(cnt, nbr, off, idx, near) == []
+    assert cnt.sum() == off[-1]
+    # Cr-C list
+    cutc = params["rc_m"] + skin
+    _, cntc, nbrc = sim.neighbors(0, 1)
+    offc, idxc = oracle.cneighbors(rep.x_cr, rep.x_c, rep.box_lo, rep.box_hi, rep.periodic, cutc)
+    assert offc[-1] > 0
+    assert compare_sets(cntc, nbrc, offc, idxc, lambda i, j: False) == []
+    sim.close()
+
+
+@pytest.mark.parametrize("tab,shifted", [(1, 1), (0, 1), (1, 0), (0, 0)])
+def test_forces_fp64(md, params, tab, shifted):
+    rep = tiny(amp=0.12, gap=1.0)
+    sim = md.MD([rep], params, precision="fp64", tabulated=tab, shifted=shifted)
+    F = sim.forces(0)
+    e = sim.energy(0)
+    o = oracle_eval(params, rep, tabulated=tab, shifted=shifted)
+    err = rel_force_err(F, o["F"])
+    assert err.max() <= FP64_TOL, err.max()
+    energy_close(e, o, 1e-12, 1e-10)
+    sim.close()
+
+
+@pytest.mark.parametrize("tab", [1, 0])
+def test_forces_mixed(md, params, tab):
+    rep = tiny(amp=0.12, gap=1.0)
+    sim = md.MD([rep], params, precision="mixed", tabulated=tab)
+    F = sim.forces(0)
+    e = sim.energy(0)
+    o = oracle_eval(params, rep, tabulated=tab)
+    err = rel_force_err(F, o["F"])
+    assert err.max() <= MIXED_TOL, err.max()
+    energy_close(e, o, 1e-5, 1e-4)
+    sim.close()
+
+
+@pytest.mark.parametrize("tpa,block", [(1, 128), (2, 256), (4, 128), (8, 256), (8, 64)])
+def test_launch_shapes_agree(md, params, tpa, block):
+    rep = tiny(amp=0.1)
+    o = oracle_eval(params, rep)
+    for prec, tol in (("fp64", FP64_TOL), ("mixed", MIXED_TOL)):
+        sim = md.MD([rep], params, precision=prec, tpa=tpa, block=block)
+        assert rel_force_err(sim.forces(0), o["F"]).max() <= tol
+        sim.close()
+
+
+def test_trajectory_fp64_fixed_rebuilds(md, params):
+    rep = tiny(amp=0.05, gap=1.0, T=400.0)
+    sim = md.MD([rep], params, precision="fp64", rebuild_every=7)
+    osim = oracle.Sim(oracle.Potential(params), rep, skin=0.3, rebuild_every=7)
+    for chunk in (1, 9, 40):
+        sim.step(chunk)
+        osim.step(chunk)
+        x, v, z, step = sim.state(0)
+        o = osim.state()
+        assert step == o["step"]
+        assert z == o["z_ind"]
+        np.testing.assert_allclose(x, o["x"], rtol=0, atol=1e-10)
+        np.testing.assert_allclose(v, o["v"], rtol=0, atol=1e-12)
+        assert rel_force_err(sim.forces(0), o["F"]).max() <= 1e-9
+        e = sim.energy(0)
+        assert e["total"] == pytest.approx(o["total"], abs=1e-9 * rep.n_cr)
+        assert e["kinetic"] == pytest.approx(o["kinetic"], rel=1e-11)
+        assert e["load"] == pytest.approx(o["load"], rel=1e-9, abs=1e-10)
+        assert e["rebuilds"] == o["rebuilds"]
+
+
+def test_trajectory_skin_mode_matches_oracle_schedule(md, params):
+    rep = tiny(amp=0.02, gap=2.0, T=600.0)
+    sim = md.MD([rep], params, precision="fp64", rebuild_every=0)
+    osim = oracle.Sim(oracle.Potential(params), rep, skin=0.3, rebuild_every=0)
+    sim.step(250)
+    osim.step(250)
+    e = sim.energy(0)
+    o = osim.state()
+    assert o["rebuilds"] > 1
+    assert e["rebuilds"] == o["rebuilds"]
+    x, v, z, _ = sim.state(0)
+    np.testing.assert_allclose(x, o["x"], rtol=0, atol=1e-9)
+
+
+def test_trajectory_mixed_tracks_oracle(md, params):
+    rep = tiny(amp=0.05, gap=1.0, T=300.0)
+    sim = md.MD([rep], params, precision="mixed", rebuild_every=0)
+    osim = oracle.Sim(oracle.Potential(params), rep, skin=0.3)
+    sim.step(100)
+    osim.step(100)
+    x, v, z, _ = sim.state(0)
+    o = osim.state()
+    np.testing.assert_allclose(x, o["x"], rtol=0, atol=1e-5)
+    assert rel_force_err(sim.forces(0), o["F"]).max() < 1e-3
+    assert sim.energy(0)["total"] == pytest.approx(o["total"], abs=1e-5 * rep.n_cr)
+
+
+def test_graph_and_direct_launch_bitwise_equal(md, params):
+    rep = tiny(amp=0.05)
+    a = md.MD([rep], params, precision="mixed", use_graph=True)
+    b = md.MD([rep], params, precision="mixed", use_graph=False)
+    a.step(37); b.step(37)
+    xa, va, _, _ = a.state(0)
+    xb, vb, _, _ = b.state(0)
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert a.energy(0) == b.energy(0)
+    t = b.step_profiled(5)
+    assert t["steps"] == 5 and t["force"] > 0 and t["density"] > 0
+
+
+def _uneven_replicas(n=5):
+    reps = []
+    for r, (nxy, nz, R, T) in enumerate([(6, 6, 5.0, 100.0), (9, 7, 6.0, 450.0), (7, 11, 5.5, 250.0),
+                                         (11, 6, 8.0, 300.0), (8, 9, 6.5, 500.0)][:n]):
+        rep = mi.make_replica(f"r{r}", nxy, nxy, nz, R, T, seed=100 + r, gap=1.2)
+        reps.append(jitter(rep, 0.08, r))
+    return reps
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("mixed", MIXED_TOL)])
+def test_batched_replicas_match_oracle(md, params, precision, tol):
+    reps = _uneven_replicas()
+    sim = md.MD(reps, params, precision=precision)
+    info = sim.info()
+    assert info["replicas"] == len(reps) and info["n_cr"] == sum(r.n_cr for r in reps)
+    assert info["slots"] % 128 == 0 and info["slots"] >= info["n_cr"]
+    for r, rep in enumerate(reps):
+        o = oracle_eval(params, rep)
+        assert rel_force_err(sim.forces(r), o["F"]).max() <= tol
+        energy_close(sim.energy(r), o, 1e-12 if precision == "fp64" else 1e-5, 1e-10 if precision == "fp64" else 1e-4)
+
+
+def test_batched_trajectory_equals_replicas_alone(md, params):
+    reps = _uneven_replicas(3)
+    batch = md.MD(reps, params, precision="fp64", rebuild_every=5)
+    batch.step(30)
+    for r, rep in enumerate(reps):
+        osim = oracle.Sim(oracle.Potential(params), rep, skin=0.3, rebuild_every=5)
+        osim.step(30)
+        x, v, z, _ = batch.state(r)
+        np.testing.assert_allclose(x, osim.state()["x"], rtol=0, atol=1e-10)
+        assert z == osim.state()["z_ind"]
+
+
+def test_ragged_free_cluster_and_no_indenter(md, params):
+    rep = mi.small_cluster(3, jitter=0.1)          # 91 atoms: not a multiple of the tile
+    rep.v_cr = np.random.default_rng(1).normal(0, 2e-3, rep.x_cr.shape)
+    for prec, tol in (("fp64", FP64_TOL), ("mixed", MIXED_TOL)):
+        sim = md.MD([rep], params, precision=prec)
+        o = oracle_eval(params, rep)
+        assert rel_force_err(sim.forces(0), o["F"]).max() <= tol
+        e = sim.energy(0)
+        assert e["morse"] == 0.0 and e["load"] == 0.0
+        sim.step(20)
+        sim.close()
+
+
+def test_single_atom(md, params):
+    rep = mi.small_cluster(1, jitter=0.0)
+    rep.x_cr = rep.x_cr[:1].copy(); rep.v_cr = rep.v_cr[:1].copy(); rep.fixed = rep.fixed[:1].copy()
+    sim = md.MD([rep], params, precision="mixed")
+    assert np.all(sim.forces(0) == 0.0)
+    e = sim.energy(0)
+    assert e["potential"] == 0.0
+    sim.step(5)
+
+
+def test_bcc_closed_form_on_gpu(md, params):
+    n = 6
+    x = mi.bcc_film(n, n, n)
+    rep = mi.Replica("bcc", x, np.zeros_like(x), np.zeros(len(x), np.uint8), np.zeros((0, 3)),
+                     np.zeros(3), np.full(3, n * mi.A_CR), np.ones(3, np.int32), 0.0, 0.0, 1.0, mi.MASS_CR,
+                     0.0, float(x[:, 2].max()))
+    for prec, tol in (("fp64", 1e-9), ("mixed", 2e-6)):
+        sim = md.MD([rep], params, precision=prec)
+        e = sim.energy(0)
+        assert e["potential"] / len(x) == pytest.approx(-params["_targets"]["E_c"], abs=tol)
+        assert np.abs(sim.forces(0)).max() < (1e-11 if prec == "fp64" else 1e-5)
+
+
+def test_state_roundtrip(md, params):
+    rep = tiny(amp=0.05)
+    sim = md.MD([rep], params, precision="fp64")
+    sim.step(10)
+    x, v, z, step = sim.state(0)
+    e0 = sim.energy(0)
+    sim.set_state(0, x, v, z, step)
+    x2, v2, z2, step2 = sim.state(0)
+    assert np.array_equal(x, x2) and np.array_equal(v, v2) and z == z2 and step == step2
+    e1 = sim.energy(0)
+    assert e1["potential"] == pytest.approx(e0["potential"], rel=1e-13)
+    # a state set from elsewhere is what the next step starts from
+    o = oracle.Sim(oracle.Potential(params), rep, skin=0.3, x=x, v=v)
+    sim.step(5)
+    o.step(5)
+    np.testing.assert_allclose(sim.state(0)[0], o.state()["x"], rtol=0, atol=1e-10)
+
+
+def test_lost_atom_reported(md, params):
+    rep = tiny(amp=0.0)
+    rep.x_cr = rep.x_cr.copy()
+    rep.x_cr[5, 2] = rep.box_hi[2] + 1.0
+    with pytest.raises(md.MDError) as ei:
+        md.MD([rep], params, precision="mixed")
+    assert ei.value.code == md.MD_ERR_LOST_ATOM
+
+
+def test_neighbour_capacity_grows_at_build(md, params):
+    rep = tiny(amp=0.05)
+    sim = md.MD([rep], params, precision="mixed", kmax=20, kcmax=8)
+    info = sim.info()
+    assert info["kmax"] >= info["max_cnt"] > 20
+    o = oracle_eval(params, rep)
+    assert rel_force_err(sim.forces(0), o["F"]).max() <= MIXED_TOL
+
+
+def test_skin_violation_reported_in_fixed_interval_mode(md, params):
+    rep = tiny(amp=0.0, T=3000.0, gap=3.0)
+    sim = md.MD([rep], params, precision="mixed", rebuild_every=100000)
+    with pytest.raises(md.MDError) as ei:
+        sim.step(200)
+    assert ei.value.code == md.MD_ERR_SKIN_VIOLATION
+
+
+def test_bad_periodic_box_rejected(md, params):
+    rep = mi.make_replica("small", 4, 4, 4, 0.0, 10.0, seed=1)   # 11.5 A < 3 cells of 4.84 A
+    with pytest.raises(md.MDError) as ei:
+        md.MD([rep], params)
+    assert ei.value.code == md.MD_ERR_ARG
