@@ -438,8 +438,11 @@ static int build_list(int32_t n, const double *x, const or_box *b, double cut, i
     return 0;
 }
 
-/* Cr-C neighbours: every indenter atom c with |x_c - x_i|^2 < cut^2, by brute force over
- * the indenter for the film atoms that lie within `cut` of the indenter's bounding box. */
+/* Cr-C neighbours: every indenter atom c with |x_c - x_i|^2 < cut^2 (minimum image), by
+ * brute force over the indenter for the film atoms that lie within `cut` of the indenter's
+ * bounding box.  The box test can only skip an atom when |minimum-image offset| > extent/2
+ * + cut, which needs L > extent + 2 cut: exactly when no periodic image of the indenter
+ * can reach the atom either. */
 static int build_clist(int32_t n, const double *x, int32_t nc, const double *xc, const or_box *b,
                        double cut, or_list *out)
 {

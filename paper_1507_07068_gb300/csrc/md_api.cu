@@ -393,9 +393,10 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
                 double ext = (bh[k] - bl[k]) + 1e-6;
                 int n = (int)floor(ext / cutc);
                 if (n < 1) n = 1;
+                if (n > 64) n = 64;   // one 64-bit cell set per axis in k_nbrc
                 R.cg_n[k] = n; R.cg_w[k] = ext / n; R.cg_lo[k] = bl[k] - 0.5e-6;
-                if (R.per[k] && (bh[k] - bl[k]) + 2.0 * cutc > R.L[k])
-                    INIT_FAIL(fail(h, MD_ERR_ARG, "replica %d: indenter (%.2f A) plus twice the Morse reach exceeds the periodic length %.2f A on axis %d", r, bh[k] - bl[k], R.L[k], k));
+                if (R.per[k] && !(R.L[k] > 2.0 * cutc))
+                    INIT_FAIL(fail(h, MD_ERR_ARG, "replica %d: periodic length %.2f A on axis %d must exceed twice the Morse reach rc_morse + skin = %.2f A", r, R.L[k], k, cutc));
             }
             ccells += R.cg_n[0] * R.cg_n[1] * R.cg_n[2];
         }

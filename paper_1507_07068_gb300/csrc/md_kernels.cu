@@ -652,7 +652,20 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
     atomicMax(&a.st->max_cnt, m);
 }
 
-// Cr-C list through the indenter's own cell grid (indenter frame = positions at z_ind = 0)
+// Cr-C list through the indenter's own cell grid (indenter frame = positions at z_ind = 0).
+// Along a periodic axis both images of the film atom that can reach the indenter are
+// searched: the cells of the two reach intervals are merged into one bit set per axis
+// (indenter grids have at most 64 cells per axis), so every cell is visited once.
+__device__ __forceinline__ unsigned long long cell_bits(double q, double reach, double lo, double w, int n)
+{
+    double tl = floor((q - reach - lo) / w);
+    double th = floor((q + reach - lo) / w);
+    if (!(th >= 0.0) || !(tl <= (double)(n - 1))) return 0ull;
+    int a = tl < 0.0 ? 0 : (int)tl;
+    int b = th > (double)(n - 1) ? n - 1 : (int)th;
+    return (2ull << b) - (1ull << a);   // bits a..b (b = 63 wraps to the top bit correctly)
+}
+
 __global__ void __launch_bounds__(128) k_nbrc(DevArgs a)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -665,22 +678,27 @@ __global__ void __launch_bounds__(128) k_nbrc(DevArgs a)
     double z_ind = a.rs[r].z_ind;
     double xi[3] = {a.x[s], a.x[S + s], a.x[2 * S + s]};
     if (!(isfinite(xi[0]) && isfinite(xi[1]) && isfinite(xi[2]))) { a.cntc[s] = 0; return; }   // reported by k_bin
-    int lo[3], hi[3];
+    unsigned long long mask[3];
     double reach = a.cutc * (1.0 + 1e-9) + 1e-9;
     for (int k = 0; k < 3; ++k) {
         double q = xi[k] - (k == 2 ? z_ind : 0.0);
         double ctr = R.cg_lo[k] + 0.5 * R.cg_n[k] * R.cg_w[k];
-        q = ctr + mi64(q - ctr, R.per[k], R.L[k]);
-        double tl = floor((q - reach - R.cg_lo[k]) / R.cg_w[k]);
-        double th = floor((q + reach - R.cg_lo[k]) / R.cg_w[k]);
-        if (th < 0.0 || tl > (double)(R.cg_n[k] - 1)) { a.cntc[s] = 0; return; }
-        lo[k] = tl < 0.0 ? 0 : (int)tl;
-        hi[k] = th > (double)(R.cg_n[k] - 1) ? R.cg_n[k] - 1 : (int)th;
+        mask[k] = 0ull;
+        if (R.per[k]) {
+            q = ctr + mi64(q - ctr, 1, R.L[k]);
+            double q2 = q > ctr ? q - R.L[k] : q + R.L[k];
+            mask[k] = cell_bits(q2, reach, R.cg_lo[k], R.cg_w[k], R.cg_n[k]);
+        }
+        mask[k] |= cell_bits(q, reach, R.cg_lo[k], R.cg_w[k], R.cg_n[k]);
+        if (!mask[k]) { a.cntc[s] = 0; return; }
     }
     int m = 0;
-    for (int q2 = lo[2]; q2 <= hi[2]; ++q2)
-        for (int q1 = lo[1]; q1 <= hi[1]; ++q1)
-            for (int q0 = lo[0]; q0 <= hi[0]; ++q0) {
+    for (unsigned long long m2 = mask[2]; m2; m2 &= m2 - 1) {
+        int q2 = __ffsll((long long)m2) - 1;
+        for (unsigned long long m1 = mask[1]; m1; m1 &= m1 - 1) {
+            int q1 = __ffsll((long long)m1) - 1;
+            for (unsigned long long m0 = mask[0]; m0; m0 &= m0 - 1) {
+                int q0 = __ffsll((long long)m0) - 1;
                 int key = R.ccell_off + (q2 * R.cg_n[1] + q1) * R.cg_n[0] + q0;
                 int b = a.ccell_start[key], e = b + a.ccell_count[key];
                 for (int c = b; c < e; ++c) {
@@ -694,6 +712,8 @@ __global__ void __launch_bounds__(128) k_nbrc(DevArgs a)
                     }
                 }
             }
+        }
+    }
     a.cntc[s] = m < a.kcmax ? m : a.kcmax;
     if (m > a.kcmax) atomicOr(&a.st->err, MDE_COVERFLOW);
     atomicMax(&a.st->max_cntc, m);

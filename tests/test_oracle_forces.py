@@ -182,3 +182,25 @@ def test_cr_c_pair(params):
     k = int(np.argmin(E))
     assert abs(ys[k] - params["y_eq"]) < 0.006
     assert min(E) == pytest.approx(-params["D_o"], rel=1e-4)
+
+
+def test_cr_c_list_in_narrow_periodic_box_matches_plain_minimum_image():
+    """Cr-C pairs by a plain numpy minimum-image double loop, in a box where the indenter
+    plus twice the reach is wider than the period (pairs through the periodic image)."""
+    # indenter sunk into the film so that its equator meets film atoms (a geometry test)
+    rep = mi.make_replica("narrow", 8, 8, 6, 6.0, 300.0, seed=4, gap=-6.0)
+    L = rep.box_hi - rep.box_lo
+    cut = 6.3
+    assert (rep.x_c[:, 0].max() - rep.x_c[:, 0].min()) + 2 * cut > L[0]
+    off, idx = oracle.cneighbors(rep.x_cr, rep.x_c, rep.box_lo, rep.box_hi, rep.periodic, cut)
+    d = rep.x_c[None, :, :] - rep.x_cr[:, None, :]
+    for k in range(2):
+        d[..., k] = np.where(d[..., k] > 0.5 * L[k], d[..., k] - L[k], d[..., k])
+        d[..., k] = np.where(d[..., k] < -0.5 * L[k], d[..., k] + L[k], d[..., k])
+    r2 = (d ** 2).sum(-1)
+    for i in range(rep.n_cr):
+        expect = set(np.nonzero(r2[i] < cut * cut)[0].tolist())
+        assert set(idx[off[i]:off[i + 1]].tolist()) == expect, i
+    # some pairs are reached only through the periodic image
+    direct = rep.x_c[None, :, :2] - rep.x_cr[:, None, :2]
+    assert np.any((r2 < cut * cut) & (np.abs(direct).max(-1) > 0.5 * L[0]))
