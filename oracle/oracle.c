@@ -110,7 +110,9 @@ static void morse_an(const or_pot *P, double y, double *v, double *dv)
     if (p->shifted) { *v -= P->m_rc + (y - p->rc_m) * P->dm_rc; *dv -= P->dm_rc; }
 }
 
-/* cubic Hermite interpolation on knots (value, slope) with spacing h from r0 */
+/* cubic Hermite interpolation on knots (value, slope) with spacing h from r0.  The basis
+ * h00 + h01 = 1 and h01' = -h00' is used to write both value and slope with the knot
+ * difference g_{k+1} - g_k, so no two large terms cancel before the division by h. */
 static void hermite(const double *kv, const double *kd, int nint, double r0, double h,
                     double r, double *v, double *dv)
 {
@@ -120,12 +122,13 @@ static void hermite(const double *kv, const double *kd, int nint, double r0, dou
     if (k > nint - 1) k = nint - 1;
     double t = s - (double)k;
     double t2 = t * t, t3 = t2 * t;
-    double h00 = 2.0 * t3 - 3.0 * t2 + 1.0, h10 = t3 - 2.0 * t2 + t;
-    double h01 = -2.0 * t3 + 3.0 * t2,      h11 = t3 - t2;
-    double g00 = 6.0 * t2 - 6.0 * t,        g10 = 3.0 * t2 - 4.0 * t + 1.0;
-    double g01 = -6.0 * t2 + 6.0 * t,       g11 = 3.0 * t2 - 2.0 * t;
-    *v = h00 * kv[k] + h10 * h * kd[k] + h01 * kv[k + 1] + h11 * h * kd[k + 1];
-    *dv = (g00 * kv[k] + g10 * h * kd[k] + g01 * kv[k + 1] + g11 * h * kd[k + 1]) / h;
+    double h01 = -2.0 * t3 + 3.0 * t2;                          /* = 1 - h00 */
+    double h10 = t3 - 2.0 * t2 + t, h11 = t3 - t2;
+    double g01 = -6.0 * t2 + 6.0 * t;                           /* = -h00'   */
+    double g10 = 3.0 * t2 - 4.0 * t + 1.0, g11 = 3.0 * t2 - 2.0 * t;
+    double dg = kv[k + 1] - kv[k];
+    *v = kv[k] + h01 * dg + h10 * h * kd[k] + h11 * h * kd[k + 1];
+    *dv = g01 * dg / h + g10 * kd[k] + g11 * kd[k + 1];
 }
 
 static int n_intervals(double a, double b, double h0)

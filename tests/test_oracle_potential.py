@@ -151,3 +151,27 @@ def test_neumaier_is_order_independent():
     s2 = oracle.neumaier(x[::-1])
     assert abs(s1 - exact) <= 1e-13 * abs(exact) and abs(s2 - exact) <= 1e-13 * abs(exact)
     assert abs(float(np.sum(x)) - exact) > abs(s1 - exact)  # plain summation is worse here
+
+
+@pytest.mark.parametrize("which", [oracle.OR_F, oracle.OR_PHI, oracle.OR_MORSE])
+def test_hermite_rounding_against_extended_precision(params, pot_an, pot_tab, which):
+    """The tabulated value and slope equal the same cubic Hermite evaluated in extended
+    precision (from the same knots) to ~1e-14: the oracle's grouping does not cancel."""
+    L = np.longdouble
+    rc = params["rc_m"] if which == oracle.OR_MORSE else params["rc"]
+    N = math.ceil((rc - params["r_min"]) / params["h"] - 1e-9)
+    h = (rc - params["r_min"]) / N
+    rng = np.random.default_rng(3)
+    for r in rng.uniform(1.8, rc - 1e-3, 400):
+        k = min(int(math.floor((r - params["r_min"]) / h)), N - 1)
+        knot = lambda q: pot_an.eval(which, rc if q == N else params["r_min"] + q * h)
+        g0, d0 = knot(k); g1, d1 = knot(k + 1)
+        t = (L(r) - L(params["r_min"])) / L(h) - L(k)
+        hh = L(h)
+        v = (2 * t**3 - 3 * t**2 + 1) * L(g0) + (t**3 - 2 * t**2 + t) * hh * L(d0) + (-2 * t**3 + 3 * t**2) * L(g1) \
+            + (t**3 - t**2) * hh * L(d1)
+        dv = ((6 * t**2 - 6 * t) * L(g0) + (3 * t**2 - 4 * t + 1) * hh * L(d0) + (-6 * t**2 + 6 * t) * L(g1)
+              + (3 * t**2 - 2 * t) * hh * L(d1)) / hh
+        tv, td = pot_tab.eval(which, r)
+        assert abs(tv - float(v)) <= 1e-14 * max(1.0, abs(float(v)))
+        assert abs(td - float(dv)) <= 5e-14 * max(1.0, abs(float(dv)))
