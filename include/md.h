@@ -86,8 +86,9 @@ typedef struct md_params {
  *   x_cr, v_cr : 3*n_cr doubles, film positions (A) and velocities (A/fs)
  *   fixed      : n_cr bytes, nonzero = atom held fixed (v = 0, never moved, still exerts
  *                and feels forces), or NULL for none
- *   x_c        : 3*n_c doubles, indenter atom positions at t = 0 (rigid; at time t they are
- *                x_c + (0, 0, z_indenter(t) - z_indenter0)); NULL when n_c = 0
+ *   x_c        : 3*n_c doubles, indenter atom positions at zero displacement (rigid; at
+ *                time t they are x_c + (0, 0, z_indenter(t)), with z_indenter(0) =
+ *                z_indenter0); NULL when n_c = 0
  *   box_lo/hi  : the cell-grid domain.  A periodic axis has period hi - lo (minimum image);
  *                along a non-periodic axis an atom outside [lo, hi] is reported as lost.
  *   z_indenter0, v_indenter : indenter displacement at t = 0 and its rate (A/fs; negative
@@ -145,7 +146,8 @@ typedef struct md_energy {
     int64_t rebuilds;   /* neighbour-list rebuilds after md_init                 */
 } md_energy;
 
-/* Per-phase device time of md_step_profiled, milliseconds summed over its steps. */
+/* Per-phase device time of md_step_profiled, milliseconds summed over its steps (reduce:
+ * the energy sums, which run once at the end of an md_step / md_step_profiled call). */
 typedef struct md_phase_times {
     double skin, rebuild, verlet1, density, force, reduce;
     int64_t steps, rebuilds;

@@ -110,6 +110,34 @@ static void morse_an(const or_pot *P, double y, double *v, double *dv)
     if (p->shifted) { *v -= P->m_rc + (y - p->rc_m) * P->dm_rc; *dv -= P->dm_rc; }
 }
 
+/* Knot values of the tables are evaluated in extended precision (long double) and rounded
+ * once to FP64: a Hermite slope carries the knot-value rounding amplified by 1.5/h, so knots
+ * rounded once from a more precise value make the table reproducible to the last bit. */
+static long double f_raw_l(const or_params *p, long double r)
+{
+    return (long double)p->f_e * powl((long double)p->r_e / r, (long double)p->beta);
+}
+
+static void phi_l(const or_params *p, long double r, long double *v, long double *dv)
+{
+    long double x = r / (long double)p->r_e, d = p->d;
+    if (x > d) { *v = 0.0L; *dv = 0.0L; return; }
+    long double a0 = p->a0, a1 = p->a1, a2 = p->a2, a3 = p->a3;
+    long double poly = ((a3 * x + a2) * x + a1) * x + a0;
+    long double dpoly = (3.0L * a3 * x + 2.0L * a2) * x + a1;
+    long double t = x - d;
+    *v = t * t * poly;
+    *dv = (2.0L * t * poly + t * t * dpoly) / (long double)p->r_e;
+}
+
+static void morse_l(const or_params *p, long double y, long double *v, long double *dv)
+{
+    long double q = y / (long double)p->y_eq - 1.0L, ax = p->alpha_x;
+    long double e1 = expl(-ax * q), e2 = expl(-0.5L * ax * q);
+    *v = (long double)p->D_o * (e1 - 2.0L * e2);
+    *dv = (long double)p->D_o * (-ax * e1 + ax * e2) / (long double)p->y_eq;
+}
+
 /* cubic Hermite interpolation on knots (value, slope) with spacing h from r0.  The basis
  * h00 + h01 = 1 and h01' = -h00' is used to write both value and slope with the knot
  * difference g_{k+1} - g_k, so no two large terms cancel before the division by h. */
@@ -161,21 +189,24 @@ or_pot *or_pot_new(const or_params *p)
         P->tp_v = malloc(sizeof(double) * (P->nf + 1)); P->tp_d = malloc(sizeof(double) * (P->nf + 1));
         P->tm_v = malloc(sizeof(double) * (P->nm + 1)); P->tm_d = malloc(sizeof(double) * (P->nm + 1));
         if (!P->tf_v || !P->tf_d || !P->tp_v || !P->tp_d || !P->tm_v || !P->tm_d) { or_pot_free(P); return NULL; }
+        long double frc = f_raw_l(p, p->rc), dfrc = -(long double)p->beta * frc / (long double)p->rc;
+        long double mrc, dmrc;
+        morse_l(p, p->rc_m, &mrc, &dmrc);
         for (int k = 0; k <= P->nf; ++k) {
             double r = (k == P->nf) ? p->rc : p->r_min + k * P->hf;
             /* knot at r = rc takes the limit from below (value of the r < rc branch) */
-            double fv, fd;
-            fv = f_raw(p, r); fd = df_raw(p, r);
-            if (p->shifted) { fv -= P->f_rc + (r - p->rc) * P->df_rc; fd -= P->df_rc; }
-            P->tf_v[k] = fv; P->tf_d[k] = fd;
-            phi_an(p, r, &P->tp_v[k], &P->tp_d[k]);
+            long double rl = r, fv = f_raw_l(p, rl), fd = -(long double)p->beta * fv / rl, pv, pd;
+            if (p->shifted) { fv -= frc + (rl - (long double)p->rc) * dfrc; fd -= dfrc; }
+            P->tf_v[k] = (double)fv; P->tf_d[k] = (double)fd;
+            phi_l(p, rl, &pv, &pd);
+            P->tp_v[k] = (double)pv; P->tp_d[k] = (double)pd;
         }
         for (int k = 0; k <= P->nm; ++k) {
             double y = (k == P->nm) ? p->rc_m : p->r_min + k * P->hm;
-            double mv, md;
-            morse_raw(p, y, &mv, &md);
-            if (p->shifted) { mv -= P->m_rc + (y - p->rc_m) * P->dm_rc; md -= P->dm_rc; }
-            P->tm_v[k] = mv; P->tm_d[k] = md;
+            long double yl = y, mv, md;
+            morse_l(p, yl, &mv, &md);
+            if (p->shifted) { mv -= mrc + (yl - (long double)p->rc_m) * dmrc; md -= dmrc; }
+            P->tm_v[k] = (double)mv; P->tm_d[k] = (double)md;
         }
     }
     return P;

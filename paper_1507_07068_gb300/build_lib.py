@@ -21,7 +21,9 @@ LIB = os.path.join(HERE, "libmd.so")
 OBJDIR = os.path.join(HERE, "_build")
 SOURCES = ["md_kernels.cu", "md_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+# host code without FMA contraction: the FP64 potential tables and cell geometry computed on
+# the host must not depend on the host compiler's contraction choices
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE]
 
 
 def nvcc() -> str:

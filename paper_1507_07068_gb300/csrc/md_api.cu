@@ -136,7 +136,7 @@ int forces_now(md_t *h, cudaStream_t s)
 {
     CU(launch_density(h->a, h->pot, h->cfg, s));
     CU(launch_force(h->a, h->pot, h->cfg, 0, s));
-    CU(launch_reduce(h->a, h->cfg, 0, s));
+    CU(launch_reduce(h->a, h->cfg, s));
     return MD_OK;
 }
 
@@ -183,7 +183,8 @@ void destroy_graphs(md_t *h)
 }
 
 // One graph of `nsteps` whole time steps: per step [k_skin -> k_decide] -> IF(rebuild) ->
-// [k_verlet1 -> k_density -> k_force -> k_reduce].  k_decide sets the step's conditional.
+// [k_verlet1 -> k_density -> k_force].  k_decide sets the step's conditional.  The energy
+// sums (k_reduce) run once after the last step of an md_step call.
 int capture(md_t *h, int nsteps, cudaGraphExec_t *out)
 {
     cudaGraph_t g = nullptr;
@@ -219,7 +220,6 @@ int capture(md_t *h, int nsteps, cudaGraphExec_t *out)
         CU(launch_verlet1(h->a, h->cap));
         CU(launch_density(h->a, h->pot, h->cfg, h->cap));
         CU(launch_force(h->a, h->pot, h->cfg, 1, h->cap));
-        CU(launch_reduce(h->a, h->cfg, 1, h->cap));
         CU(cudaStreamGetCaptureInfo(h->cap, &cs, nullptr, nullptr, &d, nullptr, &nd));
         deps.assign(d, d + nd);
         CU(cudaStreamEndCapture(h->cap, &g));
@@ -260,8 +260,6 @@ int step_direct(md_t *h, cudaEvent_t *ev, bool *rebuilt)
     if (ev) CU(cudaEventRecord(ev[5], s));
     CU(launch_force(h->a, h->pot, h->cfg, 1, s));
     if (ev) CU(cudaEventRecord(ev[6], s));
-    CU(launch_reduce(h->a, h->cfg, 1, s));
-    if (ev) CU(cudaEventRecord(ev[7], s));
     if (rebuilt) *rebuilt = flag != 0;
     return MD_OK;
 }
@@ -596,6 +594,7 @@ int md_step(md_t *h, int64_t n)
         for (int64_t k = 0; k < n; ++k)
             if ((rc = step_direct(h, nullptr, nullptr))) return rc;
     }
+    if (n > 0) CU(launch_reduce(h->a, h->cfg, h->stream));
     DevStatus st;
     if ((rc = read_status(h, &st))) return rc;
     return status_to_code(h, st);
@@ -611,17 +610,25 @@ int md_step_profiled(md_t *h, int64_t n, md_phase_times *out)
     for (int64_t k = 0; k < n; ++k) {
         bool rebuilt = false;
         if ((rc = step_direct(h, h->ev.data(), &rebuilt))) return rc;
-        CU(cudaEventSynchronize(h->ev[7]));
-        float ms[7];
-        for (int p = 0; p < 7; ++p) CU(cudaEventElapsedTime(&ms[p], h->ev[p], h->ev[p + 1]));
+        CU(cudaEventSynchronize(h->ev[6]));
+        float ms[6];
+        for (int p = 0; p < 6; ++p) CU(cudaEventElapsedTime(&ms[p], h->ev[p], h->ev[p + 1]));
         out->skin += ms[0];
         out->rebuild += ms[2];
         out->verlet1 += ms[3];
         out->density += ms[4];
         out->force += ms[5];
-        out->reduce += ms[6];
         out->steps += 1;
         out->rebuilds += rebuilt ? 1 : 0;
+    }
+    if (n > 0) {
+        CU(cudaEventRecord(h->ev[0], h->stream));
+        CU(launch_reduce(h->a, h->cfg, h->stream));
+        CU(cudaEventRecord(h->ev[1], h->stream));
+        CU(cudaEventSynchronize(h->ev[1]));
+        float ms;
+        CU(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+        out->reduce += ms;
     }
     DevStatus st;
     if ((rc = read_status(h, &st))) return rc;

@@ -149,5 +149,5 @@ cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s);
 cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s);
 cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, cudaStream_t s);
-cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, int advance, cudaStream_t s);
+cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_refresh_pos4(const DevArgs &a, cudaStream_t s);

@@ -25,36 +25,41 @@
 
 #include "md_internal.h"
 
+#define MD_UNROLL 4   // neighbour entries per lane whose loads are issued together
+
 // ============================================================================ host:
 // potential forms used to fill the tables (FP64), restated from the Appendix.
 
 namespace {
 
+// Knot values are evaluated in extended precision and rounded once to FP64: the slope of
+// a Hermite cubic carries knot-value rounding amplified by 1.5/h, so once-rounded knots
+// keep the FP64 tables reproducible to the last bit.
 struct HostPot {
     md_params p;
-    double f_rc = 0, df_rc = 0, m_rc = 0, dm_rc = 0;
-    double e[4];   // Eq. A4 about x = d: Phi = t^2 (e0 + e1 t + e2 t^2 + e3 t^3), t = r/r_e - d
+    long double f_rc = 0, df_rc = 0, m_rc = 0, dm_rc = 0;
+    long double e[4];   // Eq. A4 about x = d: Phi = t^2 (e0 + e1 t + e2 t^2 + e3 t^3), t = r/r_e - d
 
-    double f_raw(double r) const { return p.f_e * pow(p.r_e / r, p.beta); }
-    double df_raw(double r) const { return -p.beta * f_raw(r) / r; }
-    void morse_raw(double y, double &v, double &dv) const {
-        double E = exp(-0.5 * p.alpha_x * (y / p.y_eq - 1.0));
-        v = p.D_o * E * (E - 2.0);
-        dv = -p.D_o * p.alpha_x / p.y_eq * E * (E - 1.0);
+    long double f_raw(long double r) const { return (long double)p.f_e * powl((long double)p.r_e / r, (long double)p.beta); }
+    long double df_raw(long double r) const { return -(long double)p.beta * f_raw(r) / r; }
+    void morse_raw(long double y, long double &v, long double &dv) const {
+        long double E = expl(-0.5L * (long double)p.alpha_x * (y / (long double)p.y_eq - 1.0L));
+        v = (long double)p.D_o * E * (E - 2.0L);
+        dv = -(long double)p.D_o * (long double)p.alpha_x / (long double)p.y_eq * E * (E - 1.0L);
     }
-    void f(double r, double &v, double &dv) const {   // r < rc branch
-        v = f_raw(r) - f_rc - (r - p.rc) * df_rc;
+    void f(long double r, long double &v, long double &dv) const {   // r < rc branch
+        v = f_raw(r) - f_rc - (r - (long double)p.rc) * df_rc;
         dv = df_raw(r) - df_rc;
     }
-    void phi(double r, double &v, double &dv) const {
-        double t = r / p.r_e - p.d;
-        if (t > 0.0) { v = dv = 0.0; return; }
+    void phi(long double r, long double &v, long double &dv) const {
+        long double t = r / (long double)p.r_e - (long double)p.d;
+        if (t > 0.0L) { v = dv = 0.0L; return; }
         v = t * t * (e[0] + t * (e[1] + t * (e[2] + t * e[3])));
-        dv = t * (2.0 * e[0] + t * (3.0 * e[1] + t * (4.0 * e[2] + t * 5.0 * e[3]))) / p.r_e;
+        dv = t * (2.0L * e[0] + t * (3.0L * e[1] + t * (4.0L * e[2] + t * 5.0L * e[3]))) / (long double)p.r_e;
     }
-    void morse(double y, double &v, double &dv) const {
+    void morse(long double y, long double &v, long double &dv) const {
         morse_raw(y, v, dv);
-        v -= m_rc + (y - p.rc_morse) * dm_rc;
+        v -= m_rc + (y - (long double)p.rc_morse) * dm_rc;
         dv -= dm_rc;
     }
 };
@@ -75,8 +80,11 @@ void fill_table(int n, double r0, double r1, Fn g, std::vector<Cf64> &out)
     double h = (r1 - r0) / n;
     std::vector<double> v(n + 1), d(n + 1);
     for (int k = 0; k <= n; ++k) {
-        double r = (k == n) ? r1 : r0 + k * h;
-        g(r, v[k], d[k]);
+        double r = (k == n) ? r1 : r0 + k * h;   // host code is built without FMA contraction
+        long double vl, dl;
+        g((long double)r, vl, dl);
+        v[k] = (double)vl;
+        d[k] = (double)dl;
     }
     for (int k = 0; k < n; ++k) hermite_coeffs(v[k], v[k + 1], d[k] * h, d[k + 1] * h, out[k]);
 }
@@ -94,11 +102,11 @@ int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs
     HostPot H;
     H.p = *p;
     // Taylor coefficients of the cubic of Eq. A4 about x = d
-    const double *a = p->a, d = p->d;
-    H.e[0] = ((a[3] * d + a[2]) * d + a[1]) * d + a[0];
-    H.e[1] = (3.0 * a[3] * d + 2.0 * a[2]) * d + a[1];
-    H.e[2] = 3.0 * a[3] * d + a[2];
-    H.e[3] = a[3];
+    const long double a0 = p->a[0], a1 = p->a[1], a2 = p->a[2], a3 = p->a[3], d = p->d;
+    H.e[0] = ((a3 * d + a2) * d + a1) * d + a0;
+    H.e[1] = (3.0L * a3 * d + 2.0L * a2) * d + a1;
+    H.e[2] = 3.0L * a3 * d + a2;
+    H.e[3] = a3;
     if (p->shifted) {
         H.f_rc = H.f_raw(p->rc);
         H.df_rc = H.df_raw(p->rc);
@@ -107,11 +115,11 @@ int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs
     P->f_e = p->f_e; P->r_e = p->r_e; P->beta = p->beta;
     P->lf0 = log2(p->f_e) + p->beta * log2(p->r_e);
     P->F_o = p->F_o; P->n = p->n; P->rho_e = p->rho_e; P->alpha = p->alpha; P->P_e = p->P_e;
-    for (int k = 0; k < 4; ++k) P->b[k] = H.e[k];
-    P->d = d;
+    for (int k = 0; k < 4; ++k) P->b[k] = (double)H.e[k];
+    P->d = p->d;
     P->D_o = p->D_o; P->half_ax = 0.5 * p->alpha_x; P->inv_yeq = 1.0 / p->y_eq;
     P->rc = p->rc; P->rc_m = p->rc_morse; P->rc2 = p->rc * p->rc; P->rcm2 = p->rc_morse * p->rc_morse;
-    P->f_rc = H.f_rc; P->df_rc = H.df_rc; P->m_rc = H.m_rc; P->dm_rc = H.dm_rc;
+    P->f_rc = (double)H.f_rc; P->df_rc = (double)H.df_rc; P->m_rc = (double)H.m_rc; P->dm_rc = (double)H.dm_rc;
     P->shifted = p->shifted; P->tabulated = p->tabulated;
     P->r_min = p->r_min;
     int nf = (int)ceil((p->rc - p->r_min) / p->h - 1e-9);
@@ -124,9 +132,9 @@ int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs
     P->inv_hm = nm / (p->rc_morse - p->r_min);
     *d_tabs64 = nullptr; *d_tabs32 = nullptr;
     std::vector<Cf64> tf, tp, tm;
-    fill_table(nf, p->r_min, p->rc, [&](double r, double &v, double &dv) { H.f(r, v, dv); }, tf);
-    fill_table(nf, p->r_min, p->rc, [&](double r, double &v, double &dv) { H.phi(r, v, dv); }, tp);
-    fill_table(nm, p->r_min, p->rc_morse, [&](double r, double &v, double &dv) { H.morse(r, v, dv); }, tm);
+    fill_table(nf, p->r_min, p->rc, [&](long double r, long double &v, long double &dv) { H.f(r, v, dv); }, tf);
+    fill_table(nf, p->r_min, p->rc, [&](long double r, long double &v, long double &dv) { H.phi(r, v, dv); }, tp);
+    fill_table(nm, p->r_min, p->rc_morse, [&](long double r, long double &v, long double &dv) { H.morse(r, v, dv); }, tm);
     size_t ntot = (size_t)2 * nf + nm;
     std::vector<Cf64> all;
     all.reserve(ntot);
@@ -425,14 +433,15 @@ __global__ void k_decide(DevArgs a, int force, int use_cond, cudaGraphConditiona
         double dmax = sqrt(__longlong_as_double((long long)S.d2max_bits));
         S.d2max_bits = 0ull;
         int need;
-        if (a.rebuild_every > 0) {
+        if (force) {
+            need = 1;   // explicit build: no displacement test against a previous list
+        } else if (a.rebuild_every > 0) {
             need = a.st->since_build >= a.rebuild_every;
             if (!need && 2.0 * dmax > a.skin) atomicOr(&a.st->err, MDE_SKIN);
         } else {
             need = (2.0 * dmax > a.skin) ||
                    (a.rep[r].n_c > 0 && __dadd_rn(dmax, fabs(__dsub_rn(S.z_ind, S.z_build))) > a.skin);
         }
-        if (force) need = 1;
         S.need = need;
         any |= need;
     }
@@ -608,10 +617,14 @@ __global__ void k_copyback(DevArgs a)
     }
     a.orig[s] = a.sorig[s];
     a.fixed[s] = a.sfixed[s];
-    if (a.mixed) a.pos4[s] = rel_pos(a, R, s);
+    a.pos4[s] = rel_pos(a, R, s);   // also used by the FP32 prefilter of k_nbr
 }
 
-// full Cr-Cr Verlet list: every slot j != i in the 27-cell stencil with |x_j - x_i|^2 < (rc + skin)^2
+// full Cr-Cr Verlet list: every slot j != i in the 27-cell stencil with |x_j - x_i|^2 <
+// (rc + skin)^2 decided in FP64.  A candidate whose FP32 cell-relative distance is farther
+// than 1e-5 (relative) from the cut-off is decided by the FP32 value (its error is below
+// 2e-6 relative for atoms inside their cells); the rest take the exact FP64 test, so the
+// set equals the all-FP64 set bit for bit.
 __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -619,9 +632,14 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
     const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
     if (s - R.slot_off >= R.n_atoms) return;
     size_t S = a.S;
-    double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
-    int pc = a.cellc[s];
+    const float4 pi = a.pos4[s];
+    int pc = __float_as_int(pi.w);
     int c0 = cell_x(pc), c1 = cell_y(pc), c2 = cell_z(pc);
+    const float cut2 = (float)a.cut2;
+    const float lo2 = cut2 * (1.0f - 1e-5f), hi2 = cut2 * (1.0f + 1e-5f);
+    const float wx = R.w32[0], wy = R.w32[1], wz = R.w32[2];
+    const float lim = 0.75f * fminf(wx, fminf(wy, wz));   // beyond: atom clamped outside its cell
+    const bool ifar = fabsf(pi.x) > lim || fabsf(pi.y) > lim || fabsf(pi.z) > lim;
     int m = 0;
     for (int dz = -1; dz <= 1; ++dz) {
         int q2 = c2 + dz;
@@ -634,12 +652,22 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
                 if (q0 < 0 || q0 >= R.nc[0]) { if (!R.per[0]) continue; q0 = (q0 + R.nc[0]) % R.nc[0]; }
                 int key = R.cell_off + (q2 * R.nc[1] + q1) * R.nc[0] + q0;
                 int b = a.cell_start[key], e = b + a.cell_count[key];
+                const float ox = dx * wx, oy = dy * wy, oz = dz * wz;
                 for (int t = b; t < e; ++t) {
                     if (t == s) continue;
-                    double ddx = mi_exact(__dsub_rn(a.x[t], xi), R.per[0], R.L[0]);
-                    double ddy = mi_exact(__dsub_rn(a.x[S + t], yi), R.per[1], R.L[1]);
-                    double ddz = mi_exact(__dsub_rn(a.x[2 * S + t], zi), R.per[2], R.L[2]);
-                    if (norm2_exact(ddx, ddy, ddz) < a.cut2) {
+                    const float4 pj = a.pos4[t];
+                    const float fx = ox + (pj.x - pi.x), fy = oy + (pj.y - pi.y), fz = oz + (pj.z - pi.z);
+                    const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+                    bool in;
+                    if (!ifar && fabsf(pj.x) <= lim && fabsf(pj.y) <= lim && fabsf(pj.z) <= lim && (r2f < lo2 || r2f > hi2)) {
+                        in = r2f < lo2;
+                    } else {
+                        double ddx = mi_exact(__dsub_rn(a.x[t], a.x[s]), R.per[0], R.L[0]);
+                        double ddy = mi_exact(__dsub_rn(a.x[S + t], a.x[S + s]), R.per[1], R.L[1]);
+                        double ddz = mi_exact(__dsub_rn(a.x[2 * S + t], a.x[2 * S + s]), R.per[2], R.L[2]);
+                        in = norm2_exact(ddx, ddy, ddz) < a.cut2;
+                    }
+                    if (in) {
                         if (m < a.kmax) a.nbr[(size_t)m * S + s] = t;
                         ++m;
                     }
@@ -736,6 +764,7 @@ __global__ void k_verlet1(DevArgs a)
     if (s == R.slot_off) {   // Task 2: the rigid indenter moves by v_ind dt
         RepState &st = a.rs[r];
         st.z_ind = __dadd_rn(st.z_ind, __dmul_rn(R.v_ind, R.dt));
+        if (s == 0) { a.st->step += 1; a.st->since_build += 1; }   // after this step's Task 1 decision
     }
     if (s - R.slot_off >= R.n_atoms) return;
     size_t S = a.S;
@@ -782,17 +811,29 @@ __global__ void __launch_bounds__(256) k_density(DevArgs a, PotDev P)
             const float4 pi = a.pos4[s];
             const int ci = __float_as_int(pi.w);
             const int n = a.cnt[s];
-            for (int k = lane; k < n; k += TPA) {
-                const int j = __ldg(&a.nbr[(size_t)k * S + s]);
-                const float4 pj = __ldg(&a.pos4[j]);
-                float dx, dy, dz;
-                rel_disp(pi, ci, pj, R, dx, dy, dz);
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (r2 < Q.rc2) {
-                    float f, df;
-                    Q.f(sqrtf(r2), f, df);
-                    rho += f;
-                    Ps = fmaf(f, f, Ps);
+            // U list entries and their positions are loaded before any is used, so each lane
+            // keeps 2U independent loads in flight
+            for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
+                int jj[MD_UNROLL];
+#pragma unroll
+                for (int u = 0; u < MD_UNROLL; ++u) {
+                    const int k = k0 + u * TPA;
+                    jj[u] = k < n ? __ldg(&a.nbr[(size_t)k * S + s]) : s;
+                }
+                float4 pj[MD_UNROLL];
+#pragma unroll
+                for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&a.pos4[jj[u]]);
+#pragma unroll
+                for (int u = 0; u < MD_UNROLL; ++u) {
+                    float dx, dy, dz;
+                    rel_disp(pi, ci, pj[u], R, dx, dy, dz);
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    if (k0 + u * TPA < n && r2 < Q.rc2) {
+                        float f, df;
+                        Q.f(sqrtf(r2), f, df);
+                        rho += f;
+                        Ps = fmaf(f, f, Ps);
+                    }
                 }
             }
         }
@@ -866,14 +907,28 @@ __global__ void __launch_bounds__(256) k_force(DevArgs a, PotDev P, int integrat
             const int ci = __float_as_int(pi.w);
             const float2 fmi = a.fm32[s];
             const int n = a.cnt[s];
-            for (int k = lane; k < n; k += TPA) {
-                const int j = __ldg(&a.nbr[(size_t)k * S + s]);
-                const float4 pj = __ldg(&a.pos4[j]);
+            for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
+                int jj[MD_UNROLL];
+#pragma unroll
+                for (int u = 0; u < MD_UNROLL; ++u) {
+                    const int k = k0 + u * TPA;
+                    jj[u] = k < n ? __ldg(&a.nbr[(size_t)k * S + s]) : s;
+                }
+                float4 pjv[MD_UNROLL];
+                float2 fmv[MD_UNROLL];
+#pragma unroll
+                for (int u = 0; u < MD_UNROLL; ++u) {
+                    pjv[u] = __ldg(&a.pos4[jj[u]]);
+                    fmv[u] = __ldg(&a.fm32[jj[u]]);
+                }
+#pragma unroll
+                for (int u = 0; u < MD_UNROLL; ++u) {
+                const float4 pj = pjv[u];
                 float dx, dy, dz;
                 rel_disp(pi, ci, pj, R, dx, dy, dz);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (r2 < Q.rc2) {
-                    const float2 fmj = __ldg(&a.fm32[j]);
+                if (k0 + u * TPA < n && r2 < Q.rc2) {
+                    const float2 fmj = fmv[u];
                     const float rinv = rsqrtf(r2);
                     const float rr = r2 * rinv;
                     float f, df, ph, dph;
@@ -885,6 +940,7 @@ __global__ void __launch_bounds__(256) k_force(DevArgs a, PotDev P, int integrat
                     gy = fmaf(coef, dy, gy);
                     gz = fmaf(coef, dz, gz);
                     ep = fmaf(0.5f, ph, ep);
+                }
                 }
             }
         }
@@ -1004,28 +1060,30 @@ __global__ void __launch_bounds__(256) k_force(DevArgs a, PotDev P, int integrat
 }
 
 // per-replica sums of the CTA partials, fixed order: thread t adds blocks t, t+B, ...;
-// then a fixed tree over threads
-__global__ void k_reduce(DevArgs a, int atoms_per_block, int advance)
+// then a fixed tree over threads (one CTA per replica, one term at a time)
+__global__ void __launch_bounds__(1024) k_reduce(DevArgs a, int atoms_per_block)
 {
     int r = blockIdx.x;
     const RepDev &R = a.rep[r];
     int b0 = R.slot_off / atoms_per_block, b1 = (R.slot_off + R.n_slots) / atoms_per_block;
-    __shared__ double sm[6][128];
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x)
-        for (int t = 0; t < 6; ++t) acc[t] += a.part[(size_t)t * a.max_blocks + b];
-    for (int t = 0; t < 6; ++t) sm[t][threadIdx.x] = acc[t];
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w)
-            for (int t = 0; t < 6; ++t) sm[t][threadIdx.x] += sm[t][threadIdx.x + w];
+    __shared__ double sm[1024];
+    double out[6];
+    for (int t = 0; t < 6; ++t) {
+        double acc = 0.0;
+        for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) acc += a.part[(size_t)t * a.max_blocks + b];
+        sm[threadIdx.x] = acc;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+            __syncthreads();
+        }
+        out[t] = sm[0];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         RepEnergy &E = a.en[r];
-        E.embed = sm[0][0]; E.mterm = sm[1][0]; E.pair = sm[2][0]; E.morse = sm[3][0];
-        E.load = sm[4][0]; E.kinetic = sm[5][0];
-        if (advance && r == 0) { a.st->step += 1; a.st->since_build += 1; }
+        E.embed = out[0]; E.mterm = out[1]; E.pair = out[2]; E.morse = out[3];
+        E.load = out[4]; E.kinetic = out[5];
     }
 }
 
@@ -1118,8 +1176,8 @@ cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, int advance, cudaStream_t s)
+cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
-    k_reduce<<<a.n_rep, 128, 0, s>>>(a, c.block / c.tpa, advance);
+    k_reduce<<<a.n_rep, 1024, 0, s>>>(a, c.block / c.tpa);
     return cudaGetLastError();
 }

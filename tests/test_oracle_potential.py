@@ -153,10 +153,34 @@ def test_neumaier_is_order_independent():
     assert abs(float(np.sum(x)) - exact) > abs(s1 - exact)  # plain summation is worse here
 
 
+def _knot_ext(params, which, r):
+    """Value and slope at a knot in extended precision: Eq. A2 (shifted), A4, A5 (shifted)."""
+    L = np.longdouble
+    p = {k: L(v) for k, v in params.items() if isinstance(v, (int, float))}
+    r = L(r)
+    if which == oracle.OR_F:
+        f = lambda q: p["f_e"] * np.power(p["r_e"] / q, p["beta"])
+        frc = f(p["rc"]); dfrc = -p["beta"] * frc / p["rc"]
+        return f(r) - frc - (r - p["rc"]) * dfrc, -p["beta"] * f(r) / r - dfrc
+    if which == oracle.OR_PHI:
+        x = r / p["r_e"]; t = x - p["d"]
+        poly = ((p["a3"] * x + p["a2"]) * x + p["a1"]) * x + p["a0"]
+        dpoly = (3 * p["a3"] * x + 2 * p["a2"]) * x + p["a1"]
+        return t * t * poly, (2 * t * poly + t * t * dpoly) / p["r_e"]
+    def m(y):
+        q = y / p["y_eq"] - 1
+        e1 = np.exp(-p["alpha_x"] * q); e2 = np.exp(-p["alpha_x"] * q / 2)
+        return p["D_o"] * (e1 - 2 * e2), p["D_o"] * p["alpha_x"] * (e2 - e1) / p["y_eq"]
+    mrc, dmrc = m(p["rc_m"])
+    v, dv = m(r)
+    return v - mrc - (r - p["rc_m"]) * dmrc, dv - dmrc
+
+
 @pytest.mark.parametrize("which", [oracle.OR_F, oracle.OR_PHI, oracle.OR_MORSE])
-def test_hermite_rounding_against_extended_precision(params, pot_an, pot_tab, which):
-    """The tabulated value and slope equal the same cubic Hermite evaluated in extended
-    precision (from the same knots) to ~1e-14: the oracle's grouping does not cancel."""
+def test_hermite_rounding_against_extended_precision(params, pot_tab, which):
+    """Tables: knots are the extended-precision values rounded once to FP64, and the
+    tabulated value and slope equal the cubic Hermite through those knots evaluated in
+    extended precision to ~1e-14 (the oracle's grouping does not cancel)."""
     L = np.longdouble
     rc = params["rc_m"] if which == oracle.OR_MORSE else params["rc"]
     N = math.ceil((rc - params["r_min"]) / params["h"] - 1e-9)
@@ -164,7 +188,10 @@ def test_hermite_rounding_against_extended_precision(params, pot_an, pot_tab, wh
     rng = np.random.default_rng(3)
     for r in rng.uniform(1.8, rc - 1e-3, 400):
         k = min(int(math.floor((r - params["r_min"]) / h)), N - 1)
-        knot = lambda q: pot_an.eval(which, rc if q == N else params["r_min"] + q * h)
+
+        def knot(q):
+            g, d = _knot_ext(params, which, rc if q == N else params["r_min"] + q * h)
+            return float(g), float(d)
         g0, d0 = knot(k); g1, d1 = knot(k + 1)
         t = (L(r) - L(params["r_min"])) / L(h) - L(k)
         hh = L(h)
