@@ -146,8 +146,10 @@ typedef struct md_energy {
     int64_t rebuilds;   /* neighbour-list rebuilds after md_init                 */
 } md_energy;
 
-/* Per-phase device time of md_step_profiled, milliseconds summed over its steps (reduce:
- * the energy sums, which run once at the end of an md_step / md_step_profiled call). */
+/* Per-phase device time of md_step_profiled, milliseconds summed over its steps:
+ * skin = the Task 1 decision, rebuild = binning + lists (when decided), verlet1 = Tasks 2-3
+ * (with the displacement test the next decision uses), density / force = Task 4 (force
+ * includes Task 5), reduce = the energy sums, which run once at the end of the call. */
 typedef struct md_phase_times {
     double skin, rebuild, verlet1, density, force, reduce;
     int64_t steps, rebuilds;

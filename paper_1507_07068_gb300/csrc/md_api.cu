@@ -142,7 +142,6 @@ int forces_now(md_t *h, cudaStream_t s)
 
 int rebuild_now(md_t *h)
 {
-    CU(launch_skin(h->a, h->stream));
     CU(launch_decide(h->a, 1, 0, 0, h->stream));
     CU(launch_rebuild(h->a, h->stream));
     return MD_OK;
@@ -182,7 +181,7 @@ void destroy_graphs(md_t *h)
     h->exec1 = h->execU = nullptr;
 }
 
-// One graph of `nsteps` whole time steps: per step [k_skin -> k_decide] -> IF(rebuild) ->
+// One graph of `nsteps` whole time steps: per step k_decide -> IF(rebuild) ->
 // [k_verlet1 -> k_density -> k_force].  k_decide sets the step's conditional.  The energy
 // sums (k_reduce) run once after the last step of an md_step call.
 int capture(md_t *h, int nsteps, cudaGraphExec_t *out)
@@ -195,7 +194,6 @@ int capture(md_t *h, int nsteps, cudaGraphExec_t *out)
         cudaGraphConditionalHandle hc;
         CU(cudaGraphConditionalHandleCreate(&hc, g, 0, cudaGraphCondAssignDefault));
         CU(cudaStreamBeginCaptureToGraph(h->cap, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), mode));
-        CU(launch_skin(h->a, h->cap));
         CU(launch_decide(h->a, 0, 1, hc, h->cap));
         cudaStreamCaptureStatus cs;
         const cudaGraphNode_t *d = nullptr;
@@ -245,7 +243,6 @@ int step_direct(md_t *h, cudaEvent_t *ev, bool *rebuilt)
 {
     cudaStream_t s = h->stream;
     if (ev) CU(cudaEventRecord(ev[0], s));
-    CU(launch_skin(h->a, s));
     CU(launch_decide(h->a, 0, 0, 0, s));
     if (ev) CU(cudaEventRecord(ev[1], s));
     int32_t flag = 0;
@@ -359,6 +356,8 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
             R.nc[k] = n;
             R.w[k] = R.L[k] / n;
             R.w32[k] = (float)R.w[k];
+            R.wc[k] = (double)R.w32[k];
+            R.dL32[k] = (float)(R.L[k] - n * R.wc[k]);
         }
         R.cell_off = (int32_t)cells;
         R.n_cells = R.nc[0] * R.nc[1] * R.nc[2];

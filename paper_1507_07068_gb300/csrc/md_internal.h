@@ -36,6 +36,16 @@ struct alignas(32) Cf64 {
     double x, y, z, w;
 };
 
+// FP32 constants of the mixed-precision path, converted once on the host
+struct PotF32 {
+    float rmin_s_f, inv_hf, rmin_s_m, inv_hm, lf0, beta, f_rc, df_rc, rc;
+    float inv_re, d, b0, b1, b2, b3;
+    float D_o, half_ax, inv_yeq, m_rc, dm_rc, rc_m;
+    float F_o, n, inv_rho_e, alpha, inv_P_e, rc2;
+    int32_t tabulated, nf, nm;
+    const float4 *tf, *tp, *tm;
+};
+
 // potential, passed by value to kernels (lives in the constant bank)
 struct PotDev {
     // Eq. A2: f = f_e (r_e/r)^beta = exp2(lf0 - beta log2 r)
@@ -56,13 +66,18 @@ struct PotDev {
     int32_t nf, nm;
     const Cf64 *tf, *tp, *tm;
     const float4 *tf32, *tp32, *tm32;
+    PotF32 q;
 };
 
 // static per-replica description (read-only on the device)
 struct RepDev {
-    double lo[3], hi[3], L[3], w[3];  // Cr cell grid; L = hi - lo; w = L / nc
+    double lo[3], hi[3], L[3], w[3];  // Cr cell grid; L = hi - lo; w = L / nc (binning)
     int32_t per[3], nc[3];
-    float w32[3];
+    // FP32 cell-relative positions are taken about the centres lo + (c + 1/2) w32 (w32 =
+    // w rounded to FP32), so two cells' centres differ by an exact multiple of w32, plus
+    // dL32 = L - nc w32 when the pair crosses a periodic boundary
+    float w32[3], dL32[3];
+    double wc[3];                     // (double) w32
     int32_t cell_off, n_cells;
     int32_t slot_off, n_atoms, n_slots;  // first slot (TILE aligned), real atoms, slots incl. padding
     int32_t real_off;                    // atoms of the replicas before (unpadded)
@@ -143,7 +158,6 @@ struct LaunchCfg {
 int md_build_pot(const md_params *p, PotDev *out, Cf64 **d_tabs64, float4 **d_tabs32, char *err, size_t errlen);
 
 // ---- launchers (all enqueue on `s`; return cudaError_t of the launch)
-cudaError_t launch_skin(const DevArgs &a, cudaStream_t s);
 cudaError_t launch_decide(const DevArgs &a, int force, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s);
 cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s);

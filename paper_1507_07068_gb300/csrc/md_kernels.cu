@@ -1,18 +1,18 @@
 // md_kernels.cu -- the sm_103a kernels of libmd and their launchers.
 //
 // Per time step (Fig. 5 / Table 1 of Pal et al., arXiv:1507.07068):
-//   k_skin      Task 1 test: max_i |x_i - x_build,i|^2 per replica (FP64)
-//   k_decide    Task 1 decision (Sec. 2.6 skin/2 rule) -> device flag + graph conditional
+//   k_decide    Task 1 decision (Sec. 2.6 skin/2 rule on max_i |x_i - x_build,i|, which the
+//               previous step's k_verlet1 reduced) -> device flag + graph conditional
 //   [rebuild]   Task 1 rebuild: k_bin (wrap, FP64 cell keys, histogram), scan, k_scatter,
 //               k_cellsort (ascending caller id within a cell), k_gather/k_copyback
 //               (permute every per-atom array), k_nbr (full Cr-Cr Verlet list), k_nbrc
 //               (Cr-C list through the indenter's own cell grid), k_build_done
 //   k_verlet1   Tasks 2+3: indenter move, half kick + drift (Eqs. A11-A12), refresh of the
-//               FP32 cell-relative positions
+//               FP32 cell-relative positions, displacement test for the next decision
 //   k_density   Task 4a: rho_i, P_i (Eq. A2) -> F'(rho_i), M'(P_i), F(rho_i), M(P_i) (Eq. A3)
 //   k_force     Task 4b,c + 5: Eq. (1) with the M term (A6-A8, A10), Morse (A5, A9),
 //               indenter load; epilogue: closing half kick (Task 5), kinetic energy
-//   k_reduce    per-replica FP64 sums of the CTA partials in a fixed order
+//   k_reduce    per-replica FP64 sums of the CTA partials in a fixed order (once per call)
 // Every per-atom kernel writes only its own atom (full neighbour list: no atomics in
 // the force path); energy and load sums are warp-shuffle -> CTA partial -> fixed-order
 // final pass, so results do not depend on scheduling.
@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "md_internal.h"
@@ -158,6 +159,17 @@ int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs
     }
     P->tf = *d_tabs64; P->tp = *d_tabs64 + nf; P->tm = *d_tabs64 + 2 * nf;
     P->tf32 = *d_tabs32; P->tp32 = *d_tabs32 + nf; P->tm32 = *d_tabs32 + 2 * nf;
+    PotF32 &q = P->q;
+    q.inv_hf = (float)P->inv_hf; q.rmin_s_f = (float)(P->r_min * P->inv_hf);
+    q.inv_hm = (float)P->inv_hm; q.rmin_s_m = (float)(P->r_min * P->inv_hm);
+    q.lf0 = (float)P->lf0; q.beta = (float)P->beta; q.f_rc = (float)P->f_rc; q.df_rc = (float)P->df_rc;
+    q.rc = (float)P->rc; q.inv_re = (float)(1.0 / P->r_e); q.d = (float)P->d;
+    q.b0 = (float)P->b[0]; q.b1 = (float)P->b[1]; q.b2 = (float)P->b[2]; q.b3 = (float)P->b[3];
+    q.D_o = (float)P->D_o; q.half_ax = (float)P->half_ax; q.inv_yeq = (float)P->inv_yeq;
+    q.m_rc = (float)P->m_rc; q.dm_rc = (float)P->dm_rc; q.rc_m = (float)P->rc_m;
+    q.F_o = (float)P->F_o; q.n = (float)P->n; q.inv_rho_e = (float)(1.0 / P->rho_e); q.alpha = (float)P->alpha;
+    q.inv_P_e = (float)(1.0 / P->P_e); q.rc2 = (float)P->rc2;
+    q.tabulated = P->tabulated; q.nf = nf; q.nm = nm; q.tf = P->tf32; q.tp = P->tp32; q.tm = P->tm32;
     return MD_OK;
 }
 
@@ -261,26 +273,7 @@ __device__ __forceinline__ void cubic32(const float4 *T, int n, float s, float i
     dv = fmaf(fmaf(3.0f * c.w, t, 2.0f * c.z), t, c.y) * inv_h;
 }
 
-struct Pot32 {   // FP32 constants, derived once per thread from PotDev
-    float rmin_s_f, inv_hf, rmin_s_m, inv_hm, lf0, beta, f_rc, df_rc, rc;
-    float inv_re, d, b0, b1, b2, b3;
-    float D_o, half_ax, inv_yeq, m_rc, dm_rc, rc_m;
-    float F_o, n, inv_rho_e, alpha, inv_P_e, rc2;
-    int tabulated, nf, nm;
-    const float4 *tf, *tp, *tm;
-    __device__ __forceinline__ void init(const PotDev &P)
-    {
-        inv_hf = (float)P.inv_hf; rmin_s_f = (float)(P.r_min * P.inv_hf);
-        inv_hm = (float)P.inv_hm; rmin_s_m = (float)(P.r_min * P.inv_hm);
-        lf0 = (float)P.lf0; beta = (float)P.beta; f_rc = (float)P.f_rc; df_rc = (float)P.df_rc; rc = (float)P.rc;
-        inv_re = (float)(1.0 / P.r_e); d = (float)P.d;
-        b0 = (float)P.b[0]; b1 = (float)P.b[1]; b2 = (float)P.b[2]; b3 = (float)P.b[3];
-        D_o = (float)P.D_o; half_ax = (float)P.half_ax; inv_yeq = (float)P.inv_yeq;
-        m_rc = (float)P.m_rc; dm_rc = (float)P.dm_rc; rc_m = (float)P.rc_m;
-        F_o = (float)P.F_o; n = (float)P.n; inv_rho_e = (float)(1.0 / P.rho_e); alpha = (float)P.alpha;
-        inv_P_e = (float)(1.0 / P.P_e); rc2 = (float)P.rc2;
-        tabulated = P.tabulated; nf = P.nf; nm = P.nm; tf = P.tf32; tp = P.tp32; tm = P.tm32;
-    }
+struct Pot32 : PotF32 {   // the FP32 constants (filled on the host) with the FP32 forms
     __device__ __forceinline__ void f(float r, float &v, float &dv) const
     {
         if (tabulated) { cubic32(tf, nf, fmaf(r, inv_hf, -rmin_s_f), inv_hf, v, dv); return; }
@@ -324,7 +317,7 @@ struct Pot32 {   // FP32 constants, derived once per thread from PotDev
 // per-thread copy of the replica fields the pair kernels use
 struct RepPair {
     int per0, per1, per2, n0, n1, n2;
-    float w0, w1, w2;
+    float w0, w1, w2, dL0, dL1, dL2;
     double L0, L1, L2;
     int slot_off, n_atoms;
     __device__ __forceinline__ void load(const RepDev &R)
@@ -332,32 +325,32 @@ struct RepPair {
         per0 = R.per[0]; per1 = R.per[1]; per2 = R.per[2];
         n0 = R.nc[0]; n1 = R.nc[1]; n2 = R.nc[2];
         w0 = R.w32[0]; w1 = R.w32[1]; w2 = R.w32[2];
+        dL0 = R.dL32[0]; dL1 = R.dL32[1]; dL2 = R.dL32[2];
         L0 = R.L[0]; L1 = R.L[1]; L2 = R.L[2];
         slot_off = R.slot_off; n_atoms = R.n_atoms;
     }
 };
 
-__device__ __forceinline__ int wrap_shift(int s, int per, int n)
+// one axis of x_j - x_i from cell-relative FP32 coordinates: the two cell centres are
+// d cells apart (d = cj - ci); across a periodic boundary the image is one period away,
+// i.e. (d -+ n) w32 -+ dL (the centres are w32 apart, the period is n w32 + dL)
+__device__ __forceinline__ float axis_disp(float pj, float pi, int d, int per, int n, float w, float dL)
 {
+    float m = 0.0f;
     if (per) {
-        if (s > 1) s -= n;
-        else if (s < -1) s += n;
+        if (d > 1) { d -= n; m = -1.0f; }
+        else if (d < -1) { d += n; m = 1.0f; }
     }
-    return s;
+    return fmaf(m, dL, fmaf((float)d, w, pj - pi));
 }
 
-// displacement x_j - x_i from cell-relative FP32 positions: the cell-centre offset of the
-// two cells is a whole number of cell widths (periodic wrap included), added in FP32
 __device__ __forceinline__ void rel_disp(const float4 &pi, int ci, const float4 &pj, const RepPair &R,
                                          float &dx, float &dy, float &dz)
 {
     int cj = __float_as_int(pj.w);
-    int sx = wrap_shift(cell_x(cj) - cell_x(ci), R.per0, R.n0);
-    int sy = wrap_shift(cell_y(cj) - cell_y(ci), R.per1, R.n1);
-    int sz = wrap_shift(cell_z(cj) - cell_z(ci), R.per2, R.n2);
-    dx = fmaf((float)sx, R.w0, pj.x - pi.x);
-    dy = fmaf((float)sy, R.w1, pj.y - pi.y);
-    dz = fmaf((float)sz, R.w2, pj.z - pi.z);
+    dx = axis_disp(pj.x, pi.x, cell_x(cj) - cell_x(ci), R.per0, R.n0, R.w0, R.dL0);
+    dy = axis_disp(pj.y, pi.y, cell_y(cj) - cell_y(ci), R.per1, R.n1, R.w1, R.dL1);
+    dz = axis_disp(pj.z, pi.z, cell_z(cj) - cell_z(ci), R.per2, R.n2, R.w2, R.dL2);
 }
 
 __device__ __forceinline__ double mi64(double d, int per, double L)
@@ -370,15 +363,18 @@ __device__ __forceinline__ double mi64(double d, int per, double L)
     return d;
 }
 
-__device__ __forceinline__ double warp_sum(double v)
+template <class T>
+__device__ __forceinline__ T warp_sum(T v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// CTA sum of up to 4 doubles; thread 0 writes part[t * stride + blk]
-template <int NV>
-__device__ __forceinline__ void cta_partials(double (&v)[NV], double *part, int stride, int blk)
+// CTA sum of up to 4 per-thread values; thread 0 writes part[t * stride + blk] (FP64).
+// Values are summed within a warp in their own type (FP32 in mixed mode: a warp holds
+// at most 32 per-atom energies), then across warps in FP64.
+template <int NV, class T>
+__device__ __forceinline__ void cta_partials(T (&v)[NV], double *part, int stride, int blk)
 {
     __shared__ double sm[32][4];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -386,7 +382,7 @@ __device__ __forceinline__ void cta_partials(double (&v)[NV], double *part, int 
     for (int t = 0; t < NV; ++t) v[t] = warp_sum(v[t]);
     if (lane == 0) {
 #pragma unroll
-        for (int t = 0; t < NV; ++t) sm[wid][t] = v[t];
+        for (int t = 0; t < NV; ++t) sm[wid][t] = (double)v[t];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -399,31 +395,7 @@ __device__ __forceinline__ void cta_partials(double (&v)[NV], double *part, int 
     }
 }
 
-// ============================================================================ Task 1: skin test
-
-__global__ void __launch_bounds__(MD_TILE) k_skin(DevArgs a)
-{
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    int r = a.tile_rep[blockIdx.x];   // blockDim == MD_TILE
-    const RepDev &R = a.rep[r];
-    double d2 = 0.0;
-    if (s - R.slot_off < R.n_atoms) {
-        double dx = __dsub_rn(a.x[s], a.xb[s]);
-        double dy = __dsub_rn(a.x[(size_t)a.S + s], a.xb[(size_t)a.S + s]);
-        double dz = __dsub_rn(a.x[2 * (size_t)a.S + s], a.xb[2 * (size_t)a.S + s]);
-        d2 = norm2_exact(dx, dy, dz);
-        if (d2 != d2) d2 = 1e300;   // NaN position: force a rebuild, which reports it
-    }
-    for (int o = 16; o > 0; o >>= 1) d2 = fmax(d2, __shfl_xor_sync(0xffffffffu, d2, o));
-    __shared__ double sm[MD_TILE / 32];
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = d2;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sm[w]);
-        if (m > 0.0) atomicMax(&a.rs[r].d2max_bits, (unsigned long long)__double_as_longlong(m));
-    }
-}
+// ============================================================================ Task 1 decision
 
 __global__ void k_decide(DevArgs a, int force, int use_cond, cudaGraphConditionalHandle h)
 {
@@ -590,14 +562,19 @@ __global__ void k_gather(DevArgs a)
     a.cellc[s] = pack_cell(c0, c1, c2);
 }
 
+// FP32 position of slot s about its cell centre lo + (c + 1/2) w32 (see RepDev)
+__device__ __forceinline__ float4 rel_pos3(const RepDev &R, int pc, double x0, double x1, double x2)
+{
+    double c0 = fma((double)cell_x(pc) + 0.5, R.wc[0], R.lo[0]);
+    double c1 = fma((double)cell_y(pc) + 0.5, R.wc[1], R.lo[1]);
+    double c2 = fma((double)cell_z(pc) + 0.5, R.wc[2], R.lo[2]);
+    return make_float4((float)(x0 - c0), (float)(x1 - c1), (float)(x2 - c2), __int_as_float(pc));
+}
+
 __device__ __forceinline__ float4 rel_pos(const DevArgs &a, const RepDev &R, int s)
 {
-    int pc = a.cellc[s];
     size_t S = a.S;
-    double c0 = R.lo[0] + (cell_x(pc) + 0.5) * R.w[0];
-    double c1 = R.lo[1] + (cell_y(pc) + 0.5) * R.w[1];
-    double c2 = R.lo[2] + (cell_z(pc) + 0.5) * R.w[2];
-    return make_float4((float)(a.x[s] - c0), (float)(a.x[S + s] - c1), (float)(a.x[2 * S + s] - c2), __int_as_float(pc));
+    return rel_pos3(R, a.cellc[s], a.x[s], a.x[S + s], a.x[2 * S + s]);
 }
 
 __global__ void k_copyback(DevArgs a)
@@ -652,7 +629,10 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
                 if (q0 < 0 || q0 >= R.nc[0]) { if (!R.per[0]) continue; q0 = (q0 + R.nc[0]) % R.nc[0]; }
                 int key = R.cell_off + (q2 * R.nc[1] + q1) * R.nc[0] + q0;
                 int b = a.cell_start[key], e = b + a.cell_count[key];
-                const float ox = dx * wx, oy = dy * wy, oz = dz * wz;
+                // centre offset of the stencil cell: d w32, plus d dL32 through a periodic face
+                const float ox = fmaf((float)(c0 + dx != q0) * dx, R.dL32[0], dx * wx);
+                const float oy = fmaf((float)(c1 + dy != q1) * dy, R.dL32[1], dy * wy);
+                const float oz = fmaf((float)(c2 + dz != q2) * dz, R.dL32[2], dz * wz);
                 for (int t = b; t < e; ++t) {
                     if (t == s) continue;
                     const float4 pj = a.pos4[t];
@@ -755,29 +735,49 @@ __global__ void k_build_done(DevArgs a)
 
 // ============================================================================ Tasks 2 + 3
 
-__global__ void k_verlet1(DevArgs a)
+// Tasks 2 + 3 for step t, and the displacement test of step t+1's Task 1: the positions
+// x(t+1) written here are the ones the next step's decision examines (Sec. 2.6 rule on
+// max_i |x_i - x_build,i|, FP64, every operation separately rounded).  One CTA = one tile.
+__global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.S) return;
-    int r = a.tile_rep[s / MD_TILE];
+    const int s = blockIdx.x * MD_TILE + threadIdx.x;
+    const int r = a.tile_rep[blockIdx.x];
     const RepDev &R = a.rep[r];
     if (s == R.slot_off) {   // Task 2: the rigid indenter moves by v_ind dt
         RepState &st = a.rs[r];
         st.z_ind = __dadd_rn(st.z_ind, __dmul_rn(R.v_ind, R.dt));
         if (s == 0) { a.st->step += 1; a.st->since_build += 1; }   // after this step's Task 1 decision
     }
-    if (s - R.slot_off >= R.n_atoms) return;
-    size_t S = a.S;
-    if (!a.fixed[s]) {
-        double hk = 0.5 * R.dt * R.acc_per_f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            double v = a.v[k * S + s] + hk * a.F[k * S + s];   // Eq. A12
-            a.v[k * S + s] = v;
-            a.x[k * S + s] += R.dt * v;                         // Eq. A11 with the half-step velocity
+    unsigned long long d2bits = 0ull;
+    if (s - R.slot_off < R.n_atoms) {
+        const size_t S = a.S;
+        double x0 = a.x[s], x1 = a.x[S + s], x2 = a.x[2 * S + s];
+        if (!a.fixed[s]) {
+            const double hk = 0.5 * R.dt * R.acc_per_f;
+            double v0 = fma(hk, a.F[s], a.v[s]);                    // Eq. A12
+            double v1 = fma(hk, a.F[S + s], a.v[S + s]);
+            double v2 = fma(hk, a.F[2 * S + s], a.v[2 * S + s]);
+            a.v[s] = v0; a.v[S + s] = v1; a.v[2 * S + s] = v2;
+            x0 = fma(R.dt, v0, x0); x1 = fma(R.dt, v1, x1); x2 = fma(R.dt, v2, x2);   // Eq. A11
+            a.x[s] = x0; a.x[S + s] = x1; a.x[2 * S + s] = x2;
         }
+        double d2 = norm2_exact(__dsub_rn(x0, a.xb[s]), __dsub_rn(x1, a.xb[S + s]), __dsub_rn(x2, a.xb[2 * S + s]));
+        if (d2 != d2) d2 = 1e300;   // NaN position: force a rebuild, which reports it
+        d2bits = (unsigned long long)__double_as_longlong(d2);   // d2 >= 0: bit order = value order
+        if (a.mixed) a.pos4[s] = rel_pos3(R, a.cellc[s], x0, x1, x2);
     }
-    if (a.mixed) a.pos4[s] = rel_pos(a, R, s);
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(0xffffffffu, d2bits, o);
+        d2bits = t > d2bits ? t : d2bits;
+    }
+    __shared__ unsigned long long sm[MD_TILE / 32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = d2bits;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long m = 0ull;
+        for (int w = 0; w < MD_TILE / 32; ++w) m = sm[w] > m ? sm[w] : m;
+        if (m) atomicMax(&a.rs[r].d2max_bits, m);
+    }
 }
 
 __global__ void k_refresh_pos4(DevArgs a)
@@ -801,11 +801,11 @@ __global__ void __launch_bounds__(256) k_density(DevArgs a, PotDev P)
     RepPair R;
     R.load(a.rep[r]);
     const bool real = s < a.S && (s - R.slot_off) < R.n_atoms;
-    double acc[2] = {0.0, 0.0};
+    using Acc = typename std::conditional<MIXED, float, double>::type;
+    Acc acc[2] = {0, 0};
     const size_t S = a.S;
     if (MIXED) {
-        Pot32 Q;
-        Q.init(P);
+        const Pot32 &Q = static_cast<const Pot32 &>(P.q);
         float rho = 0.f, Ps = 0.f;
         if (real) {
             const float4 pi = a.pos4[s];
@@ -847,7 +847,7 @@ __global__ void __launch_bounds__(256) k_density(DevArgs a, PotDev P)
             Q.embed(rho, F, Fp);
             Q.mterm(Ps, M, Mp);
             a.fm32[s] = make_float2(Fp, Mp);
-            acc[0] = F; acc[1] = M;
+            acc[0] = (Acc)F; acc[1] = (Acc)M;
         }
     } else {
         double rho = 0.0, Ps = 0.0;
@@ -878,7 +878,7 @@ __global__ void __launch_bounds__(256) k_density(DevArgs a, PotDev P)
             embed_64(P, rho, F, Fp);
             mterm_64(P, Ps, M, Mp);
             a.fm64[s] = make_double2(Fp, Mp);
-            acc[0] = F; acc[1] = M;
+            acc[0] = (Acc)F; acc[1] = (Acc)M;
         }
     }
     cta_partials<2>(acc, a.part, a.max_blocks, blockIdx.x);
@@ -897,10 +897,10 @@ __global__ void __launch_bounds__(256) k_force(DevArgs a, PotDev P, int integrat
     R.load(a.rep[r]);
     const bool real = s < a.S && (s - R.slot_off) < R.n_atoms;
     const size_t S = a.S, C = a.C;
-    double fx = 0.0, fy = 0.0, fz = 0.0, e_pair = 0.0, e_mor = 0.0, load = 0.0;
+    using Acc = typename std::conditional<MIXED, float, double>::type;
+    Acc fx = 0, fy = 0, fz = 0, e_pair = 0, e_mor = 0, load = 0;
     if (MIXED) {
-        Pot32 Q;
-        Q.init(P);
+        const Pot32 &Q = static_cast<const Pot32 &>(P.q);
         float gx = 0.f, gy = 0.f, gz = 0.f, ep = 0.f;
         if (real) {
             const float4 pi = a.pos4[s];
@@ -986,7 +986,7 @@ __global__ void __launch_bounds__(256) k_force(DevArgs a, PotDev P, int integrat
             mz += __shfl_xor_sync(0xffffffffu, mz, o);
             em += __shfl_xor_sync(0xffffffffu, em, o);
         }
-        fx += mx; fy += my; fz += mz; e_mor = em; load = -(double)mz;
+        fx += mx; fy += my; fz += mz; e_mor = em; load = -mz;
     } else {
         double gx = 0.0, gy = 0.0, gz = 0.0, ep = 0.0;
         double mx = 0.0, my = 0.0, mz = 0.0, em = 0.0;
@@ -1043,18 +1043,20 @@ __global__ void __launch_bounds__(256) k_force(DevArgs a, PotDev P, int integrat
         }
         fx = gx + mx; fy = gy + my; fz = gz + mz; e_pair = ep; e_mor = em; load = -mz;
     }
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    Acc acc[4] = {0, 0, 0, 0};
     if (real && lane == 0) {
-        a.F[s] = fx; a.F[S + s] = fy; a.F[2 * S + s] = fz;
+        const double Fx = fx, Fy = fy, Fz = fz;
+        a.F[s] = Fx; a.F[S + s] = Fy; a.F[2 * S + s] = Fz;
         double vx = a.v[s], vy = a.v[S + s], vz = a.v[2 * S + s];
         const RepDev &RD = a.rep[r];
-        if (integrate && !a.fixed[s]) {   // Task 5: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2
+        if (integrate && !a.fixed[s]) {   // Task 5: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2 (FP64)
             const double hk = 0.5 * RD.dt * RD.acc_per_f;
-            vx += hk * fx; vy += hk * fy; vz += hk * fz;
+            vx = fma(hk, Fx, vx); vy = fma(hk, Fy, vy); vz = fma(hk, Fz, vz);
             a.v[s] = vx; a.v[S + s] = vy; a.v[2 * S + s] = vz;
         }
         acc[0] = e_pair; acc[1] = e_mor; acc[2] = load;
-        acc[3] = 0.5 * RD.mass * (vx * vx + vy * vy + vz * vz) / MD_ACC;
+        const Acc ux = (Acc)vx, uy = (Acc)vy, uz = (Acc)vz;
+        acc[3] = (Acc)(0.5 / MD_ACC) * (Acc)RD.mass * (ux * ux + uy * uy + uz * uz);
     }
     cta_partials<4>(acc, a.part + 2 * (size_t)a.max_blocks, a.max_blocks, blockIdx.x);
 }
@@ -1093,12 +1095,6 @@ inline unsigned nblk(long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // ============================================================================ launchers
 
-cudaError_t launch_skin(const DevArgs &a, cudaStream_t s)
-{
-    k_skin<<<a.S / MD_TILE, MD_TILE, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_decide(const DevArgs &a, int force, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s)
 {
     k_decide<<<1, 256, 0, s>>>(a, force, use_cond, h);
@@ -1128,7 +1124,7 @@ cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s)
 
 cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s)
 {
-    k_verlet1<<<nblk(a.S, 256), 256, 0, s>>>(a);
+    k_verlet1<<<a.S / MD_TILE, MD_TILE, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -244,7 +244,8 @@ def test_state_roundtrip(md, params):
     e1 = sim.energy(0)
     assert e1["potential"] == pytest.approx(e0["potential"], rel=1e-13)
     # a state set from elsewhere is what the next step starts from
-    o = oracle.Sim(oracle.Potential(params), rep, skin=0.3, x=x, v=v)
+    import dataclasses
+    o = oracle.Sim(oracle.Potential(params), dataclasses.replace(rep, z_indenter0=z), skin=0.3, x=x, v=v)
     sim.step(5)
     o.step(5)
     np.testing.assert_allclose(sim.state(0)[0], o.state()["x"], rtol=0, atol=1e-10)
