@@ -303,7 +303,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
         return fail(nullptr, MD_ERR_ARG, "md_init: precision must be MD_FP64 or MD_MIXED");
     if (!(opt->skin >= 0.0) || opt->rebuild_every < 0)
         return fail(nullptr, MD_ERR_ARG, "md_init: skin must be >= 0 and rebuild_every >= 0");
-    int tpa = opt->tpa ? opt->tpa : (opt->precision == MD_MIXED ? 4 : 4);
+    int tpa = opt->tpa ? opt->tpa : 1;
     int block = opt->block ? opt->block : 128;
     if (!(tpa == 1 || tpa == 2 || tpa == 4 || tpa == 8) || block < 32 || block > 256 || block % 32 ||
         MD_TILE % (block / tpa) != 0)
@@ -399,8 +399,8 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
         }
         cslots += y.n_c;
     }
-    if (slots >= (int64_t)1 << 31 || cells >= (int64_t)1 << 31)
-        INIT_FAIL(fail(h, MD_ERR_ARG, "too many atoms or cells for 32-bit slot indices"));
+    if (slots >= (int64_t)1 << MD_J_BITS || cells >= (int64_t)1 << 31)
+        INIT_FAIL(fail(h, MD_ERR_ARG, "too many atom slots (%lld) for the %d-bit neighbour entries", (long long)slots, MD_J_BITS));
     h->n_cr = real; h->n_c = cslots;
     const int S = (int)slots;
     DevArgs &a = h->a;
@@ -758,7 +758,7 @@ int md_get_neighbors(md_t *h, int32_t r, int32_t which, int32_t *cell_xyz, int32
             int m = std::min(c[i], kmax);
             for (int k = 0; k < m; ++k) {
                 int e = list[(size_t)k * n + i];
-                nbr[(size_t)o * kmax + k] = which ? h->c_orig[e] : orig[e - R.slot_off];
+                nbr[(size_t)o * kmax + k] = which ? h->c_orig[e] : orig[(int)((unsigned)e & MD_J_MASK) - R.slot_off];
             }
         }
     }

@@ -27,6 +27,10 @@
 #define MD_ACC 9.6485332e-3  // 1 eV/(A u) in A/fs^2
 #define MD_KB 8.617333262e-5 // Boltzmann constant, eV/K
 #define MD_CELL_BITS 10      // bits per packed cell coordinate (grids up to 1024 cells per axis)
+// Cr-Cr list entry: slot of the neighbour in the low MD_J_BITS bits, and in the top 6 bits
+// the direction of its stencil cell: bit 0/1 = x-/x+, 2/3 = y-/y+, 4/5 = z-/z+
+#define MD_J_BITS 26
+#define MD_J_MASK ((1u << MD_J_BITS) - 1u)
 
 // error bits raised by kernels (device word, read by the host after md_step)
 enum { MDE_OVERFLOW = 1, MDE_LOST = 2, MDE_SKIN = 4, MDE_COVERFLOW = 8 };
@@ -44,6 +48,7 @@ struct PotF32 {
     float F_o, n, inv_rho_e, alpha, inv_P_e, rc2;
     int32_t tabulated, nf, nm;
     const float4 *tf, *tp, *tm;
+    const float4 *tfp;   // f and Phi coefficients interleaved: [2k] = f, [2k + 1] = Phi
 };
 
 // potential, passed by value to kernels (lives in the constant bank)

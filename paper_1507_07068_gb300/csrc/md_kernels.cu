@@ -136,15 +136,20 @@ int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs
     fill_table(nf, p->r_min, p->rc, [&](long double r, long double &v, long double &dv) { H.f(r, v, dv); }, tf);
     fill_table(nf, p->r_min, p->rc, [&](long double r, long double &v, long double &dv) { H.phi(r, v, dv); }, tp);
     fill_table(nm, p->r_min, p->rc_morse, [&](long double r, long double &v, long double &dv) { H.morse(r, v, dv); }, tm);
-    size_t ntot = (size_t)2 * nf + nm;
+    size_t ntot = (size_t)4 * nf + nm;   // FP64: f, Phi, Morse (+ unused); FP32 adds f/Phi interleaved
     std::vector<Cf64> all;
     all.reserve(ntot);
     all.insert(all.end(), tf.begin(), tf.end());
     all.insert(all.end(), tp.begin(), tp.end());
     all.insert(all.end(), tm.begin(), tm.end());
     std::vector<float4> all32(ntot);
-    for (size_t k = 0; k < ntot; ++k)
+    for (size_t k = 0; k < (size_t)2 * nf + nm; ++k)
         all32[k] = make_float4((float)all[k].x, (float)all[k].y, (float)all[k].z, (float)all[k].w);
+    for (int k = 0; k < nf; ++k) {
+        all32[2 * nf + nm + 2 * k] = all32[k];
+        all32[2 * nf + nm + 2 * k + 1] = all32[nf + k];
+    }
+    all.resize(ntot);
     if (cudaMalloc(d_tabs64, ntot * sizeof(Cf64)) != cudaSuccess ||
         cudaMalloc(d_tabs32, ntot * sizeof(float4)) != cudaSuccess) {
         snprintf(err, errlen, "cudaMalloc of potential tables failed");
@@ -170,6 +175,7 @@ int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs
     q.F_o = (float)P->F_o; q.n = (float)P->n; q.inv_rho_e = (float)(1.0 / P->rho_e); q.alpha = (float)P->alpha;
     q.inv_P_e = (float)(1.0 / P->P_e); q.rc2 = (float)P->rc2;
     q.tabulated = P->tabulated; q.nf = nf; q.nm = nm; q.tf = P->tf32; q.tp = P->tp32; q.tm = P->tm32;
+    q.tfp = *d_tabs32 + 2 * nf + nm;
     return MD_OK;
 }
 
@@ -313,45 +319,6 @@ struct Pot32 : PotF32 {   // the FP32 constants (filled on the host) with the FP
         Mp = 2.0f * alpha * inv_P_e * u * (1.0f - u * u) * e;
     }
 };
-
-// per-thread copy of the replica fields the pair kernels use
-struct RepPair {
-    int per0, per1, per2, n0, n1, n2;
-    float w0, w1, w2, dL0, dL1, dL2;
-    double L0, L1, L2;
-    int slot_off, n_atoms;
-    __device__ __forceinline__ void load(const RepDev &R)
-    {
-        per0 = R.per[0]; per1 = R.per[1]; per2 = R.per[2];
-        n0 = R.nc[0]; n1 = R.nc[1]; n2 = R.nc[2];
-        w0 = R.w32[0]; w1 = R.w32[1]; w2 = R.w32[2];
-        dL0 = R.dL32[0]; dL1 = R.dL32[1]; dL2 = R.dL32[2];
-        L0 = R.L[0]; L1 = R.L[1]; L2 = R.L[2];
-        slot_off = R.slot_off; n_atoms = R.n_atoms;
-    }
-};
-
-// one axis of x_j - x_i from cell-relative FP32 coordinates: the two cell centres are
-// d cells apart (d = cj - ci); across a periodic boundary the image is one period away,
-// i.e. (d -+ n) w32 -+ dL (the centres are w32 apart, the period is n w32 + dL)
-__device__ __forceinline__ float axis_disp(float pj, float pi, int d, int per, int n, float w, float dL)
-{
-    float m = 0.0f;
-    if (per) {
-        if (d > 1) { d -= n; m = -1.0f; }
-        else if (d < -1) { d += n; m = 1.0f; }
-    }
-    return fmaf(m, dL, fmaf((float)d, w, pj - pi));
-}
-
-__device__ __forceinline__ void rel_disp(const float4 &pi, int ci, const float4 &pj, const RepPair &R,
-                                         float &dx, float &dy, float &dz)
-{
-    int cj = __float_as_int(pj.w);
-    dx = axis_disp(pj.x, pi.x, cell_x(cj) - cell_x(ci), R.per0, R.n0, R.w0, R.dL0);
-    dy = axis_disp(pj.y, pi.y, cell_y(cj) - cell_y(ci), R.per1, R.n1, R.w1, R.dL1);
-    dz = axis_disp(pj.z, pi.z, cell_z(cj) - cell_z(ci), R.per2, R.n2, R.w2, R.dL2);
-}
 
 __device__ __forceinline__ double mi64(double d, int per, double L)
 {
@@ -629,6 +596,8 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
                 if (q0 < 0 || q0 >= R.nc[0]) { if (!R.per[0]) continue; q0 = (q0 + R.nc[0]) % R.nc[0]; }
                 int key = R.cell_off + (q2 * R.nc[1] + q1) * R.nc[0] + q0;
                 int b = a.cell_start[key], e = b + a.cell_count[key];
+                const unsigned dir = (dx < 0 ? 1u : 0u) | (dx > 0 ? 2u : 0u) | (dy < 0 ? 4u : 0u) | (dy > 0 ? 8u : 0u) |
+                                     (dz < 0 ? 16u : 0u) | (dz > 0 ? 32u : 0u);
                 // centre offset of the stencil cell: d w32, plus d dL32 through a periodic face
                 const float ox = fmaf((float)(c0 + dx != q0) * dx, R.dL32[0], dx * wx);
                 const float oy = fmaf((float)(c1 + dy != q1) * dy, R.dL32[1], dy * wy);
@@ -648,7 +617,7 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
                         in = norm2_exact(ddx, ddy, ddz) < a.cut2;
                     }
                     if (in) {
-                        if (m < a.kmax) a.nbr[(size_t)m * S + s] = t;
+                        if (m < a.kmax) a.nbr[(size_t)m * S + s] = (int32_t)((unsigned)t | (dir << MD_J_BITS));
                         ++m;
                     }
                 }
@@ -789,274 +758,369 @@ __global__ void k_refresh_pos4(DevArgs a)
     a.pos4[s] = rel_pos(a, R, s);
 }
 
-// ============================================================================ Task 4a
+// ============================================================================ Task 4, mixed precision
+//
+// Geometry of a pair from FP32 cell-relative positions: x_j - x_i = (p_j - p_i) + offset,
+// the offset being the centre-to-centre vector of the two cells, read from a 64-entry
+// table indexed by the direction bits of the list entry (exact multiples of w32); a pair
+// that crosses a periodic face (atom i in an edge cell, direction bit towards that face)
+// adds -+dL32 on that axis.
 
-template <int TPA, bool MIXED>
-__global__ void __launch_bounds__(256) k_density(DevArgs a, PotDev P)
+struct PairGeom {
+    unsigned xmask;          // direction bits that cross a periodic face for this atom
+    float dL0, dL1, dL2;
+};
+
+__device__ __forceinline__ void fill_offsets(float4 *sm_off, const RepDev &R)
 {
+    for (int c = threadIdx.x; c < 64; c += blockDim.x) {
+        float ox = (c & 1 ? -R.w32[0] : 0.f) + (c & 2 ? R.w32[0] : 0.f);
+        float oy = (c & 4 ? -R.w32[1] : 0.f) + (c & 8 ? R.w32[1] : 0.f);
+        float oz = (c & 16 ? -R.w32[2] : 0.f) + (c & 32 ? R.w32[2] : 0.f);
+        sm_off[c] = make_float4(ox, oy, oz, 0.f);
+    }
+}
+
+__device__ __forceinline__ PairGeom pair_geom(const RepDev &R, int ci)
+{
+    PairGeom G;
+    const int c0 = cell_x(ci), c1 = cell_y(ci), c2 = cell_z(ci);
+    G.xmask = (R.per[0] && c0 == 0 ? 1u : 0u) | (R.per[0] && c0 == R.nc[0] - 1 ? 2u : 0u) |
+              (R.per[1] && c1 == 0 ? 4u : 0u) | (R.per[1] && c1 == R.nc[1] - 1 ? 8u : 0u) |
+              (R.per[2] && c2 == 0 ? 16u : 0u) | (R.per[2] && c2 == R.nc[2] - 1 ? 32u : 0u);
+    G.dL0 = R.dL32[0]; G.dL1 = R.dL32[1]; G.dL2 = R.dL32[2];
+    return G;
+}
+
+__device__ __forceinline__ void disp(const float4 &pi, const float4 &pj, unsigned dir, const float4 *sm_off,
+                                     const PairGeom &G, float &dx, float &dy, float &dz)
+{
+    const float4 o = sm_off[dir];
+    dx = (pj.x - pi.x) + o.x;
+    dy = (pj.y - pi.y) + o.y;
+    dz = (pj.z - pi.z) + o.z;
+    const unsigned c = dir & G.xmask;
+    if (c) {   // through a periodic face: the period is nc w32 + dL
+        dx += (c & 1 ? -G.dL0 : 0.f) + (c & 2 ? G.dL0 : 0.f);
+        dy += (c & 4 ? -G.dL1 : 0.f) + (c & 8 ? G.dL1 : 0.f);
+        dz += (c & 16 ? -G.dL2 : 0.f) + (c & 32 ? G.dL2 : 0.f);
+    }
+}
+
+// f and Phi from the interleaved FP32 tables (one index computation); value of f only, or
+// value and slope of both
+__device__ __forceinline__ float f_only(const Pot32 &Q, float r)
+{
+    if (!Q.tabulated) { float v, dv; Q.f(r, v, dv); return v; }
+    const float s = fmaf(r, Q.inv_hf, -Q.rmin_s_f);
+    const float kf = fminf(fmaxf(floorf(s), 0.0f), (float)(Q.nf - 1));
+    const float t = s - kf;
+    const float4 c = __ldg(&Q.tfp[2 * (int)kf]);
+    return fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
+}
+
+__device__ __forceinline__ void f_phi(const Pot32 &Q, float r, float &f, float &df, float &ph, float &dph)
+{
+    if (!Q.tabulated) { Q.f(r, f, df); Q.phi(r, ph, dph); return; }
+    const float s = fmaf(r, Q.inv_hf, -Q.rmin_s_f);
+    const float kf = fminf(fmaxf(floorf(s), 0.0f), (float)(Q.nf - 1));
+    const float t = s - kf;
+    const int k = 2 * (int)kf;
+    const float4 a = __ldg(&Q.tfp[k]), b = __ldg(&Q.tfp[k + 1]);
+    f = fmaf(fmaf(fmaf(a.w, t, a.z), t, a.y), t, a.x);
+    df = fmaf(fmaf(3.0f * a.w, t, 2.0f * a.z), t, a.y) * Q.inv_hf;
+    ph = fmaf(fmaf(fmaf(b.w, t, b.z), t, b.y), t, b.x);
+    dph = fmaf(fmaf(3.0f * b.w, t, 2.0f * b.z), t, b.y) * Q.inv_hf;
+}
+
+// Task 4a (Eqs. A2-A3): rho_i, P_i over the list entries within rc; F'(rho_i), M'(P_i) stored,
+// F(rho_i), M(P_i) into the CTA's energy partials.  MD_UNROLL entries per lane are loaded
+// (list entry, then position) before any is used.
+template <int TPA>
+__global__ void __launch_bounds__(256) k_density_mixed(DevArgs a, PotDev P)
+{
+    __shared__ float4 sm_off[64];
     const int A = blockDim.x / TPA;
     const int g = threadIdx.x / TPA, lane = threadIdx.x % TPA;
     const int s = blockIdx.x * A + g;
-    const int r = a.tile_rep[(blockIdx.x * A) / MD_TILE];
-    RepPair R;
-    R.load(a.rep[r]);
-    const bool real = s < a.S && (s - R.slot_off) < R.n_atoms;
-    using Acc = typename std::conditional<MIXED, float, double>::type;
-    Acc acc[2] = {0, 0};
+    const RepDev &R = a.rep[a.tile_rep[(blockIdx.x * A) / MD_TILE]];
+    fill_offsets(sm_off, R);
+    __syncthreads();
+    const Pot32 &Q = static_cast<const Pot32 &>(P.q);
+    const bool real = (s - R.slot_off) < R.n_atoms;
     const size_t S = a.S;
-    if (MIXED) {
-        const Pot32 &Q = static_cast<const Pot32 &>(P.q);
-        float rho = 0.f, Ps = 0.f;
-        if (real) {
-            const float4 pi = a.pos4[s];
-            const int ci = __float_as_int(pi.w);
-            const int n = a.cnt[s];
-            // U list entries and their positions are loaded before any is used, so each lane
-            // keeps 2U independent loads in flight
-            for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
-                int jj[MD_UNROLL];
+    float rho = 0.f, Ps = 0.f;
+    if (real) {
+        const float4 pi = a.pos4[s];
+        const PairGeom G = pair_geom(R, __float_as_int(pi.w));
+        const int n = a.cnt[s];
+        for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
+            unsigned e[MD_UNROLL];
 #pragma unroll
-                for (int u = 0; u < MD_UNROLL; ++u) {
-                    const int k = k0 + u * TPA;
-                    jj[u] = k < n ? __ldg(&a.nbr[(size_t)k * S + s]) : s;
-                }
-                float4 pj[MD_UNROLL];
-#pragma unroll
-                for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&a.pos4[jj[u]]);
-#pragma unroll
-                for (int u = 0; u < MD_UNROLL; ++u) {
-                    float dx, dy, dz;
-                    rel_disp(pi, ci, pj[u], R, dx, dy, dz);
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    if (k0 + u * TPA < n && r2 < Q.rc2) {
-                        float f, df;
-                        Q.f(sqrtf(r2), f, df);
-                        rho += f;
-                        Ps = fmaf(f, f, Ps);
-                    }
-                }
+            for (int u = 0; u < MD_UNROLL; ++u) {
+                const int k = k0 + u * TPA;
+                e[u] = k < n ? (unsigned)__ldg(&a.nbr[(size_t)k * S + s]) : (unsigned)s;
             }
-        }
+            float4 pj[MD_UNROLL];
 #pragma unroll
-        for (int o = TPA / 2; o > 0; o >>= 1) {
-            rho += __shfl_xor_sync(0xffffffffu, rho, o);
-            Ps += __shfl_xor_sync(0xffffffffu, Ps, o);
-        }
-        if (real && lane == 0) {
-            float F, Fp, M, Mp;
-            Q.embed(rho, F, Fp);
-            Q.mterm(Ps, M, Mp);
-            a.fm32[s] = make_float2(Fp, Mp);
-            acc[0] = (Acc)F; acc[1] = (Acc)M;
-        }
-    } else {
-        double rho = 0.0, Ps = 0.0;
-        if (real) {
-            const double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
-            const int n = a.cnt[s];
-            for (int k = lane; k < n; k += TPA) {
-                const int j = __ldg(&a.nbr[(size_t)k * S + s]);
-                const double dx = mi64(a.x[j] - xi, R.per0, R.L0);
-                const double dy = mi64(a.x[S + j] - yi, R.per1, R.L1);
-                const double dz = mi64(a.x[2 * S + j] - zi, R.per2, R.L2);
-                const double r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < P.rc2) {
-                    double f, df;
-                    f_64(P, sqrt(r2), f, df);
+            for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&a.pos4[e[u] & MD_J_MASK]);
+#pragma unroll
+            for (int u = 0; u < MD_UNROLL; ++u) {
+                float dx, dy, dz;
+                disp(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (k0 + u * TPA < n && r2 < Q.rc2) {
+                    const float f = f_only(Q, sqrtf(r2));
                     rho += f;
-                    Ps += f * f;
+                    Ps = fmaf(f, f, Ps);
                 }
             }
         }
+    }
 #pragma unroll
-        for (int o = TPA / 2; o > 0; o >>= 1) {
-            rho += __shfl_xor_sync(0xffffffffu, rho, o);
-            Ps += __shfl_xor_sync(0xffffffffu, Ps, o);
-        }
-        if (real && lane == 0) {
-            double F, Fp, M, Mp;
-            embed_64(P, rho, F, Fp);
-            mterm_64(P, Ps, M, Mp);
-            a.fm64[s] = make_double2(Fp, Mp);
-            acc[0] = (Acc)F; acc[1] = (Acc)M;
-        }
+    for (int o = TPA / 2; o > 0; o >>= 1) {
+        rho += __shfl_xor_sync(0xffffffffu, rho, o);
+        Ps += __shfl_xor_sync(0xffffffffu, Ps, o);
+    }
+    float acc[2] = {0.f, 0.f};
+    if (real && lane == 0) {
+        float F, Fp, M, Mp;
+        Q.embed(rho, F, Fp);
+        Q.mterm(Ps, M, Mp);
+        a.fm32[s] = make_float2(Fp, Mp);
+        acc[0] = F; acc[1] = M;
     }
     cta_partials<2>(acc, a.part, a.max_blocks, blockIdx.x);
 }
 
-// ============================================================================ Task 4b,c + Task 5
-
-template <int TPA, bool MIXED>
-__global__ void __launch_bounds__(256) k_force(DevArgs a, PotDev P, int integrate)
+// Task 4b,c (Eq. (1) with the M term, Eqs. A6-A10; Morse Eqs. A5, A9) and Task 5 (the
+// closing half kick, FP64).  The force on i from j is coef * (x_j - x_i), coef = [(F'_i +
+// F'_j) f' + (M'_i + M'_j) 2 f f' + Phi'] / r.
+template <int TPA>
+__global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int integrate)
 {
+    __shared__ float4 sm_off[64];
     const int A = blockDim.x / TPA;
     const int g = threadIdx.x / TPA, lane = threadIdx.x % TPA;
     const int s = blockIdx.x * A + g;
     const int r = a.tile_rep[(blockIdx.x * A) / MD_TILE];
-    RepPair R;
-    R.load(a.rep[r]);
-    const bool real = s < a.S && (s - R.slot_off) < R.n_atoms;
+    const RepDev &R = a.rep[r];
+    fill_offsets(sm_off, R);
+    __syncthreads();
+    const Pot32 &Q = static_cast<const Pot32 &>(P.q);
+    const bool real = (s - R.slot_off) < R.n_atoms;
     const size_t S = a.S, C = a.C;
-    using Acc = typename std::conditional<MIXED, float, double>::type;
-    Acc fx = 0, fy = 0, fz = 0, e_pair = 0, e_mor = 0, load = 0;
-    if (MIXED) {
-        const Pot32 &Q = static_cast<const Pot32 &>(P.q);
-        float gx = 0.f, gy = 0.f, gz = 0.f, ep = 0.f;
-        if (real) {
-            const float4 pi = a.pos4[s];
-            const int ci = __float_as_int(pi.w);
-            const float2 fmi = a.fm32[s];
-            const int n = a.cnt[s];
-            for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
-                int jj[MD_UNROLL];
+    float gx = 0.f, gy = 0.f, gz = 0.f, ep = 0.f;
+    float mx = 0.f, my = 0.f, mz = 0.f, em = 0.f;
+    if (real) {
+        const float4 pi = a.pos4[s];
+        const PairGeom G = pair_geom(R, __float_as_int(pi.w));
+        const float2 fmi = a.fm32[s];
+        const int n = a.cnt[s];
+        for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
+            unsigned e[MD_UNROLL];
 #pragma unroll
-                for (int u = 0; u < MD_UNROLL; ++u) {
-                    const int k = k0 + u * TPA;
-                    jj[u] = k < n ? __ldg(&a.nbr[(size_t)k * S + s]) : s;
-                }
-                float4 pjv[MD_UNROLL];
-                float2 fmv[MD_UNROLL];
+            for (int u = 0; u < MD_UNROLL; ++u) {
+                const int k = k0 + u * TPA;
+                e[u] = k < n ? (unsigned)__ldg(&a.nbr[(size_t)k * S + s]) : (unsigned)s;
+            }
+            float4 pj[MD_UNROLL];
+            float2 fmj[MD_UNROLL];
 #pragma unroll
-                for (int u = 0; u < MD_UNROLL; ++u) {
-                    pjv[u] = __ldg(&a.pos4[jj[u]]);
-                    fmv[u] = __ldg(&a.fm32[jj[u]]);
-                }
+            for (int u = 0; u < MD_UNROLL; ++u) {
+                const unsigned j = e[u] & MD_J_MASK;
+                pj[u] = __ldg(&a.pos4[j]);
+                fmj[u] = __ldg(&a.fm32[j]);
+            }
 #pragma unroll
-                for (int u = 0; u < MD_UNROLL; ++u) {
-                const float4 pj = pjv[u];
+            for (int u = 0; u < MD_UNROLL; ++u) {
                 float dx, dy, dz;
-                rel_disp(pi, ci, pj, R, dx, dy, dz);
+                disp(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 if (k0 + u * TPA < n && r2 < Q.rc2) {
-                    const float2 fmj = fmv[u];
                     const float rinv = rsqrtf(r2);
-                    const float rr = r2 * rinv;
                     float f, df, ph, dph;
-                    Q.f(rr, f, df);
-                    Q.phi(rr, ph, dph);
-                    // Eq. (1) with the M term: coef * (x_j - x_i)/r is the force on i
-                    const float coef = fmaf(fmi.x + fmj.x, df, fmaf((fmi.y + fmj.y) * 2.0f * f, df, dph)) * rinv;
+                    f_phi(Q, r2 * rinv, f, df, ph, dph);
+                    const float coef = fmaf(fmi.x + fmj[u].x, df, fmaf((fmi.y + fmj[u].y) * 2.0f * f, df, dph)) * rinv;
                     gx = fmaf(coef, dx, gx);
                     gy = fmaf(coef, dy, gy);
                     gz = fmaf(coef, dz, gz);
                     ep = fmaf(0.5f, ph, ep);
                 }
-                }
             }
         }
-#pragma unroll
-        for (int o = TPA / 2; o > 0; o >>= 1) {
-            gx += __shfl_xor_sync(0xffffffffu, gx, o);
-            gy += __shfl_xor_sync(0xffffffffu, gy, o);
-            gz += __shfl_xor_sync(0xffffffffu, gz, o);
-            ep += __shfl_xor_sync(0xffffffffu, ep, o);
-        }
-        fx = gx; fy = gy; fz = gz; e_pair = ep;
-        // Cr-C (Morse): FP64 geometry, FP32 potential
-        float mx = 0.f, my = 0.f, mz = 0.f, em = 0.f;
-        if (real) {
-            const int nc = a.cntc[s];
-            if (nc > 0) {
-                const double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
-                const double z_ind = a.rs[r].z_ind;
-                for (int k = lane; k < nc; k += TPA) {
-                    const int c = __ldg(&a.nbrc[(size_t)k * S + s]);
-                    const double ddx = mi64(a.xc0[c] - xi, R.per0, R.L0);
-                    const double ddy = mi64(a.xc0[C + c] - yi, R.per1, R.L1);
-                    const double ddz = mi64(a.xc0[2 * C + c] + z_ind - zi, R.per2, R.L2);
-                    const double y2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    if (y2 < P.rcm2) {
-                        const float yinv = rsqrtf((float)y2);
-                        const float y = (float)y2 * yinv;
-                        float v, dv;
-                        Q.morse(y, v, dv);
-                        const float c1 = dv * yinv;
-                        mx = fmaf(c1, (float)ddx, mx);
-                        my = fmaf(c1, (float)ddy, my);
-                        mz = fmaf(c1, (float)ddz, mz);
-                        em += v;
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int o = TPA / 2; o > 0; o >>= 1) {
-            mx += __shfl_xor_sync(0xffffffffu, mx, o);
-            my += __shfl_xor_sync(0xffffffffu, my, o);
-            mz += __shfl_xor_sync(0xffffffffu, mz, o);
-            em += __shfl_xor_sync(0xffffffffu, em, o);
-        }
-        fx += mx; fy += my; fz += mz; e_mor = em; load = -mz;
-    } else {
-        double gx = 0.0, gy = 0.0, gz = 0.0, ep = 0.0;
-        double mx = 0.0, my = 0.0, mz = 0.0, em = 0.0;
-        if (real) {
+        // Cr-C (Morse): FP64 geometry of the few near-indenter pairs, FP32 potential
+        const int nc = a.cntc[s];
+        if (nc > 0) {
             const double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
-            const double2 fmi = a.fm64[s];
-            const int n = a.cnt[s];
-            for (int k = lane; k < n; k += TPA) {
-                const int j = __ldg(&a.nbr[(size_t)k * S + s]);
-                const double dx = mi64(a.x[j] - xi, R.per0, R.L0);
-                const double dy = mi64(a.x[S + j] - yi, R.per1, R.L1);
-                const double dz = mi64(a.x[2 * S + j] - zi, R.per2, R.L2);
-                const double r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < P.rc2) {
-                    const double2 fmj = a.fm64[j];
-                    const double rr = sqrt(r2);
-                    double f, df, ph, dph;
-                    f_64(P, rr, f, df);
-                    phi_64(P, rr, ph, dph);
-                    const double coef = ((fmi.x + fmj.x) * df + (fmi.y + fmj.y) * 2.0 * f * df + dph) / rr;
-                    gx += coef * dx; gy += coef * dy; gz += coef * dz;
-                    ep += 0.5 * ph;
-                }
-            }
-            const int nc = a.cntc[s];
-            if (nc > 0) {
-                const double z_ind = a.rs[r].z_ind;
-                for (int k = lane; k < nc; k += TPA) {
-                    const int c = __ldg(&a.nbrc[(size_t)k * S + s]);
-                    const double ddx = mi64(a.xc0[c] - xi, R.per0, R.L0);
-                    const double ddy = mi64(a.xc0[C + c] - yi, R.per1, R.L1);
-                    const double ddz = mi64(a.xc0[2 * C + c] + z_ind - zi, R.per2, R.L2);
-                    const double y2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    if (y2 < P.rcm2) {
-                        const double y = sqrt(y2);
-                        double v, dv;
-                        morse_64(P, y, v, dv);
-                        mx += dv * ddx / y; my += dv * ddy / y; mz += dv * ddz / y;
-                        em += v;
-                    }
+            const double z_ind = a.rs[r].z_ind;
+            for (int k = lane; k < nc; k += TPA) {
+                const int c = __ldg(&a.nbrc[(size_t)k * S + s]);
+                const double ddx = mi64(a.xc0[c] - xi, R.per[0], R.L[0]);
+                const double ddy = mi64(a.xc0[C + c] - yi, R.per[1], R.L[1]);
+                const double ddz = mi64(a.xc0[2 * C + c] + z_ind - zi, R.per[2], R.L[2]);
+                const double y2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                if (y2 < P.rcm2) {
+                    const float yinv = rsqrtf((float)y2);
+                    float v, dv;
+                    Q.morse((float)y2 * yinv, v, dv);
+                    const float c1 = dv * yinv;
+                    mx = fmaf(c1, (float)ddx, mx);
+                    my = fmaf(c1, (float)ddy, my);
+                    mz = fmaf(c1, (float)ddz, mz);
+                    em += v;
                 }
             }
         }
-#pragma unroll
-        for (int o = TPA / 2; o > 0; o >>= 1) {
-            gx += __shfl_xor_sync(0xffffffffu, gx, o);
-            gy += __shfl_xor_sync(0xffffffffu, gy, o);
-            gz += __shfl_xor_sync(0xffffffffu, gz, o);
-            ep += __shfl_xor_sync(0xffffffffu, ep, o);
-            mx += __shfl_xor_sync(0xffffffffu, mx, o);
-            my += __shfl_xor_sync(0xffffffffu, my, o);
-            mz += __shfl_xor_sync(0xffffffffu, mz, o);
-            em += __shfl_xor_sync(0xffffffffu, em, o);
-        }
-        fx = gx + mx; fy = gy + my; fz = gz + mz; e_pair = ep; e_mor = em; load = -mz;
     }
-    Acc acc[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int o = TPA / 2; o > 0; o >>= 1) {
+        gx += __shfl_xor_sync(0xffffffffu, gx, o);
+        gy += __shfl_xor_sync(0xffffffffu, gy, o);
+        gz += __shfl_xor_sync(0xffffffffu, gz, o);
+        ep += __shfl_xor_sync(0xffffffffu, ep, o);
+        mx += __shfl_xor_sync(0xffffffffu, mx, o);
+        my += __shfl_xor_sync(0xffffffffu, my, o);
+        mz += __shfl_xor_sync(0xffffffffu, mz, o);
+        em += __shfl_xor_sync(0xffffffffu, em, o);
+    }
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
     if (real && lane == 0) {
-        const double Fx = fx, Fy = fy, Fz = fz;
+        const double Fx = gx + mx, Fy = gy + my, Fz = gz + mz;
         a.F[s] = Fx; a.F[S + s] = Fy; a.F[2 * S + s] = Fz;
         double vx = a.v[s], vy = a.v[S + s], vz = a.v[2 * S + s];
-        const RepDev &RD = a.rep[r];
         if (integrate && !a.fixed[s]) {   // Task 5: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2 (FP64)
-            const double hk = 0.5 * RD.dt * RD.acc_per_f;
+            const double hk = 0.5 * R.dt * R.acc_per_f;
             vx = fma(hk, Fx, vx); vy = fma(hk, Fy, vy); vz = fma(hk, Fz, vz);
             a.v[s] = vx; a.v[S + s] = vy; a.v[2 * S + s] = vz;
         }
-        acc[0] = e_pair; acc[1] = e_mor; acc[2] = load;
-        const Acc ux = (Acc)vx, uy = (Acc)vy, uz = (Acc)vz;
-        acc[3] = (Acc)(0.5 / MD_ACC) * (Acc)RD.mass * (ux * ux + uy * uy + uz * uz);
+        const float ux = (float)vx, uy = (float)vy, uz = (float)vz;
+        acc[0] = ep; acc[1] = em; acc[2] = -mz;
+        acc[3] = (float)(0.5 / MD_ACC) * (float)R.mass * (ux * ux + uy * uy + uz * uz);
+    }
+    cta_partials<4>(acc, a.part + 2 * (size_t)a.max_blocks, a.max_blocks, blockIdx.x);
+}
+
+// ============================================================================ Task 4, FP64
+
+template <int TPA>
+__global__ void __launch_bounds__(256) k_density_fp64(DevArgs a, PotDev P)
+{
+    const int A = blockDim.x / TPA;
+    const int g = threadIdx.x / TPA, lane = threadIdx.x % TPA;
+    const int s = blockIdx.x * A + g;
+    const RepDev &R = a.rep[a.tile_rep[(blockIdx.x * A) / MD_TILE]];
+    const bool real = (s - R.slot_off) < R.n_atoms;
+    const size_t S = a.S;
+    double rho = 0.0, Ps = 0.0;
+    if (real) {
+        const double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
+        const int n = a.cnt[s];
+        for (int k = lane; k < n; k += TPA) {
+            const int j = (int)((unsigned)__ldg(&a.nbr[(size_t)k * S + s]) & MD_J_MASK);
+            const double dx = mi64(a.x[j] - xi, R.per[0], R.L[0]);
+            const double dy = mi64(a.x[S + j] - yi, R.per[1], R.L[1]);
+            const double dz = mi64(a.x[2 * S + j] - zi, R.per[2], R.L[2]);
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < P.rc2) {
+                double f, df;
+                f_64(P, sqrt(r2), f, df);
+                rho += f;
+                Ps += f * f;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = TPA / 2; o > 0; o >>= 1) {
+        rho += __shfl_xor_sync(0xffffffffu, rho, o);
+        Ps += __shfl_xor_sync(0xffffffffu, Ps, o);
+    }
+    double acc[2] = {0.0, 0.0};
+    if (real && lane == 0) {
+        double F, Fp, M, Mp;
+        embed_64(P, rho, F, Fp);
+        mterm_64(P, Ps, M, Mp);
+        a.fm64[s] = make_double2(Fp, Mp);
+        acc[0] = F; acc[1] = M;
+    }
+    cta_partials<2>(acc, a.part, a.max_blocks, blockIdx.x);
+}
+
+template <int TPA>
+__global__ void __launch_bounds__(256) k_force_fp64(DevArgs a, PotDev P, int integrate)
+{
+    const int A = blockDim.x / TPA;
+    const int g = threadIdx.x / TPA, lane = threadIdx.x % TPA;
+    const int s = blockIdx.x * A + g;
+    const int r = a.tile_rep[(blockIdx.x * A) / MD_TILE];
+    const RepDev &R = a.rep[r];
+    const bool real = (s - R.slot_off) < R.n_atoms;
+    const size_t S = a.S, C = a.C;
+    double gx = 0.0, gy = 0.0, gz = 0.0, ep = 0.0;
+    double mx = 0.0, my = 0.0, mz = 0.0, em = 0.0;
+    if (real) {
+        const double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
+        const double2 fmi = a.fm64[s];
+        const int n = a.cnt[s];
+        for (int k = lane; k < n; k += TPA) {
+            const int j = (int)((unsigned)__ldg(&a.nbr[(size_t)k * S + s]) & MD_J_MASK);
+            const double dx = mi64(a.x[j] - xi, R.per[0], R.L[0]);
+            const double dy = mi64(a.x[S + j] - yi, R.per[1], R.L[1]);
+            const double dz = mi64(a.x[2 * S + j] - zi, R.per[2], R.L[2]);
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < P.rc2) {
+                const double2 fmj = a.fm64[j];
+                const double rr = sqrt(r2);
+                double f, df, ph, dph;
+                f_64(P, rr, f, df);
+                phi_64(P, rr, ph, dph);
+                const double coef = ((fmi.x + fmj.x) * df + (fmi.y + fmj.y) * 2.0 * f * df + dph) / rr;
+                gx += coef * dx; gy += coef * dy; gz += coef * dz;
+                ep += 0.5 * ph;
+            }
+        }
+        const int nc = a.cntc[s];
+        if (nc > 0) {
+            const double z_ind = a.rs[r].z_ind;
+            for (int k = lane; k < nc; k += TPA) {
+                const int c = __ldg(&a.nbrc[(size_t)k * S + s]);
+                const double ddx = mi64(a.xc0[c] - xi, R.per[0], R.L[0]);
+                const double ddy = mi64(a.xc0[C + c] - yi, R.per[1], R.L[1]);
+                const double ddz = mi64(a.xc0[2 * C + c] + z_ind - zi, R.per[2], R.L[2]);
+                const double y2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                if (y2 < P.rcm2) {
+                    const double y = sqrt(y2);
+                    double v, dv;
+                    morse_64(P, y, v, dv);
+                    mx += dv * ddx / y; my += dv * ddy / y; mz += dv * ddz / y;
+                    em += v;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = TPA / 2; o > 0; o >>= 1) {
+        gx += __shfl_xor_sync(0xffffffffu, gx, o);
+        gy += __shfl_xor_sync(0xffffffffu, gy, o);
+        gz += __shfl_xor_sync(0xffffffffu, gz, o);
+        ep += __shfl_xor_sync(0xffffffffu, ep, o);
+        mx += __shfl_xor_sync(0xffffffffu, mx, o);
+        my += __shfl_xor_sync(0xffffffffu, my, o);
+        mz += __shfl_xor_sync(0xffffffffu, mz, o);
+        em += __shfl_xor_sync(0xffffffffu, em, o);
+    }
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (real && lane == 0) {
+        const double Fx = gx + mx, Fy = gy + my, Fz = gz + mz;
+        a.F[s] = Fx; a.F[S + s] = Fy; a.F[2 * S + s] = Fz;
+        double vx = a.v[s], vy = a.v[S + s], vz = a.v[2 * S + s];
+        if (integrate && !a.fixed[s]) {   // Task 5: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2
+            const double hk = 0.5 * R.dt * R.acc_per_f;
+            vx += hk * Fx; vy += hk * Fy; vz += hk * Fz;
+            a.v[s] = vx; a.v[S + s] = vy; a.v[2 * S + s] = vz;
+        }
+        acc[0] = ep; acc[1] = em; acc[2] = -mz;
+        acc[3] = 0.5 * R.mass * (vx * vx + vy * vy + vz * vz) / MD_ACC;
     }
     cta_partials<4>(acc, a.part + 2 * (size_t)a.max_blocks, a.max_blocks, blockIdx.x);
 }
@@ -1138,16 +1202,16 @@ template <int TPA>
 static void dens_t(const DevArgs &a, const PotDev &p, int block, cudaStream_t s)
 {
     int A = block / TPA;
-    if (a.mixed) k_density<TPA, true><<<a.S / A, block, 0, s>>>(a, p);
-    else k_density<TPA, false><<<a.S / A, block, 0, s>>>(a, p);
+    if (a.mixed) k_density_mixed<TPA><<<a.S / A, block, 0, s>>>(a, p);
+    else k_density_fp64<TPA><<<a.S / A, block, 0, s>>>(a, p);
 }
 
 template <int TPA>
 static void force_t(const DevArgs &a, const PotDev &p, int block, int integ, cudaStream_t s)
 {
     int A = block / TPA;
-    if (a.mixed) k_force<TPA, true><<<a.S / A, block, 0, s>>>(a, p, integ);
-    else k_force<TPA, false><<<a.S / A, block, 0, s>>>(a, p, integ);
+    if (a.mixed) k_force_mixed<TPA><<<a.S / A, block, 0, s>>>(a, p, integ);
+    else k_force_fp64<TPA><<<a.S / A, block, 0, s>>>(a, p, integ);
 }
 
 cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c, cudaStream_t s)
