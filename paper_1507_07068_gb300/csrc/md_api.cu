@@ -427,9 +427,9 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     INIT_FAIL(dalloc(h, &a.v, 3 * (size_t)S));
     INIT_FAIL(dalloc(h, &a.F, 3 * (size_t)S));
     INIT_FAIL(dalloc(h, &a.xb, 3 * (size_t)S));
-    INIT_FAIL(dalloc(h, &a.pos4, S));
+    INIT_FAIL(dalloc(h, &a.rec, 2 * (size_t)S));
     INIT_FAIL(dalloc(h, &a.fm64, S));
-    INIT_FAIL(dalloc(h, &a.fm32, S));
+    INIT_FAIL(dalloc(h, &a.imask, S));
     INIT_FAIL(dalloc(h, &a.cellc, S));
     INIT_FAIL(dalloc(h, &a.orig, S));
     INIT_FAIL(dalloc(h, &a.fixed, S));

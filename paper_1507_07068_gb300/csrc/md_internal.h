@@ -5,11 +5,14 @@
 //     replicas, so a CTA's atoms belong to one replica and per-replica sums are plain
 //     per-CTA partials); slots past a replica's last atom are padding (never binned,
 //     never listed, never integrated);
-//   - per-atom SoA arrays: x[3][S], v[3][S], F[3][S], x_build[3][S] (FP64),
-//     pos4[S] (float4: position relative to the atom's cell centre in FP32, and the
-//     atom's cell coordinates packed in .w), fm (F'(rho), M'(P) per atom: double2 in FP64
-//     mode, float2 in mixed mode), cellc[S] (packed cell coordinates), orig[S] (caller id),
-//     fixed[S] (uint8);
+//   - per-atom SoA arrays: x[3][S], v[3][S], F[3][S], x_build[3][S] (FP64), cellc[S]
+//     (packed cell coordinates), orig[S] (caller id), fixed[S] (uint8), fm64[S] (F'(rho),
+//     M'(P) in FP64 mode);
+//   - rec[2S] (mixed precision, 32-byte records, one L1 sector per neighbour): rec[2i] =
+//     position relative to the atom's cell centre in FP32 with the packed cell coordinates
+//     in .w, rec[2i + 1].xy = F'(rho_i), M'(P_i) in FP32;
+//   - imask[S]: bit k set when entry k of the Verlet list lies within rc at the current
+//     positions (the inner list of the two-tier scheme, rebuilt every step by k_density);
 //   - Verlet lists in SoA form nbr[k * S + i] (slot of the k-th neighbour of slot i), so a
 //     warp reading its 32 atoms' k-th entries reads 128 consecutive bytes, and cnt[S];
 //     the Cr-C list the same with indenter slots;
@@ -134,9 +137,9 @@ struct DevArgs {
     const int32_t *cell_rep;     // replica of each cell
     // per-atom
     double *x, *v, *F, *xb;      // [3][S]
-    float4 *pos4;
+    float4 *rec;                 // [2S], 32-byte aligned records (see above)
     double2 *fm64;
-    float2 *fm32;
+    unsigned long long *imask;
     int32_t *cellc, *orig;
     uint8_t *fixed;
     int32_t *nbr, *cnt, *nbrc, *cntc;
@@ -169,4 +172,3 @@ cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s);
 cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, cudaStream_t s);
 cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s);
-cudaError_t launch_refresh_pos4(const DevArgs &a, cudaStream_t s);

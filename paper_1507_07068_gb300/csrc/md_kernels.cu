@@ -561,7 +561,7 @@ __global__ void k_copyback(DevArgs a)
     }
     a.orig[s] = a.sorig[s];
     a.fixed[s] = a.sfixed[s];
-    a.pos4[s] = rel_pos(a, R, s);   // also used by the FP32 prefilter of k_nbr
+    a.rec[2 * (size_t)s] = rel_pos(a, R, s);   // also used by the FP32 prefilter of k_nbr
 }
 
 // full Cr-Cr Verlet list: every slot j != i in the 27-cell stencil with |x_j - x_i|^2 <
@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
     const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
     if (s - R.slot_off >= R.n_atoms) return;
     size_t S = a.S;
-    const float4 pi = a.pos4[s];
+    const float4 pi = a.rec[2 * (size_t)s];
     int pc = __float_as_int(pi.w);
     int c0 = cell_x(pc), c1 = cell_y(pc), c2 = cell_z(pc);
     const float cut2 = (float)a.cut2;
@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
                 const float oz = fmaf((float)(c2 + dz != q2) * dz, R.dL32[2], dz * wz);
                 for (int t = b; t < e; ++t) {
                     if (t == s) continue;
-                    const float4 pj = a.pos4[t];
+                    const float4 pj = a.rec[2 * (size_t)t];
                     const float fx = ox + (pj.x - pi.x), fy = oy + (pj.y - pi.y), fz = oz + (pj.z - pi.z);
                     const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
                     bool in;
@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
         double d2 = norm2_exact(__dsub_rn(x0, a.xb[s]), __dsub_rn(x1, a.xb[S + s]), __dsub_rn(x2, a.xb[2 * S + s]));
         if (d2 != d2) d2 = 1e300;   // NaN position: force a rebuild, which reports it
         d2bits = (unsigned long long)__double_as_longlong(d2);   // d2 >= 0: bit order = value order
-        if (a.mixed) a.pos4[s] = rel_pos3(R, a.cellc[s], x0, x1, x2);
+        if (a.mixed) a.rec[2 * (size_t)s] = rel_pos3(R, a.cellc[s], x0, x1, x2);
     }
     for (int o = 16; o > 0; o >>= 1) {
         unsigned long long t = __shfl_xor_sync(0xffffffffu, d2bits, o);
@@ -747,15 +747,6 @@ __global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
         for (int w = 0; w < MD_TILE / 32; ++w) m = sm[w] > m ? sm[w] : m;
         if (m) atomicMax(&a.rs[r].d2max_bits, m);
     }
-}
-
-__global__ void k_refresh_pos4(DevArgs a)
-{
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.S) return;
-    const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
-    if (s - R.slot_off >= R.n_atoms) return;
-    a.pos4[s] = rel_pos(a, R, s);
 }
 
 // ============================================================================ Task 4, mixed precision
@@ -850,8 +841,9 @@ __global__ void __launch_bounds__(256) k_density_mixed(DevArgs a, PotDev P)
     const bool real = (s - R.slot_off) < R.n_atoms;
     const size_t S = a.S;
     float rho = 0.f, Ps = 0.f;
+    unsigned long long inner = 0ull;   // entries k < 64 found within rc (the inner list)
     if (real) {
-        const float4 pi = a.pos4[s];
+        const float4 pi = a.rec[2 * (size_t)s];
         const PairGeom G = pair_geom(R, __float_as_int(pi.w));
         const int n = a.cnt[s];
         for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
@@ -863,16 +855,18 @@ __global__ void __launch_bounds__(256) k_density_mixed(DevArgs a, PotDev P)
             }
             float4 pj[MD_UNROLL];
 #pragma unroll
-            for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&a.pos4[e[u] & MD_J_MASK]);
+            for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&a.rec[2 * (size_t)(e[u] & MD_J_MASK)]);
 #pragma unroll
             for (int u = 0; u < MD_UNROLL; ++u) {
                 float dx, dy, dz;
                 disp(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (k0 + u * TPA < n && r2 < Q.rc2) {
+                const int k = k0 + u * TPA;
+                if (k < n && r2 < Q.rc2) {
                     const float f = f_only(Q, sqrtf(r2));
                     rho += f;
                     Ps = fmaf(f, f, Ps);
+                    if (k < 64) inner |= 1ull << k;
                 }
             }
         }
@@ -881,13 +875,15 @@ __global__ void __launch_bounds__(256) k_density_mixed(DevArgs a, PotDev P)
     for (int o = TPA / 2; o > 0; o >>= 1) {
         rho += __shfl_xor_sync(0xffffffffu, rho, o);
         Ps += __shfl_xor_sync(0xffffffffu, Ps, o);
+        inner |= __shfl_xor_sync(0xffffffffu, inner, o);
     }
     float acc[2] = {0.f, 0.f};
     if (real && lane == 0) {
         float F, Fp, M, Mp;
         Q.embed(rho, F, Fp);
         Q.mterm(Ps, M, Mp);
-        a.fm32[s] = make_float2(Fp, Mp);
+        a.rec[2 * (size_t)s + 1] = make_float4(Fp, Mp, 0.f, 0.f);
+        a.imask[s] = inner;
         acc[0] = F; acc[1] = M;
     }
     cta_partials<2>(acc, a.part, a.max_blocks, blockIdx.x);
@@ -913,31 +909,41 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
     float gx = 0.f, gy = 0.f, gz = 0.f, ep = 0.f;
     float mx = 0.f, my = 0.f, mz = 0.f, em = 0.f;
     if (real) {
-        const float4 pi = a.pos4[s];
+        const float4 pi = a.rec[2 * (size_t)s];
         const PairGeom G = pair_geom(R, __float_as_int(pi.w));
-        const float2 fmi = a.fm32[s];
+        const float4 fmi = a.rec[2 * (size_t)s + 1];
+        const unsigned long long inner = a.imask[s];
         const int n = a.cnt[s];
+        const ulonglong4_32a *rec32 = reinterpret_cast<const ulonglong4_32a *>(a.rec);
         for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
             unsigned e[MD_UNROLL];
+            bool use[MD_UNROLL];
 #pragma unroll
             for (int u = 0; u < MD_UNROLL; ++u) {
                 const int k = k0 + u * TPA;
-                e[u] = k < n ? (unsigned)__ldg(&a.nbr[(size_t)k * S + s]) : (unsigned)s;
+                // the inner list (bits set by k_density at these positions); entries past
+                // 64 are tested against rc here
+                use[u] = k < n && (k >= 64 || ((inner >> k) & 1ull));
+                e[u] = use[u] ? (unsigned)__ldg(&a.nbr[(size_t)k * S + s]) : (unsigned)s;
             }
-            float4 pj[MD_UNROLL];
-            float2 fmj[MD_UNROLL];
+            float4 pj[MD_UNROLL], fmj[MD_UNROLL];
 #pragma unroll
             for (int u = 0; u < MD_UNROLL; ++u) {
-                const unsigned j = e[u] & MD_J_MASK;
-                pj[u] = __ldg(&a.pos4[j]);
-                fmj[u] = __ldg(&a.fm32[j]);
+                if (use[u]) {   // position and F', M' of j: one 32-byte record
+                    const ulonglong4_32a w = rec32[e[u] & MD_J_MASK];
+                    pj[u] = make_float4(__uint_as_float((unsigned)w.x), __uint_as_float((unsigned)(w.x >> 32)),
+                                        __uint_as_float((unsigned)w.y), __uint_as_float((unsigned)(w.y >> 32)));
+                    fmj[u] = make_float4(__uint_as_float((unsigned)w.z), __uint_as_float((unsigned)(w.z >> 32)), 0.f, 0.f);
+                } else {
+                    pj[u] = pi; fmj[u] = fmi;
+                }
             }
 #pragma unroll
             for (int u = 0; u < MD_UNROLL; ++u) {
                 float dx, dy, dz;
                 disp(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (k0 + u * TPA < n && r2 < Q.rc2) {
+                if (use[u] && r2 < Q.rc2) {
                     const float rinv = rsqrtf(r2);
                     float f, df, ph, dph;
                     f_phi(Q, r2 * rinv, f, df, ph, dph);
@@ -1189,12 +1195,6 @@ cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s)
 cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s)
 {
     k_verlet1<<<a.S / MD_TILE, MD_TILE, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_refresh_pos4(const DevArgs &a, cudaStream_t s)
-{
-    k_refresh_pos4<<<nblk(a.S, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
