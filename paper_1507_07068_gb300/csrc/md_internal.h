@@ -8,11 +8,16 @@
 //   - per-atom SoA arrays: x[3][S], v[3][S], F[3][S], x_build[3][S] (FP64), cellc[S]
 //     (packed cell coordinates), orig[S] (caller id), fixed[S] (uint8), fm64[S] (F'(rho),
 //     M'(P) in FP64 mode);
-//   - rec[2S] (mixed precision, 32-byte records, one L1 sector per neighbour): rec[2i] =
-//     position relative to the atom's cell centre in FP32 with the packed cell coordinates
-//     in .w, rec[2i + 1].xy = F'(rho_i), M'(P_i) in FP32;
-//   - imask[S]: bit k set when entry k of the Verlet list lies within rc at the current
-//     positions (the inner list of the two-tier scheme, rebuilt every step by k_density);
+//   - pos4[S] (mixed precision): position relative to the atom's cell centre in FP32, with
+//     the packed cell coordinates in .w; fm32[S]: F'(rho_i), M'(P_i) in FP32;
+//   - chunks: every cell row (fixed y, z) is cut into chunks of MD_W cells along x; a CTA
+//     of the mixed-precision pair kernels owns one chunk and stages the 9 neighbouring
+//     row windows (cells x0-1 .. x1 of rows y-1..y+1, z-1..z+1) into shared memory;
+//     win[q][row][wx] is the shared-memory offset of window cell wx of row `row` for chunk
+//     q (and win[q][9 (MD_W + 2)] the window total);
+//   - snbr[k * S + i]: the Verlet list again, with each entry the shared-memory index of
+//     the neighbour in its owner CTA's window (plus the same direction bits), so the
+//     mixed-precision kernels read neighbours from shared memory;
 //   - Verlet lists in SoA form nbr[k * S + i] (slot of the k-th neighbour of slot i), so a
 //     warp reading its 32 atoms' k-th entries reads 128 consecutive bytes, and cnt[S];
 //     the Cr-C list the same with indenter slots;
@@ -34,9 +39,12 @@
 // the direction of its stencil cell: bit 0/1 = x-/x+, 2/3 = y-/y+, 4/5 = z-/z+
 #define MD_J_BITS 26
 #define MD_J_MASK ((1u << MD_J_BITS) - 1u)
+#define MD_W 12        // cells per chunk along x
+#define MD_WIN ((MD_W + 2) * 9)   // window cells per chunk
+#define MD_CAP 2048    // atoms a chunk's window may hold (shared memory of the pair kernels)
 
 // error bits raised by kernels (device word, read by the host after md_step)
-enum { MDE_OVERFLOW = 1, MDE_LOST = 2, MDE_SKIN = 4, MDE_COVERFLOW = 8 };
+enum { MDE_OVERFLOW = 1, MDE_LOST = 2, MDE_SKIN = 4, MDE_COVERFLOW = 8, MDE_WINDOW = 16 };
 
 // Hermite cubic coefficients of one table interval, c0 + c1 t + c2 t^2 + c3 t^3
 struct alignas(32) Cf64 {
@@ -88,6 +96,7 @@ struct RepDev {
     double wc[3];                     // (double) w32
     int32_t cell_off, n_cells;
     int32_t slot_off, n_atoms, n_slots;  // first slot (TILE aligned), real atoms, slots incl. padding
+    int32_t nchx, chunk_off, n_chunks;   // chunks per cell row, first chunk, chunks
     int32_t real_off;                    // atoms of the replicas before (unpadded)
     int32_t n_mobile;
     // indenter
@@ -116,7 +125,7 @@ struct RepEnergy {
 struct DevStatus {
     int32_t err;            // MDE_* bits
     int32_t any_rebuild;    // rebuild decided this step (host-readable)
-    int32_t max_cnt, max_cntc;
+    int32_t max_cnt, max_cntc, max_window, pad;
     int64_t step, rebuilds, since_build;
 };
 
@@ -137,9 +146,12 @@ struct DevArgs {
     const int32_t *cell_rep;     // replica of each cell
     // per-atom
     double *x, *v, *F, *xb;      // [3][S]
-    float4 *rec;                 // [2S], 32-byte aligned records (see above)
+    float4 *pos4;
+    float2 *fm32;
     double2 *fm64;
-    unsigned long long *imask;
+    int32_t *snbr, *win;
+    const int32_t *chunk_rep;    // replica of each chunk
+    int32_t n_chunks;
     int32_t *cellc, *orig;
     uint8_t *fixed;
     int32_t *nbr, *cnt, *nbrc, *cntc;
@@ -164,6 +176,9 @@ struct LaunchCfg {
 
 // ---- host-side helpers implemented in md_kernels.cu
 int md_build_pot(const md_params *p, PotDev *out, Cf64 **d_tabs64, float4 **d_tabs32, char *err, size_t errlen);
+
+// ---- one-time kernel attributes (shared-memory opt-in of the staged pair kernels)
+cudaError_t md_prepare_kernels();
 
 // ---- launchers (all enqueue on `s`; return cudaError_t of the launch)
 cudaError_t launch_decide(const DevArgs &a, int force, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s);
