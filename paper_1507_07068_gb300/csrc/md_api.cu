@@ -123,9 +123,6 @@ int status_to_code(md_t *h, const DevStatus &st)
     if (st.err & MDE_OVERFLOW) return fail(h, MD_ERR_NBR_OVERFLOW, "Cr-Cr neighbour list overflow: %d > kmax %d", st.max_cnt, h->a.kmax);
     if (st.err & MDE_COVERFLOW) return fail(h, MD_ERR_NBR_OVERFLOW, "Cr-C neighbour list overflow: %d > kcmax %d", st.max_cntc, h->a.kcmax);
     if (st.err & MDE_SKIN) return fail(h, MD_ERR_SKIN_VIOLATION, "an atom moved more than skin/2 between fixed-interval rebuilds");
-    if (st.err & MDE_WINDOW)
-        return fail(h, MD_ERR_NBR_OVERFLOW, "a chunk's neighbour window holds %d atoms, more than the %d the staged kernels take (density too high)",
-                    st.max_window, MD_CAP);
     return MD_OK;
 }
 
@@ -164,12 +161,7 @@ int rebuild_growing(md_t *h)
             int k = st.max_cnt + 16;
             int32_t *p;
             if ((rc = dalloc(h, &p, (size_t)k * h->a.S))) return rc;
-            h->a.nbr = p;
-            if (h->a.mixed) {
-                if ((rc = dalloc(h, &p, (size_t)k * h->a.S))) return rc;
-                h->a.snbr = p;
-            }
-            h->a.kmax = k; grow = true;
+            h->a.nbr = p; h->a.kmax = k; grow = true;
         }
         if ((st.err & MDE_COVERFLOW) && st.max_cntc > h->a.kcmax) {
             int k = st.max_cntc + 32;
@@ -337,13 +329,12 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
 
 #define CUI(call) INIT_FAIL(cu_check(h, (call), #call))
     char ebuf[256] = {0};
-    CUI(md_prepare_kernels());
     rc = md_build_pot(&h->pot_h, &h->pot, &h->tab64, &h->tab32, ebuf, sizeof ebuf);
     if (rc) { h->err = ebuf; INIT_FAIL(rc); }
 
     const double cut = h->pot_h.rc + opt->skin, cutc = h->pot_h.rc_morse + opt->skin;
     // ---- layout
-    int64_t slots = 0, cells = 0, ccells = 0, real = 0, cslots = 0, chunks = 0;
+    int64_t slots = 0, cells = 0, ccells = 0, real = 0, cslots = 0;
     size_t max_n = 1;
     h->rep.resize(n_replicas);
     for (int r = 0; r < n_replicas; ++r) {
@@ -371,10 +362,6 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
         R.cell_off = (int32_t)cells;
         R.n_cells = R.nc[0] * R.nc[1] * R.nc[2];
         cells += R.n_cells;
-        R.nchx = (R.nc[0] + MD_W - 1) / MD_W;
-        R.chunk_off = (int32_t)chunks;
-        R.n_chunks = R.nchx * R.nc[1] * R.nc[2];
-        chunks += R.n_chunks;
         R.slot_off = (int32_t)slots;
         R.n_atoms = y.n_cr;
         R.n_slots = (y.n_cr + MD_TILE - 1) / MD_TILE * MD_TILE;
@@ -424,8 +411,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     a.rebuild_every = opt->rebuild_every;
     a.skin = opt->skin; a.cut = cut; a.cutc = cutc; a.cut2 = cut * cut; a.cutc2 = cutc * cutc;
     a.C = (int)cslots;
-    a.n_chunks = (int)chunks;
-    a.max_blocks = (int)std::max<int64_t>(S / (block / tpa), chunks) + 1;
+    a.max_blocks = S / (block / tpa) + 1;
 
     // ---- device memory
     RepDev *d_rep; RepState *d_rs; RepEnergy *d_en; DevStatus *d_st;
@@ -442,17 +428,12 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     INIT_FAIL(dalloc(h, &a.F, 3 * (size_t)S));
     INIT_FAIL(dalloc(h, &a.xb, 3 * (size_t)S));
     INIT_FAIL(dalloc(h, &a.pos4, S));
-    INIT_FAIL(dalloc(h, &a.fm32, S));
     INIT_FAIL(dalloc(h, &a.fm64, S));
+    INIT_FAIL(dalloc(h, &a.fm32, S));
     INIT_FAIL(dalloc(h, &a.cellc, S));
     INIT_FAIL(dalloc(h, &a.orig, S));
     INIT_FAIL(dalloc(h, &a.fixed, S));
     INIT_FAIL(dalloc(h, &a.nbr, (size_t)a.kmax * S));
-    INIT_FAIL(dalloc(h, &a.snbr, a.mixed ? (size_t)a.kmax * S : 1));
-    INIT_FAIL(dalloc(h, &a.win, (size_t)chunks * (MD_WIN + 1)));
-    int32_t *d_chunk_rep;
-    INIT_FAIL(dalloc(h, &d_chunk_rep, chunks));
-    a.chunk_rep = d_chunk_rep;
     INIT_FAIL(dalloc(h, &a.cnt, S));
     INIT_FAIL(dalloc(h, &a.nbrc, (size_t)a.kcmax * S));
     INIT_FAIL(dalloc(h, &a.cntc, S));
@@ -478,7 +459,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     // ---- host staging in slot order (initial slot order = caller order)
     {
         std::vector<double> hx(3 * (size_t)S, 0.0), hv(3 * (size_t)S, 0.0);
-        std::vector<int32_t> horig(S, 0), htile(S / MD_TILE), hcell(cells), hchunk(chunks > 0 ? chunks : 1);
+        std::vector<int32_t> horig(S, 0), htile(S / MD_TILE), hcell(cells);
         std::vector<uint8_t> hfix(S, 1);
         std::vector<double> hxc(3 * (size_t)(cslots > 0 ? cslots : 1), 0.0);
         std::vector<int32_t> hccs(ccells > 0 ? ccells : 1, 0), hccc(ccells > 0 ? ccells : 1, 0);
@@ -489,7 +470,6 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
             const RepDev &R = h->rep[r];
             for (int t = R.slot_off / MD_TILE; t < (R.slot_off + R.n_slots) / MD_TILE; ++t) htile[t] = r;
             for (int c = R.cell_off; c < R.cell_off + R.n_cells; ++c) hcell[c] = r;
-            for (int q = R.chunk_off; q < R.chunk_off + R.n_chunks; ++q) hchunk[q] = r;
             for (int i = 0; i < y.n_cr; ++i) {
                 int s = R.slot_off + i;
                 for (int k = 0; k < 3; ++k) {
@@ -531,7 +511,6 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
         CUI(cudaMemcpy(a.fixed, hfix.data(), S, cudaMemcpyHostToDevice));
         CUI(cudaMemcpy(d_tile_rep, htile.data(), htile.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
         CUI(cudaMemcpy(d_cell_rep, hcell.data(), hcell.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-        CUI(cudaMemcpy(d_chunk_rep, hchunk.data(), chunks * sizeof(int32_t), cudaMemcpyHostToDevice));
         CUI(cudaMemcpy(d_rep, h->rep.data(), n_replicas * sizeof(RepDev), cudaMemcpyHostToDevice));
         CUI(cudaMemcpy(d_rs, hrs.data(), n_replicas * sizeof(RepState), cudaMemcpyHostToDevice));
         if (cslots > 0) {

@@ -5,19 +5,11 @@
 //     replicas, so a CTA's atoms belong to one replica and per-replica sums are plain
 //     per-CTA partials); slots past a replica's last atom are padding (never binned,
 //     never listed, never integrated);
-//   - per-atom SoA arrays: x[3][S], v[3][S], F[3][S], x_build[3][S] (FP64), cellc[S]
-//     (packed cell coordinates), orig[S] (caller id), fixed[S] (uint8), fm64[S] (F'(rho),
-//     M'(P) in FP64 mode);
-//   - pos4[S] (mixed precision): position relative to the atom's cell centre in FP32, with
-//     the packed cell coordinates in .w; fm32[S]: F'(rho_i), M'(P_i) in FP32;
-//   - chunks: every cell row (fixed y, z) is cut into chunks of MD_W cells along x; a CTA
-//     of the mixed-precision pair kernels owns one chunk and stages the 9 neighbouring
-//     row windows (cells x0-1 .. x1 of rows y-1..y+1, z-1..z+1) into shared memory;
-//     win[q][row][wx] is the shared-memory offset of window cell wx of row `row` for chunk
-//     q (and win[q][9 (MD_W + 2)] the window total);
-//   - snbr[k * S + i]: the Verlet list again, with each entry the shared-memory index of
-//     the neighbour in its owner CTA's window (plus the same direction bits), so the
-//     mixed-precision kernels read neighbours from shared memory;
+//   - per-atom SoA arrays: x[3][S], v[3][S], F[3][S], x_build[3][S] (FP64),
+//     pos4[S] (float4: position relative to the atom's cell centre in FP32, and the
+//     atom's cell coordinates packed in .w), fm (F'(rho), M'(P) per atom: double2 in FP64
+//     mode, float2 in mixed mode), cellc[S] (packed cell coordinates), orig[S] (caller id),
+//     fixed[S] (uint8);
 //   - Verlet lists in SoA form nbr[k * S + i] (slot of the k-th neighbour of slot i), so a
 //     warp reading its 32 atoms' k-th entries reads 128 consecutive bytes, and cnt[S];
 //     the Cr-C list the same with indenter slots;
@@ -39,12 +31,9 @@
 // the direction of its stencil cell: bit 0/1 = x-/x+, 2/3 = y-/y+, 4/5 = z-/z+
 #define MD_J_BITS 26
 #define MD_J_MASK ((1u << MD_J_BITS) - 1u)
-#define MD_W 12        // cells per chunk along x
-#define MD_WIN ((MD_W + 2) * 9)   // window cells per chunk
-#define MD_CAP 2048    // atoms a chunk's window may hold (shared memory of the pair kernels)
 
 // error bits raised by kernels (device word, read by the host after md_step)
-enum { MDE_OVERFLOW = 1, MDE_LOST = 2, MDE_SKIN = 4, MDE_COVERFLOW = 8, MDE_WINDOW = 16 };
+enum { MDE_OVERFLOW = 1, MDE_LOST = 2, MDE_SKIN = 4, MDE_COVERFLOW = 8 };
 
 // Hermite cubic coefficients of one table interval, c0 + c1 t + c2 t^2 + c3 t^3
 struct alignas(32) Cf64 {
@@ -60,6 +49,10 @@ struct PotF32 {
     int32_t tabulated, nf, nm;
     const float4 *tf, *tp, *tm;
     const float4 *tfp;   // f and Phi coefficients interleaved: [2k] = f, [2k + 1] = Phi
+    // direct FP32 forms of the pair loops: f = f_e (r_e^2 / r^2)^ipow when beta = 2 ipow
+    // (ipow = 0: exp2/log2 form); r / r_e - d with the FP32 rounding of 1/r_e and d carried
+    float f_e, re2, inv_re_lo, d_lo;
+    int32_t ipow;
 };
 
 // potential, passed by value to kernels (lives in the constant bank)
@@ -96,7 +89,6 @@ struct RepDev {
     double wc[3];                     // (double) w32
     int32_t cell_off, n_cells;
     int32_t slot_off, n_atoms, n_slots;  // first slot (TILE aligned), real atoms, slots incl. padding
-    int32_t nchx, chunk_off, n_chunks;   // chunks per cell row, first chunk, chunks
     int32_t real_off;                    // atoms of the replicas before (unpadded)
     int32_t n_mobile;
     // indenter
@@ -125,7 +117,7 @@ struct RepEnergy {
 struct DevStatus {
     int32_t err;            // MDE_* bits
     int32_t any_rebuild;    // rebuild decided this step (host-readable)
-    int32_t max_cnt, max_cntc, max_window, pad;
+    int32_t max_cnt, max_cntc;
     int64_t step, rebuilds, since_build;
 };
 
@@ -147,11 +139,8 @@ struct DevArgs {
     // per-atom
     double *x, *v, *F, *xb;      // [3][S]
     float4 *pos4;
-    float2 *fm32;
     double2 *fm64;
-    int32_t *snbr, *win;
-    const int32_t *chunk_rep;    // replica of each chunk
-    int32_t n_chunks;
+    float2 *fm32;
     int32_t *cellc, *orig;
     uint8_t *fixed;
     int32_t *nbr, *cnt, *nbrc, *cntc;
@@ -177,9 +166,6 @@ struct LaunchCfg {
 // ---- host-side helpers implemented in md_kernels.cu
 int md_build_pot(const md_params *p, PotDev *out, Cf64 **d_tabs64, float4 **d_tabs32, char *err, size_t errlen);
 
-// ---- one-time kernel attributes (shared-memory opt-in of the staged pair kernels)
-cudaError_t md_prepare_kernels();
-
 // ---- launchers (all enqueue on `s`; return cudaError_t of the launch)
 cudaError_t launch_decide(const DevArgs &a, int force, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s);
@@ -187,3 +173,4 @@ cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s);
 cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, cudaStream_t s);
 cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_refresh_pos4(const DevArgs &a, cudaStream_t s);

@@ -176,6 +176,12 @@ int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs
     q.inv_P_e = (float)(1.0 / P->P_e); q.rc2 = (float)P->rc2;
     q.tabulated = P->tabulated; q.nf = nf; q.nm = nm; q.tf = P->tf32; q.tp = P->tp32; q.tm = P->tm32;
     q.tfp = *d_tabs32 + 2 * nf + nm;
+    q.f_e = (float)p->f_e;
+    q.re2 = (float)(p->r_e * p->r_e);
+    q.inv_re_lo = (float)(1.0 / p->r_e - (double)q.inv_re);
+    q.d_lo = (float)(p->d - (double)q.d);
+    const double half_beta = 0.5 * p->beta;
+    q.ipow = (half_beta == floor(half_beta) && half_beta >= 1.0 && half_beta <= 8.0) ? (int)half_beta : 0;
     return MD_OK;
 }
 
@@ -403,7 +409,7 @@ __global__ void k_zero_i32(int32_t *p, int n)
 __global__ void k_bin(DevArgs a)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s == 0) { a.st->max_cnt = 0; a.st->max_cntc = 0; a.st->max_window = 0; }
+    if (s == 0) { a.st->max_cnt = 0; a.st->max_cntc = 0; }
     if (s >= a.S) return;
     int r = a.tile_rep[s / MD_TILE];
     const RepDev &R = a.rep[r];
@@ -480,45 +486,6 @@ __global__ void k_scan3(DevArgs a, int per_block)
     if (c >= a.total_cells) return;
     const RepDev &R = a.rep[a.cell_rep[c]];
     a.cell_start[c] += a.scan_blk[c / per_block] + (R.slot_off - R.real_off);
-}
-
-// Window table of every chunk: shared-memory offset of each of the 9 x (MD_W + 2) window
-// cells (rows dz-major then dy, cells x0-1 .. x1 of each row), in the order the pair
-// kernels stage them.  A row or cell outside a non-periodic axis is empty.
-__device__ __forceinline__ bool wrap_axis(int &c, int n, int per)
-{
-    if (c >= 0 && c < n) return true;
-    if (!per) return false;
-    c = (c + n) % n;
-    return true;
-}
-
-__global__ void k_windows(DevArgs a)
-{
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= a.n_chunks) return;
-    const RepDev &R = a.rep[a.chunk_rep[q]];
-    const int ql = q - R.chunk_off;
-    const int xc = ql % R.nchx, row = ql / R.nchx;
-    const int y = row % R.nc[1], z = row / R.nc[1];
-    const int x0 = xc * MD_W, x1 = min(R.nc[0], x0 + MD_W);
-    int32_t *w = a.win + (size_t)q * (MD_WIN + 1);
-    int off = 0;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy) {
-            int zz = z + dz, yy = y + dy;
-            const bool rowok = wrap_axis(zz, R.nc[2], R.per[2]) && wrap_axis(yy, R.nc[1], R.per[1]);
-            const int rw = (dz + 1) * 3 + (dy + 1);
-            for (int wx = 0; wx < MD_W + 2; ++wx) {
-                w[rw * (MD_W + 2) + wx] = off;
-                int xx = x0 - 1 + wx;
-                if (!rowok || xx > x1 || !wrap_axis(xx, R.nc[0], R.per[0])) continue;
-                off += a.cell_count[R.cell_off + (zz * R.nc[1] + yy) * R.nc[0] + xx];
-            }
-        }
-    w[MD_WIN] = off;
-    if (off > MD_CAP) atomicOr(&a.st->err, MDE_WINDOW);
-    atomicMax(&a.st->max_window, off);
 }
 
 __global__ void k_scatter(DevArgs a)
@@ -623,14 +590,6 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
     const float wx = R.w32[0], wy = R.w32[1], wz = R.w32[2];
     const float lim = 0.75f * fminf(wx, fminf(wy, wz));   // beyond: atom clamped outside its cell
     const bool ifar = fabsf(pi.x) > lim || fabsf(pi.y) > lim || fabsf(pi.z) > lim;
-    // this atom's chunk and its window table (mixed precision: staged list entries)
-    const int32_t *win = nullptr;
-    int wx0 = 0;
-    if (a.mixed) {
-        const int xc = c0 / MD_W;
-        win = a.win + (size_t)(R.chunk_off + (c2 * R.nc[1] + c1) * R.nchx + xc) * (MD_WIN + 1);
-        wx0 = c0 - xc * MD_W + 1;
-    }
     int m = 0;
     for (int dz = -1; dz <= 1; ++dz) {
         int q2 = c2 + dz;
@@ -643,8 +602,6 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
                 if (q0 < 0 || q0 >= R.nc[0]) { if (!R.per[0]) continue; q0 = (q0 + R.nc[0]) % R.nc[0]; }
                 int key = R.cell_off + (q2 * R.nc[1] + q1) * R.nc[0] + q0;
                 int b = a.cell_start[key], e = b + a.cell_count[key];
-                const int sbase = a.mixed ? win[((dz + 1) * 3 + (dy + 1)) * (MD_W + 2) + wx0 + dx] - b : 0;
-                const int slimit = MD_CAP - 1 - sbase;   // an overflowing window (reported by k_windows) maps to 0
                 const unsigned dir = (dx < 0 ? 1u : 0u) | (dx > 0 ? 2u : 0u) | (dy < 0 ? 4u : 0u) | (dy > 0 ? 8u : 0u) |
                                      (dz < 0 ? 16u : 0u) | (dz > 0 ? 32u : 0u);
                 // centre offset of the stencil cell: d w32, plus d dL32 through a periodic face
@@ -666,10 +623,7 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
                         in = norm2_exact(ddx, ddy, ddz) < a.cut2;
                     }
                     if (in) {
-                        if (m < a.kmax) {
-                            a.nbr[(size_t)m * S + s] = (int32_t)((unsigned)t | (dir << MD_J_BITS));
-                            if (a.mixed) a.snbr[(size_t)m * S + s] = (int32_t)((unsigned)(t <= slimit ? sbase + t : 0) | (dir << MD_J_BITS));
-                        }
+                        if (m < a.kmax) a.nbr[(size_t)m * S + s] = (int32_t)((unsigned)t | (dir << MD_J_BITS));
                         ++m;
                     }
                 }
@@ -801,6 +755,15 @@ __global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
     }
 }
 
+__global__ void k_refresh_pos4(DevArgs a)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.S) return;
+    const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
+    if (s - R.slot_off >= R.n_atoms) return;
+    a.pos4[s] = rel_pos(a, R, s);
+}
+
 // ============================================================================ Task 4, mixed precision
 //
 // Geometry of a pair from FP32 cell-relative positions: x_j - x_i = (p_j - p_i) + offset,
@@ -850,172 +813,152 @@ __device__ __forceinline__ void disp(const float4 &pi, const float4 &pj, unsigne
     }
 }
 
-// f and Phi from the interleaved FP32 tables (one index computation); value of f only, or
-// value and slope of both
-__device__ __forceinline__ float f_only(const Pot32 &Q, float r)
+// The pair loops of the mixed path evaluate the forms of Eqs. A2 and A4 directly in FP32
+// (no table gather: at FP32 resolution a Hermite table adds nothing but 32 bytes of memory
+// traffic per pair; its deviation from the forms is below 1e-11).  f: for an even integer
+// beta the power is (r_e^2/r^2)^(beta/2) by multiplication; Phi: Taylor form about the
+// double root, with t = r/r_e - d formed with the rounding of 1/r_e and d compensated.
+__device__ __forceinline__ float f_direct(const Pot32 &Q, float r2, float r)
 {
-    if (!Q.tabulated) { float v, dv; Q.f(r, v, dv); return v; }
-    const float s = fmaf(r, Q.inv_hf, -Q.rmin_s_f);
-    const float kf = fminf(fmaxf(floorf(s), 0.0f), (float)(Q.nf - 1));
-    const float t = s - kf;
-    const float4 c = __ldg(&Q.tfp[2 * (int)kf]);
-    return fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
-}
-
-__device__ __forceinline__ void f_phi(const Pot32 &Q, float r, float &f, float &df, float &ph, float &dph)
-{
-    if (!Q.tabulated) { Q.f(r, f, df); Q.phi(r, ph, dph); return; }
-    const float s = fmaf(r, Q.inv_hf, -Q.rmin_s_f);
-    const float kf = fminf(fmaxf(floorf(s), 0.0f), (float)(Q.nf - 1));
-    const float t = s - kf;
-    const int k = 2 * (int)kf;
-    const float4 a = __ldg(&Q.tfp[k]), b = __ldg(&Q.tfp[k + 1]);
-    f = fmaf(fmaf(fmaf(a.w, t, a.z), t, a.y), t, a.x);
-    df = fmaf(fmaf(3.0f * a.w, t, 2.0f * a.z), t, a.y) * Q.inv_hf;
-    ph = fmaf(fmaf(fmaf(b.w, t, b.z), t, b.y), t, b.x);
-    dph = fmaf(fmaf(3.0f * b.w, t, 2.0f * b.z), t, b.y) * Q.inv_hf;
-}
-
-// Stage a chunk's window into shared memory: each warp copies whole window cells (the
-// cell order of the window table), so a neighbour's staged index is its window cell's
-// offset plus its place in the cell.
-template <bool FM>
-__device__ __forceinline__ void stage_window(const DevArgs &a, const RepDev &R, int q, float4 *s_pos, float2 *s_fm,
-                                             int *s_src, int *s_cnt, int *s_dst)
-{
-    const int ql = q - R.chunk_off;
-    const int xc = ql % R.nchx, row = ql / R.nchx;
-    const int y = row % R.nc[1], z = row / R.nc[1];
-    const int x0 = xc * MD_W, x1 = min(R.nc[0], x0 + MD_W);
-    const int32_t *w = a.win + (size_t)q * (MD_WIN + 1);
-    for (int c = threadIdx.x; c < MD_WIN; c += blockDim.x) {
-        const int rw = c / (MD_W + 2), wx = c % (MD_W + 2);
-        int zz = z + rw / 3 - 1, yy = y + rw % 3 - 1, xx = x0 - 1 + wx;
-        int src = 0, cnt = 0;
-        if (xx <= x1 && wrap_axis(zz, R.nc[2], R.per[2]) && wrap_axis(yy, R.nc[1], R.per[1]) &&
-            wrap_axis(xx, R.nc[0], R.per[0])) {
-            const int key = R.cell_off + (zz * R.nc[1] + yy) * R.nc[0] + xx;
-            src = a.cell_start[key];
-            cnt = a.cell_count[key];
-        }
-        s_src[c] = src; s_cnt[c] = cnt; s_dst[c] = w[c];
+    float fr;
+    if (Q.ipow > 0) {
+        const float q = Q.re2 / r2;
+        fr = q;
+        for (int k = 1; k < Q.ipow; ++k) fr *= q;
+        fr *= Q.f_e;
+    } else {
+        fr = exp2f(Q.lf0 - Q.beta * log2f(r));
     }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int c = threadIdx.x >> 5; c < MD_WIN; c += nw) {
-        const int cnt = s_cnt[c], src = s_src[c], dst = s_dst[c];
-        for (int k = lane; k < cnt && dst + k < MD_CAP; k += 32) {
-            s_pos[dst + k] = __ldg(&a.pos4[src + k]);
-            if (FM) s_fm[dst + k] = __ldg(&a.fm32[src + k]);
-        }
-    }
-    __syncthreads();
+    return fr;
 }
 
-__device__ __forceinline__ void chunk_atoms(const DevArgs &a, const RepDev &R, int q, int &first, int &count)
+__device__ __forceinline__ float fa_val(const Pot32 &Q, float r2)
 {
-    const int ql = q - R.chunk_off;
-    const int xc = ql % R.nchx, row = ql / R.nchx;
-    const int x0 = xc * MD_W, x1 = min(R.nc[0], x0 + MD_W);
-    const int base = R.cell_off + row * R.nc[0];
-    first = a.cell_start[base + x0];
-    count = a.cell_start[base + x1 - 1] + a.cell_count[base + x1 - 1] - first;
+    const float r = sqrtf(r2);
+    return f_direct(Q, r2, r) - Q.f_rc - (r - Q.rc) * Q.df_rc;
 }
 
-// Task 4a (Eqs. A2-A3): rho_i, P_i over the list entries within rc; F'(rho_i), M'(P_i)
-// stored, F(rho_i), M(P_i) into the chunk's energy partials.  One CTA per chunk, one thread
-// per atom; neighbours are read from the staged window.
-__global__ void __launch_bounds__(128) k_density_mixed(DevArgs a, PotDev P)
+__device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, float &f, float &df, float &ph, float &dph)
 {
-    extern __shared__ float4 s_pos[];
+    const float r = r2 * rinv;
+    const float fr = f_direct(Q, r2, r);
+    f = fr - Q.f_rc - (r - Q.rc) * Q.df_rc;
+    df = -Q.beta * fr * rinv - Q.df_rc;
+    const float t = fmaf(r, Q.inv_re, -Q.d) + fmaf(r, Q.inv_re_lo, -Q.d_lo);
+    if (t > 0.0f) { ph = dph = 0.0f; return; }
+    ph = t * t * fmaf(fmaf(fmaf(Q.b3, t, Q.b2), t, Q.b1), t, Q.b0);
+    dph = t * fmaf(fmaf(fmaf(5.0f * Q.b3, t, 4.0f * Q.b2), t, 3.0f * Q.b1), t, 2.0f * Q.b0) * Q.inv_re;
+}
+
+// Task 4a (Eqs. A2-A3): rho_i, P_i over the list entries within rc; F'(rho_i), M'(P_i) stored,
+// F(rho_i), M(P_i) into the CTA's energy partials.  MD_UNROLL entries per lane are loaded
+// (list entry, then position) before any is used.
+template <int TPA>
+__global__ void __launch_bounds__(256) k_density_mixed(DevArgs a, PotDev P)
+{
     __shared__ float4 sm_off[64];
-    __shared__ int s_src[MD_WIN], s_cnt[MD_WIN], s_dst[MD_WIN];
-    const int q = blockIdx.x;
-    const RepDev &R = a.rep[a.chunk_rep[q]];
+    const int A = blockDim.x / TPA;
+    const int g = threadIdx.x / TPA, lane = threadIdx.x % TPA;
+    const int s = blockIdx.x * A + g;
+    const RepDev &R = a.rep[a.tile_rep[(blockIdx.x * A) / MD_TILE]];
     fill_offsets(sm_off, R);
-    stage_window<false>(a, R, q, s_pos, nullptr, s_src, s_cnt, s_dst);
+    __syncthreads();
     const Pot32 &Q = static_cast<const Pot32 &>(P.q);
+    const bool real = (s - R.slot_off) < R.n_atoms;
     const size_t S = a.S;
-    int first, count;
-    chunk_atoms(a, R, q, first, count);
-    float acc[2] = {0.f, 0.f};
-    for (int t = threadIdx.x; t < count; t += blockDim.x) {
-        const int s = first + t;
+    float rho = 0.f, Ps = 0.f;
+    if (real) {
         const float4 pi = a.pos4[s];
         const PairGeom G = pair_geom(R, __float_as_int(pi.w));
         const int n = a.cnt[s];
-        float rho = 0.f, Ps = 0.f;
-        for (int k0 = 0; k0 < n; k0 += MD_UNROLL) {
+        for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
             unsigned e[MD_UNROLL];
 #pragma unroll
-            for (int u = 0; u < MD_UNROLL; ++u)
-                e[u] = k0 + u < n ? (unsigned)__ldg(&a.snbr[(size_t)(k0 + u) * S + s]) : 0u;
+            for (int u = 0; u < MD_UNROLL; ++u) {
+                const int k = k0 + u * TPA;
+                e[u] = k < n ? (unsigned)__ldg(&a.nbr[(size_t)k * S + s]) : (unsigned)s;
+            }
+            float4 pj[MD_UNROLL];
+#pragma unroll
+            for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&a.pos4[e[u] & MD_J_MASK]);
 #pragma unroll
             for (int u = 0; u < MD_UNROLL; ++u) {
-                const float4 pj = s_pos[e[u] & MD_J_MASK];
                 float dx, dy, dz;
-                disp(pi, pj, e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
+                disp(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (k0 + u < n && r2 < Q.rc2) {
-                    const float f = f_only(Q, sqrtf(r2));
+                if (k0 + u * TPA < n && r2 < Q.rc2) {
+                    const float f = fa_val(Q, r2);
                     rho += f;
                     Ps = fmaf(f, f, Ps);
                 }
             }
         }
+    }
+#pragma unroll
+    for (int o = TPA / 2; o > 0; o >>= 1) {
+        rho += __shfl_xor_sync(0xffffffffu, rho, o);
+        Ps += __shfl_xor_sync(0xffffffffu, Ps, o);
+    }
+    float acc[2] = {0.f, 0.f};
+    if (real && lane == 0) {
         float F, Fp, M, Mp;
         Q.embed(rho, F, Fp);
         Q.mterm(Ps, M, Mp);
         a.fm32[s] = make_float2(Fp, Mp);
-        acc[0] += F; acc[1] += M;
+        acc[0] = F; acc[1] = M;
     }
-    cta_partials<2>(acc, a.part, a.max_blocks, q);
+    cta_partials<2>(acc, a.part, a.max_blocks, blockIdx.x);
 }
 
 // Task 4b,c (Eq. (1) with the M term, Eqs. A6-A10; Morse Eqs. A5, A9) and Task 5 (the
 // closing half kick, FP64).  The force on i from j is coef * (x_j - x_i), coef = [(F'_i +
 // F'_j) f' + (M'_i + M'_j) 2 f f' + Phi'] / r.
-__global__ void __launch_bounds__(128) k_force_mixed(DevArgs a, PotDev P, int integrate)
+template <int TPA>
+__global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int integrate)
 {
-    extern __shared__ float4 s_pos[];
     __shared__ float4 sm_off[64];
-    __shared__ int s_src[MD_WIN], s_cnt[MD_WIN], s_dst[MD_WIN];
-    float2 *s_fm = reinterpret_cast<float2 *>(s_pos + MD_CAP);
-    const int q = blockIdx.x;
-    const int r = a.chunk_rep[q];
+    const int A = blockDim.x / TPA;
+    const int g = threadIdx.x / TPA, lane = threadIdx.x % TPA;
+    const int s = blockIdx.x * A + g;
+    const int r = a.tile_rep[(blockIdx.x * A) / MD_TILE];
     const RepDev &R = a.rep[r];
     fill_offsets(sm_off, R);
-    stage_window<true>(a, R, q, s_pos, s_fm, s_src, s_cnt, s_dst);
+    __syncthreads();
     const Pot32 &Q = static_cast<const Pot32 &>(P.q);
+    const bool real = (s - R.slot_off) < R.n_atoms;
     const size_t S = a.S, C = a.C;
-    int first, count;
-    chunk_atoms(a, R, q, first, count);
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int t = threadIdx.x; t < count; t += blockDim.x) {
-        const int s = first + t;
+    float gx = 0.f, gy = 0.f, gz = 0.f, ep = 0.f;
+    float mx = 0.f, my = 0.f, mz = 0.f, em = 0.f;
+    if (real) {
         const float4 pi = a.pos4[s];
         const PairGeom G = pair_geom(R, __float_as_int(pi.w));
         const float2 fmi = a.fm32[s];
         const int n = a.cnt[s];
-        float gx = 0.f, gy = 0.f, gz = 0.f, ep = 0.f;
-        for (int k0 = 0; k0 < n; k0 += MD_UNROLL) {
+        for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
             unsigned e[MD_UNROLL];
 #pragma unroll
-            for (int u = 0; u < MD_UNROLL; ++u)
-                e[u] = k0 + u < n ? (unsigned)__ldg(&a.snbr[(size_t)(k0 + u) * S + s]) : 0u;
+            for (int u = 0; u < MD_UNROLL; ++u) {
+                const int k = k0 + u * TPA;
+                e[u] = k < n ? (unsigned)__ldg(&a.nbr[(size_t)k * S + s]) : (unsigned)s;
+            }
+            float4 pj[MD_UNROLL];
+            float2 fmj[MD_UNROLL];
 #pragma unroll
             for (int u = 0; u < MD_UNROLL; ++u) {
                 const unsigned j = e[u] & MD_J_MASK;
-                const float4 pj = s_pos[j];
+                pj[u] = __ldg(&a.pos4[j]);
+                fmj[u] = __ldg(&a.fm32[j]);
+            }
+#pragma unroll
+            for (int u = 0; u < MD_UNROLL; ++u) {
                 float dx, dy, dz;
-                disp(pi, pj, e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
+                disp(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (k0 + u < n && r2 < Q.rc2) {
-                    const float2 fmj = s_fm[j];
+                if (k0 + u * TPA < n && r2 < Q.rc2) {
                     const float rinv = rsqrtf(r2);
                     float f, df, ph, dph;
-                    f_phi(Q, r2 * rinv, f, df, ph, dph);
-                    const float coef = fmaf(fmi.x + fmj.x, df, fmaf((fmi.y + fmj.y) * 2.0f * f, df, dph)) * rinv;
+                    fa_phi(Q, r2, rinv, f, df, ph, dph);
+                    const float coef = fmaf(fmi.x + fmj[u].x, df, fmaf((fmi.y + fmj[u].y) * 2.0f * f, df, dph)) * rinv;
                     gx = fmaf(coef, dx, gx);
                     gy = fmaf(coef, dy, gy);
                     gz = fmaf(coef, dz, gz);
@@ -1024,12 +967,11 @@ __global__ void __launch_bounds__(128) k_force_mixed(DevArgs a, PotDev P, int in
             }
         }
         // Cr-C (Morse): FP64 geometry of the few near-indenter pairs, FP32 potential
-        float mx = 0.f, my = 0.f, mz = 0.f, em = 0.f;
         const int nc = a.cntc[s];
         if (nc > 0) {
             const double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
             const double z_ind = a.rs[r].z_ind;
-            for (int k = 0; k < nc; ++k) {
+            for (int k = lane; k < nc; k += TPA) {
                 const int c = __ldg(&a.nbrc[(size_t)k * S + s]);
                 const double ddx = mi64(a.xc0[c] - xi, R.per[0], R.L[0]);
                 const double ddy = mi64(a.xc0[C + c] - yi, R.per[1], R.L[1]);
@@ -1047,6 +989,20 @@ __global__ void __launch_bounds__(128) k_force_mixed(DevArgs a, PotDev P, int in
                 }
             }
         }
+    }
+#pragma unroll
+    for (int o = TPA / 2; o > 0; o >>= 1) {
+        gx += __shfl_xor_sync(0xffffffffu, gx, o);
+        gy += __shfl_xor_sync(0xffffffffu, gy, o);
+        gz += __shfl_xor_sync(0xffffffffu, gz, o);
+        ep += __shfl_xor_sync(0xffffffffu, ep, o);
+        mx += __shfl_xor_sync(0xffffffffu, mx, o);
+        my += __shfl_xor_sync(0xffffffffu, my, o);
+        mz += __shfl_xor_sync(0xffffffffu, mz, o);
+        em += __shfl_xor_sync(0xffffffffu, em, o);
+    }
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    if (real && lane == 0) {
         const double Fx = gx + mx, Fy = gy + my, Fz = gz + mz;
         a.F[s] = Fx; a.F[S + s] = Fy; a.F[2 * S + s] = Fz;
         double vx = a.v[s], vy = a.v[S + s], vz = a.v[2 * S + s];
@@ -1056,10 +1012,10 @@ __global__ void __launch_bounds__(128) k_force_mixed(DevArgs a, PotDev P, int in
             a.v[s] = vx; a.v[S + s] = vy; a.v[2 * S + s] = vz;
         }
         const float ux = (float)vx, uy = (float)vy, uz = (float)vz;
-        acc[0] += ep; acc[1] += em; acc[2] -= mz;
-        acc[3] += (float)(0.5 / MD_ACC) * (float)R.mass * (ux * ux + uy * uy + uz * uz);
+        acc[0] = ep; acc[1] = em; acc[2] = -mz;
+        acc[3] = (float)(0.5 / MD_ACC) * (float)R.mass * (ux * ux + uy * uy + uz * uz);
     }
-    cta_partials<4>(acc, a.part + 2 * (size_t)a.max_blocks, a.max_blocks, q);
+    cta_partials<4>(acc, a.part + 2 * (size_t)a.max_blocks, a.max_blocks, blockIdx.x);
 }
 
 // ============================================================================ Task 4, FP64
@@ -1193,7 +1149,6 @@ __global__ void __launch_bounds__(1024) k_reduce(DevArgs a, int atoms_per_block)
     int r = blockIdx.x;
     const RepDev &R = a.rep[r];
     int b0 = R.slot_off / atoms_per_block, b1 = (R.slot_off + R.n_slots) / atoms_per_block;
-    if (a.mixed) { b0 = R.chunk_off; b1 = R.chunk_off + R.n_chunks; }   // one partial per chunk
     __shared__ double sm[1024];
     double out[6];
     for (int t = 0; t < 6; ++t) {
@@ -1238,7 +1193,6 @@ cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s)
     k_scan1<<<nb, SB, SB * sizeof(int32_t), s>>>(a.cell_count, a.cell_start, a.scan_blk, a.total_cells);
     k_scan2<<<1, 1024, 1024 * sizeof(int32_t), s>>>(a.scan_blk, nb);
     k_scan3<<<nblk(a.total_cells, B), B, 0, s>>>(a, per_block);
-    if (a.mixed) k_windows<<<nblk(a.n_chunks, 128), 128, 0, s>>>(a);
     k_scatter<<<nblk(a.S, B), B, 0, s>>>(a);
     k_cellsort<<<nblk(a.total_cells, B), B, 0, s>>>(a);
     k_gather<<<nblk(a.S, B), B, 0, s>>>(a);
@@ -1255,34 +1209,30 @@ cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_refresh_pos4(const DevArgs &a, cudaStream_t s)
+{
+    k_refresh_pos4<<<nblk(a.S, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int TPA>
 static void dens_t(const DevArgs &a, const PotDev &p, int block, cudaStream_t s)
 {
-    k_density_fp64<TPA><<<a.S / (block / TPA), block, 0, s>>>(a, p);
+    int A = block / TPA;
+    if (a.mixed) k_density_mixed<TPA><<<a.S / A, block, 0, s>>>(a, p);
+    else k_density_fp64<TPA><<<a.S / A, block, 0, s>>>(a, p);
 }
 
 template <int TPA>
 static void force_t(const DevArgs &a, const PotDev &p, int block, int integ, cudaStream_t s)
 {
-    k_force_fp64<TPA><<<a.S / (block / TPA), block, 0, s>>>(a, p, integ);
-}
-
-static const size_t SMEM_DENS = MD_CAP * sizeof(float4);
-static const size_t SMEM_FORCE = MD_CAP * (sizeof(float4) + sizeof(float2));
-
-cudaError_t md_prepare_kernels()
-{
-    cudaError_t e = cudaFuncSetAttribute(k_density_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_DENS);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_force_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_FORCE);
+    int A = block / TPA;
+    if (a.mixed) k_force_mixed<TPA><<<a.S / A, block, 0, s>>>(a, p, integ);
+    else k_force_fp64<TPA><<<a.S / A, block, 0, s>>>(a, p, integ);
 }
 
 cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c, cudaStream_t s)
 {
-    if (a.mixed) {
-        k_density_mixed<<<a.n_chunks, 128, SMEM_DENS, s>>>(a, p);
-        return cudaGetLastError();
-    }
     switch (c.tpa) {
     case 1: dens_t<1>(a, p, c.block, s); break;
     case 2: dens_t<2>(a, p, c.block, s); break;
@@ -1294,10 +1244,6 @@ cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c
 
 cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, cudaStream_t s)
 {
-    if (a.mixed) {
-        k_force_mixed<<<a.n_chunks, 128, SMEM_FORCE, s>>>(a, p, integrate);
-        return cudaGetLastError();
-    }
     switch (c.tpa) {
     case 1: force_t<1>(a, p, c.block, integrate, s); break;
     case 2: force_t<2>(a, p, c.block, integrate, s); break;
