@@ -450,7 +450,10 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     INIT_FAIL(dalloc(h, &a.sfixed, S));
     INIT_FAIL(dalloc(h, &a.part, 6 * (size_t)a.max_blocks));
     double *d_xc0; int32_t *d_ccs, *d_ccc;
+    float4 *d_xc32;
     INIT_FAIL(dalloc(h, &d_xc0, 3 * (size_t)(cslots > 0 ? cslots : 1)));
+    INIT_FAIL(dalloc(h, &d_xc32, (size_t)(cslots > 0 ? cslots : 1)));
+    a.xc32 = d_xc32;
     INIT_FAIL(dalloc(h, &d_ccs, ccells > 0 ? ccells : 1));
     INIT_FAIL(dalloc(h, &d_ccc, ccells > 0 ? ccells : 1));
     a.xc0 = d_xc0; a.ccell_start = d_ccs; a.ccell_count = d_ccc;
@@ -462,6 +465,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
         std::vector<int32_t> horig(S, 0), htile(S / MD_TILE), hcell(cells);
         std::vector<uint8_t> hfix(S, 1);
         std::vector<double> hxc(3 * (size_t)(cslots > 0 ? cslots : 1), 0.0);
+        std::vector<float4> hxc32((size_t)(cslots > 0 ? cslots : 1));
         std::vector<int32_t> hccs(ccells > 0 ? ccells : 1, 0), hccc(ccells > 0 ? ccells : 1, 0);
         h->c_orig.assign(cslots > 0 ? cslots : 1, 0);
         std::vector<RepState> hrs(n_replicas);
@@ -498,6 +502,8 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
                 for (int c = 0; c < y.n_c; ++c) {
                     int t = R.c_off + fill[key[c]]++;
                     for (int k = 0; k < 3; ++k) hxc[(size_t)k * cslots + t] = y.x_c[3 * c + k];
+                    hxc32[t] = make_float4((float)(y.x_c[3 * c] - R.cg_lo[0]), (float)(y.x_c[3 * c + 1] - R.cg_lo[1]),
+                                           (float)(y.x_c[3 * c + 2] - R.cg_lo[2]), 0.0f);
                     h->c_orig[t] = c;
                 }
                 for (int k = 0; k < nc3; ++k) { hccs[R.ccell_off + k] = R.c_off + start[k]; hccc[R.ccell_off + k] = cnt[k]; }
@@ -515,6 +521,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
         CUI(cudaMemcpy(d_rs, hrs.data(), n_replicas * sizeof(RepState), cudaMemcpyHostToDevice));
         if (cslots > 0) {
             CUI(cudaMemcpy(d_xc0, hxc.data(), 3 * (size_t)cslots * sizeof(double), cudaMemcpyHostToDevice));
+            CUI(cudaMemcpy(d_xc32, hxc32.data(), (size_t)cslots * sizeof(float4), cudaMemcpyHostToDevice));
             CUI(cudaMemcpy(d_ccs, hccs.data(), ccells * sizeof(int32_t), cudaMemcpyHostToDevice));
             CUI(cudaMemcpy(d_ccc, hccc.data(), ccells * sizeof(int32_t), cudaMemcpyHostToDevice));
         }

@@ -151,6 +151,7 @@ struct DevArgs {
     uint8_t *sfixed;
     // indenter (sorted by indenter cell)
     const double *xc0;           // [3][C]
+    const float4 *xc32;          // [C] position relative to its replica's indenter-grid origin (FP32)
     const int32_t *ccell_start, *ccell_count;
     int32_t C;
     // block partial sums: [6][max_blocks]

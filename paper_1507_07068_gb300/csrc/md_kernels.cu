@@ -663,6 +663,7 @@ __global__ void __launch_bounds__(128) k_nbrc(DevArgs a)
     if (!(isfinite(xi[0]) && isfinite(xi[1]) && isfinite(xi[2]))) { a.cntc[s] = 0; return; }   // reported by k_bin
     unsigned long long mask[3];
     double reach = a.cutc * (1.0 + 1e-9) + 1e-9;
+    float q32[3], L32[3];
     for (int k = 0; k < 3; ++k) {
         double q = xi[k] - (k == 2 ? z_ind : 0.0);
         double ctr = R.cg_lo[k] + 0.5 * R.cg_n[k] * R.cg_w[k];
@@ -674,7 +675,12 @@ __global__ void __launch_bounds__(128) k_nbrc(DevArgs a)
         }
         mask[k] |= cell_bits(q, reach, R.cg_lo[k], R.cg_w[k], R.cg_n[k]);
         if (!mask[k]) { a.cntc[s] = 0; return; }
+        q32[k] = (float)(q - R.cg_lo[k]);
+        L32[k] = (float)R.L[k];
     }
+    // FP32 prefilter (indenter frame, positions below ~100 A: error < 1e-4 A^2 on y^2); the
+    // exact FP64 test decides every candidate within 1e-4 (relative) of the cut-off
+    const float cut2f = (float)a.cutc2, lo2 = cut2f * (1.0f - 1e-4f), hi2 = cut2f * (1.0f + 1e-4f);
     int m = 0;
     for (unsigned long long m2 = mask[2]; m2; m2 &= m2 - 1) {
         int q2 = __ffsll((long long)m2) - 1;
@@ -685,11 +691,21 @@ __global__ void __launch_bounds__(128) k_nbrc(DevArgs a)
                 int key = R.ccell_off + (q2 * R.cg_n[1] + q1) * R.cg_n[0] + q0;
                 int b = a.ccell_start[key], e = b + a.ccell_count[key];
                 for (int c = b; c < e; ++c) {
-                    double ddx = mi_exact(__dsub_rn(a.xc0[c], xi[0]), R.per[0], R.L[0]);
-                    double ddy = mi_exact(__dsub_rn(a.xc0[C + c], xi[1]), R.per[1], R.L[1]);
-                    double zc = __dadd_rn(a.xc0[2 * C + c], z_ind);
-                    double ddz = mi_exact(__dsub_rn(zc, xi[2]), R.per[2], R.L[2]);
-                    if (norm2_exact(ddx, ddy, ddz) < a.cutc2) {
+                    const float4 pc = __ldg(&a.xc32[c]);
+                    float fx = pc.x - q32[0], fy = pc.y - q32[1], fz = pc.z - q32[2];
+                    if (R.per[0]) fx -= L32[0] * rintf(fx / L32[0]);
+                    if (R.per[1]) fy -= L32[1] * rintf(fy / L32[1]);
+                    const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+                    if (r2f > hi2) continue;
+                    bool in = r2f < lo2;
+                    if (!in) {
+                        double ddx = mi_exact(__dsub_rn(a.xc0[c], xi[0]), R.per[0], R.L[0]);
+                        double ddy = mi_exact(__dsub_rn(a.xc0[C + c], xi[1]), R.per[1], R.L[1]);
+                        double zc = __dadd_rn(a.xc0[2 * C + c], z_ind);
+                        double ddz = mi_exact(__dsub_rn(zc, xi[2]), R.per[2], R.L[2]);
+                        in = norm2_exact(ddx, ddy, ddz) < a.cutc2;
+                    }
+                    if (in) {
                         if (m < a.kcmax) a.nbrc[(size_t)m * S + s] = c;
                         ++m;
                     }
