@@ -115,13 +115,34 @@ class ClockSampler:
 
 
 def make_workload(name: str, rank: int):
-    wl = mi.make_workload(name)
-    reps = wl.replicas
-    if rank and name != "batched":
-        # weak scaling: each rank runs its own replica of the workload (fresh velocity draw)
-        nx, ny, nz, R, nf, _ = mi.PRESETS[name]
-        reps = [mi.make_replica(name, nx, ny, nz, R, 300.0, seed=1507 * 1000 + 97 * rank, n_fixed_planes=nf)]
-    return wl, reps
+    """The replicas rank `rank` runs.  Weak scaling: every rank runs the whole workload on
+    its own GPU, rank 0 with the preset seed, other ranks with their own velocity draw
+    (and, for the batched set, their own replica draw); ranks never exchange data."""
+    if rank == 0:
+        wl = mi.make_workload(name)
+        return wl, wl.replicas
+    if name == "batched":
+        reps = mi.batched_replicas(256, seed_base=1507 * 1000 + 100000 * rank)
+        return mi.Workload("batched", reps, steps=1000), reps
+    nx, ny, nz, R, nf, steps = mi.PRESETS[name]
+    reps = [mi.make_replica(name, nx, ny, nz, R, 300.0, seed=1507 * 1000 + 97 * rank, n_fixed_planes=nf)]
+    return mi.Workload(name, reps, steps=steps), reps
+
+
+def max_over_ranks(ms: float, dist) -> float:
+    """The job's time: the slowest rank's (ranks start together after a barrier)."""
+    if dist is None:
+        return ms
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_cr_per_rank: int, world: int, steps: int, ms_max: float) -> float:
+    """Whole-job throughput: atoms of all ranks times steps over the slowest rank's time."""
+    return n_cr_per_rank * world * steps / (ms_max * 1e-3)
 
 
 def algorithmic_bytes(kernel: str, kmean: float, precision: str) -> float:
@@ -196,12 +217,8 @@ def run_gpu(args):
     ms = ev0.elapsed_time(ev1)
     e1 = sim.energy(0)
     rebuilds = e1["rebuilds"] - e0["rebuilds"]
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = n_cr * ws * args.steps / (t_max * 1e-3)
+    t_max = max_over_ranks(ms, dist)
+    value = job_value(n_cr, ws, args.steps, t_max)
 
     # ---- per-kernel device time (direct launches with CUDA events around each phase)
     prof = sim.step_profiled(args.profile_steps)
