@@ -161,7 +161,12 @@ int rebuild_growing(md_t *h)
             int k = st.max_cnt + 16;
             int32_t *p;
             if ((rc = dalloc(h, &p, (size_t)k * h->a.S))) return rc;
-            h->a.nbr = p; h->a.kmax = k; grow = true;
+            h->a.nbr = p;
+            if (h->a.mixed) {
+                if ((rc = dalloc(h, &p, (size_t)k * h->a.S))) return rc;
+                h->a.inner = p;
+            }
+            h->a.kmax = k; grow = true;
         }
         if ((st.err & MDE_COVERFLOW) && st.max_cntc > h->a.kcmax) {
             int k = st.max_cntc + 32;
@@ -435,6 +440,8 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     INIT_FAIL(dalloc(h, &a.fixed, S));
     INIT_FAIL(dalloc(h, &a.nbr, (size_t)a.kmax * S));
     INIT_FAIL(dalloc(h, &a.cnt, S));
+    INIT_FAIL(dalloc(h, &a.inner, a.mixed ? (size_t)a.kmax * S : 1));
+    INIT_FAIL(dalloc(h, &a.icnt, S));
     INIT_FAIL(dalloc(h, &a.nbrc, (size_t)a.kcmax * S));
     INIT_FAIL(dalloc(h, &a.cntc, S));
     INIT_FAIL(dalloc(h, &a.key, S));

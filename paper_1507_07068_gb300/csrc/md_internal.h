@@ -141,6 +141,8 @@ struct DevArgs {
     float4 *pos4;
     double2 *fm64;
     float2 *fm32;
+    int32_t *inner, *icnt;       // mixed precision: entries of the Verlet list within rc at the
+                                 // current positions (the inner list, rebuilt every step)
     int32_t *cellc, *orig;
     uint8_t *fixed;
     int32_t *nbr, *cnt, *nbrc, *cntc;

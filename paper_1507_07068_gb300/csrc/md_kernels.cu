@@ -834,23 +834,35 @@ __device__ __forceinline__ void disp(const float4 &pi, const float4 &pj, unsigne
 // traffic per pair; its deviation from the forms is below 1e-11).  f: for an even integer
 // beta the power is (r_e^2/r^2)^(beta/2) by multiplication; Phi: Taylor form about the
 // double root, with t = r/r_e - d formed with the rounding of 1/r_e and d compensated.
+// r_e^2 / r^2 from one reciprocal refined by a Newton step (about 1 ulp, no IEEE divide)
 __device__ __forceinline__ float f_direct(const Pot32 &Q, float r2, float r)
 {
-    float fr;
     if (Q.ipow > 0) {
-        const float q = Q.re2 / r2;
-        fr = q;
-        for (int k = 1; k < Q.ipow; ++k) fr *= q;
-        fr *= Q.f_e;
-    } else {
-        fr = exp2f(Q.lf0 - Q.beta * log2f(r));
+        const float rcp = __fdividef(1.0f, r2);
+        float q = Q.re2 * rcp;
+        q = fmaf(rcp, fmaf(-q, r2, Q.re2), q);
+        float fr;
+        if (Q.ipow == 3) {
+            fr = q * q * q;
+        } else {
+            fr = q;
+            for (int k = 1; k < Q.ipow; ++k) fr *= q;
+        }
+        return fr * Q.f_e;
     }
-    return fr;
+    return exp2f(Q.lf0 - Q.beta * log2f(r));
+}
+
+// 1/sqrt(r2) refined by a Newton step
+__device__ __forceinline__ float rsqrt_nr(float r2)
+{
+    const float y = rsqrtf(r2);
+    return y * fmaf(-0.5f * r2 * y, y, 1.5f);
 }
 
 __device__ __forceinline__ float fa_val(const Pot32 &Q, float r2)
 {
-    const float r = sqrtf(r2);
+    const float r = r2 * rsqrt_nr(r2);
     return f_direct(Q, r2, r) - Q.f_rc - (r - Q.rc) * Q.df_rc;
 }
 
@@ -883,6 +895,7 @@ __global__ void __launch_bounds__(256) k_density_mixed(DevArgs a, PotDev P)
     const bool real = (s - R.slot_off) < R.n_atoms;
     const size_t S = a.S;
     float rho = 0.f, Ps = 0.f;
+    int m = 0;   // inner-list entries of this lane
     if (real) {
         const float4 pi = a.pos4[s];
         const PairGeom G = pair_geom(R, __float_as_int(pi.w));
@@ -906,14 +919,25 @@ __global__ void __launch_bounds__(256) k_density_mixed(DevArgs a, PotDev P)
                     const float f = fa_val(Q, r2);
                     rho += f;
                     Ps = fmaf(f, f, Ps);
+                    // the inner list (Sec. 2.6): entries within rc at these positions, in
+                    // lane-interleaved rows so each lane owns rows lane, lane + TPA, ...
+                    a.inner[(size_t)(m * TPA + lane) * S + s] = (int32_t)e[u];
+                    ++m;
                 }
             }
         }
     }
+    int mmax = m;
 #pragma unroll
     for (int o = TPA / 2; o > 0; o >>= 1) {
         rho += __shfl_xor_sync(0xffffffffu, rho, o);
         Ps += __shfl_xor_sync(0xffffffffu, Ps, o);
+        mmax = max(mmax, __shfl_xor_sync(0xffffffffu, mmax, o));
+    }
+    // rows of lanes with fewer entries are padded with the atom itself (skipped by k_force)
+    if (real) {
+        for (int k = m; k < mmax; ++k) a.inner[(size_t)(k * TPA + lane) * S + s] = s;
+        if (lane == 0) a.icnt[s] = mmax * TPA;
     }
     float acc[2] = {0.f, 0.f};
     if (real && lane == 0) {
@@ -949,13 +973,13 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
         const float4 pi = a.pos4[s];
         const PairGeom G = pair_geom(R, __float_as_int(pi.w));
         const float2 fmi = a.fm32[s];
-        const int n = a.cnt[s];
+        const int n = a.icnt[s];
         for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
             unsigned e[MD_UNROLL];
 #pragma unroll
             for (int u = 0; u < MD_UNROLL; ++u) {
                 const int k = k0 + u * TPA;
-                e[u] = k < n ? (unsigned)__ldg(&a.nbr[(size_t)k * S + s]) : (unsigned)s;
+                e[u] = k < n ? (unsigned)__ldg(&a.inner[(size_t)k * S + s]) : (unsigned)s;
             }
             float4 pj[MD_UNROLL];
             float2 fmj[MD_UNROLL];
@@ -970,8 +994,8 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
                 float dx, dy, dz;
                 disp(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (k0 + u * TPA < n && r2 < Q.rc2) {
-                    const float rinv = rsqrtf(r2);
+                if ((e[u] & MD_J_MASK) != (unsigned)s) {   // inner entries are within rc; padding is the atom itself
+                    const float rinv = rsqrt_nr(r2);
                     float f, df, ph, dph;
                     fa_phi(Q, r2, rinv, f, df, ph, dph);
                     const float coef = fmaf(fmi.x + fmj[u].x, df, fmaf((fmi.y + fmj[u].y) * 2.0f * f, df, dph)) * rinv;
