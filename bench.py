@@ -145,15 +145,36 @@ def job_value(n_cr_per_rank: int, world: int, steps: int, ms_max: float) -> floa
     return n_cr_per_rank * world * steps / (ms_max * 1e-3)
 
 
-def algorithmic_bytes(kernel: str, kmean: float, precision: str) -> float:
-    """Bytes per Cr atom that the kernel must move (int32 list, neighbour data counted once)."""
+def algorithmic_bytes(kernel: str, kmean: float, kin: float, precision: str) -> float:
+    """Bytes per Cr atom that the kernel must move (int32 lists, neighbour data counted
+    once): K = Verlet-list length, K_in = inner-list length (entries within rc)."""
     if precision == "mixed":
         if kernel == "density":
-            return 4 * kmean + 28      # cnt 4 + list 4K + float4 position 16 + (F', M') write 8
-        return 4 * kmean + 44          # cnt 4 + list 4K + position 16 + (F', M') 8 + force write 16
+            # cnt 4 + list 4K + float4 position 16 + (F', M') out 8 + inner list out 4K_in + icnt out 4
+            return 4 * kmean + 4 * kin + 32
+        # icnt 4 + inner 4K_in + position 16 + (F', M') 8 + F out 24 + v in/out 48 + fixed 1 + cntc 4
+        return 4 * kin + 105
     if kernel == "density":
-        return 4 * kmean + 44          # cnt + list + 3 FP64 coordinates 24 + (F', M') 16
-    return 4 * kmean + 68              # cnt + list + coordinates 24 + (F', M') 16 + force write 24
+        return 4 * kmean + 44          # cnt + list + 3 FP64 coordinates 24 + (F', M') out 16
+    return 4 * kmean + 121             # cnt + list + coordinates 24 + (F', M') 16 + F 24 + v 48 + fixed + cntc
+
+
+def inner_mean(sim, rep, rc: float, sample: int = 20000, seed: int = 0) -> float:
+    """Mean number of Verlet-list entries within rc at the current positions (the inner
+    list length), from a random sample of atoms of replica 0."""
+    x = sim.state(0)[0]
+    _, cnt, nbr = sim.neighbors(0, 0)
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(len(x), min(sample, len(x)), replace=False)
+    nb = nbr[idx]
+    valid = np.arange(nb.shape[1])[None, :] < cnt[idx][:, None]
+    d = x[np.where(valid, nb, 0)] - x[idx][:, None, :]
+    L = rep.box_hi - rep.box_lo
+    for k in range(3):
+        if rep.periodic[k]:
+            d[..., k] -= np.round(d[..., k] / L[k]) * L[k]
+    r2 = (d * d).sum(-1)
+    return float(((r2 < rc * rc) & valid).sum(1).mean())
 
 
 def kernel_source_hash() -> str:
@@ -197,7 +218,8 @@ def run_gpu(args):
     n_cr = sum(r.n_cr for r in reps)
     n_c = sum(r.n_c for r in reps)
     stream = torch.cuda.current_stream()
-    sim = md.MD(reps, params, precision=args.precision, skin=0.3, tpa=args.tpa, block=args.block)
+    sim = md.MD(reps, params, precision=args.precision, skin=args.skin, rebuild_every=args.rebuild_every,
+                tpa=args.tpa, block=args.block, use_graph=not args.no_graph)
 
     def barrier():
         if dist is not None:
@@ -224,10 +246,11 @@ def run_gpu(args):
     prof = sim.step_profiled(args.profile_steps)
     _, cnt, _ = sim.neighbors(0, 0, kmax=1)
     kmean = float(cnt.mean())
+    kin = inner_mean(sim, reps[0], params["rc"])
     phases = {k: prof[k] / prof["steps"] for k in ("skin", "rebuild", "verlet1", "density", "force", "reduce")}
     dom = "force" if phases["force"] >= phases["density"] else "density"
     peak, peak_kind = load_peaks()
-    bytes_per_launch = algorithmic_bytes(dom, kmean, args.precision) * n_cr
+    bytes_per_launch = algorithmic_bytes(dom, kmean, kin, args.precision) * n_cr
     achieved = bytes_per_launch / (phases[dom] * 1e-3) / 1e9
     traffic = dram_traffic(args.workload, args.precision, dom)
 
@@ -296,19 +319,23 @@ def run_gpu(args):
         "dtype": "f32+f64" if args.precision == "mixed" else "f64",
         "data": "synthetic (seeded BCC film + diamond hemisphere, Maxwell-Boltzmann velocities)",
         "config": {"workload": WORKLOAD_TEXT[args.workload], "n_cr": n_cr * ws, "n_c": n_c * ws,
-                   "precision": args.precision, "potential": "cubic Hermite tables, shifted-force cut-offs",
-                   "skin_A": 0.3, "rebuild": "skin/2 rule (conditional graph node)",
-                   "rebuilds_in_timed_region": rebuilds, "tpa": args.tpa or 4, "block": args.block or 128,
+                   "precision": args.precision,
+                   "potential": ("analytic FP32 forms in the pair loops, FP64 state" if args.precision == "mixed"
+                                 else "cubic Hermite tables (FP64)") + ", shifted-force cut-offs",
+                   "skin_A": args.skin,
+                   "rebuild": ("every %d steps" % args.rebuild_every) if args.rebuild_every
+                   else "displacement rule 2 max|dx| > skin (conditional graph node)",
+                   "rebuilds_in_timed_region": rebuilds, "tpa": args.tpa or 1, "block": args.block or 128,
                    "l2": "working set larger than L2 (neighbour list alone %.0f MB)" % (n_cr * kmean * 4 / 1e6),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
-                     "algorithmic_bytes_per_atom": algorithmic_bytes(dom, kmean, args.precision),
-                     "mean_list_length": kmean, "launch_ms": phases[dom]},
+                     "algorithmic_bytes_per_atom": algorithmic_bytes(dom, kmean, kin, args.precision),
+                     "mean_list_length": kmean, "mean_inner_length": kin, "launch_ms": phases[dom]},
         "phases_ms_per_step": phases,
         "clocks": clk.summary(),
         "e2e": e2e,
-        "gpu_launches": int(6 * args.steps + 13 * rebuilds),
+        "gpu_launches": int(4 * args.steps + 13 * rebuilds + 1),
         "variants": variants,
     }
     if cpu is not None:
@@ -408,6 +435,10 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--tpa", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--skin", type=float, default=0.3)
+    ap.add_argument("--rebuild-every", type=int, default=0)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="direct launches instead of graph replay (for launch-list profiling)")
     ap.add_argument("--profile-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--fp64-steps", type=int, default=40)

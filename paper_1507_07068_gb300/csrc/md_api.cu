@@ -339,7 +339,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
 
     const double cut = h->pot_h.rc + opt->skin, cutc = h->pot_h.rc_morse + opt->skin;
     // ---- layout
-    int64_t slots = 0, cells = 0, ccells = 0, real = 0, cslots = 0;
+    int64_t slots = 0, cells = 0, ccells = 0, real = 0, cslots = 0, ncen = 0;
     size_t max_n = 1;
     h->rep.resize(n_replicas);
     for (int r = 0; r < n_replicas; ++r) {
@@ -360,9 +360,15 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
                 INIT_FAIL(fail(h, MD_ERR_ARG, "replica %d: axis %d needs %d cells, more than %d", r, k, n, (1 << MD_CELL_BITS) - 1));
             R.nc[k] = n;
             R.w[k] = R.L[k] / n;
+            R.iw[k] = 1.0 / R.w[k];
+            R.iL[k] = 1.0 / R.L[k];
             R.w32[k] = (float)R.w[k];
             R.wc[k] = (double)R.w32[k];
             R.dL32[k] = (float)(R.L[k] - n * R.wc[k]);
+            R.pad32[k] = (float)(1e-4 + (n + 1) * fabs(R.w[k] - R.wc[k]));
+            R.lo32[k] = (float)R.lo[k];
+            R.L32[k] = (float)R.L[k];
+            R.iL32[k] = (float)(1.0 / R.L[k]);
         }
         R.cell_off = (int32_t)cells;
         R.n_cells = R.nc[0] * R.nc[1] * R.nc[2];
@@ -378,6 +384,8 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
         for (int i = 0; i < y.n_cr; ++i) nmob += (y.fixed && y.fixed[i]) ? 0 : 1;
         R.n_mobile = nmob;
         R.v_ind = y.v_indenter; R.dt = y.dt; R.mass = y.mass_cr; R.acc_per_f = MD_ACC / y.mass_cr;
+        R.hk = 0.5 * R.dt * R.acc_per_f;
+        for (int k = 0; k < 3; ++k) { R.cen_off[k] = (int32_t)ncen; ncen += R.nc[k]; }
         double ztop = -1e300;
         for (int i = 0; i < y.n_cr; ++i) ztop = std::max(ztop, y.x_cr[3 * i + 2]);
         R.z_surface0 = ztop;
@@ -397,6 +405,8 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
                 if (n < 1) n = 1;
                 if (n > 64) n = 64;   // one 64-bit cell set per axis in k_nbrc
                 R.cg_n[k] = n; R.cg_w[k] = ext / n; R.cg_lo[k] = bl[k] - 0.5e-6;
+                R.cg_ctr32[k] = (float)(R.cg_lo[k] + 0.5 * n * R.cg_w[k]);
+                R.cg_half32[k] = (float)(0.5 * n * R.cg_w[k]);
                 if (R.per[k] && !(R.L[k] > 2.0 * cutc))
                     INIT_FAIL(fail(h, MD_ERR_ARG, "replica %d: periodic length %.2f A on axis %d must exceed twice the Morse reach rc_morse + skin = %.2f A", r, R.L[k], k, cutc));
             }
@@ -465,6 +475,17 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     INIT_FAIL(dalloc(h, &d_ccc, ccells > 0 ? ccells : 1));
     a.xc0 = d_xc0; a.ccell_start = d_ccs; a.ccell_count = d_ccc;
     INIT_FAIL(dalloc(h, &h->stage, 6 * max_n));
+    double *d_cen;
+    INIT_FAIL(dalloc(h, &d_cen, ncen));
+    a.cen = d_cen;
+    {
+        std::vector<double> hc(ncen);
+        for (int r = 0; r < n_replicas; ++r)
+            for (int k = 0; k < 3; ++k)
+                for (int c = 0; c < h->rep[r].nc[k]; ++c)
+                    hc[h->rep[r].cen_off[k] + c] = h->rep[r].lo[k] + (c + 0.5) * h->rep[r].wc[k];
+        CUI(cudaMemcpy(d_cen, hc.data(), ncen * sizeof(double), cudaMemcpyHostToDevice));
+    }
 
     // ---- host staging in slot order (initial slot order = caller order)
     {
@@ -728,6 +749,7 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
         CU(cudaMemcpyAsync(h->stage, x3n, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         k_state_in<<<(n + 255) / 256, 256, 0, h->stream>>>(h->stage, h->a.x, h->a.orig, R.slot_off, n, h->a.S);
         CU(cudaGetLastError());
+        CU(cudaMemsetAsync(&h->a.st->pos4_ok, 0, sizeof(int32_t), h->stream));   // pos4 is stale now
     }
     if (v3n) {
         double *st2 = h->stage + 3 * (size_t)n;

@@ -81,12 +81,16 @@ struct PotDev {
 // static per-replica description (read-only on the device)
 struct RepDev {
     double lo[3], hi[3], L[3], w[3];  // Cr cell grid; L = hi - lo; w = L / nc (binning)
+    double iw[3], iL[3];              // 1 / w, 1 / L (fast path of the exact quotient floors)
     int32_t per[3], nc[3];
     // FP32 cell-relative positions are taken about the centres lo + (c + 1/2) w32 (w32 =
     // w rounded to FP32), so two cells' centres differ by an exact multiple of w32, plus
     // dL32 = L - nc w32 when the pair crosses a periodic boundary
     float w32[3], dL32[3];
     double wc[3];                     // (double) w32
+    // in the w32 frame a cell's box is off by at most c |w - w32| (c < nc): the margin that
+    // k_nbr adds to the half-width of a stencil cell's box
+    float pad32[3];
     int32_t cell_off, n_cells;
     int32_t slot_off, n_atoms, n_slots;  // first slot (TILE aligned), real atoms, slots incl. padding
     int32_t real_off;                    // atoms of the replicas before (unpadded)
@@ -95,8 +99,13 @@ struct RepDev {
     int32_t c_off, n_c;                  // indenter slots
     double cg_lo[3], cg_w[3];            // indenter cell grid in its own frame (t = 0)
     int32_t cg_n[3], ccell_off;
+    // FP32 copies for the rejection test of k_nbrc: Cr grid origin, box lengths, and the
+    // indenter grid's centre and half extent
+    float lo32[3], L32[3], iL32[3], cg_ctr32[3], cg_half32[3];
     // dynamics
     double v_ind, dt, mass, acc_per_f;   // acc_per_f = MD_ACC / mass
+    double hk;                           // dt acc_per_f / 2, the half-kick factor
+    int32_t cen_off[3];                  // per-axis cell centres lo + (c + 1/2) w32 in DevArgs::cen
     double z_surface0, zc_min0;
 };
 
@@ -118,6 +127,8 @@ struct DevStatus {
     int32_t err;            // MDE_* bits
     int32_t any_rebuild;    // rebuild decided this step (host-readable)
     int32_t max_cnt, max_cntc;
+    int32_t pos4_ok;        // pos4 holds every atom's current position about its cell's centre
+    int32_t pad_;
     int64_t step, rebuilds, since_build;
 };
 
@@ -135,6 +146,7 @@ struct DevArgs {
     RepEnergy *en;
     DevStatus *st;
     const int32_t *tile_rep;     // replica of each tile
+    const double *cen;           // cell-centre coordinates per axis (see RepDev::cen_off)
     const int32_t *cell_rep;     // replica of each cell
     // per-atom
     double *x, *v, *F, *xb;      // [3][S]

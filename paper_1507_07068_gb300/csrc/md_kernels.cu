@@ -200,14 +200,25 @@ __device__ __forceinline__ int cell_z(int p) { return (p >> (2 * MD_CELL_BITS)) 
 // ---- exact FP64 geometry of the list build and the skin test: every operation is a
 // separately rounded IEEE operation (no FMA contraction), so cell keys and neighbour
 // sets are reproducible on any IEEE machine from the same positions.
-__device__ __forceinline__ double wrap_exact(double x, double lo, double L)
+// floor(RN(d / w)) without the FP64 divide on the common path: q = d * (1/w) is within
+// 3.4e-16 |q| of RN(d / w); when |q| < 1e6 and its fractional part is farther than 1e-9
+// from an integer, both have the same floor.  Otherwise the divide decides.
+__device__ __forceinline__ double floor_quot(double d, double w, double iw)
 {
-    double m = floor(__ddiv_rn(__dsub_rn(x, lo), L));
+    const double q = __dmul_rn(d, iw);
+    const double t = floor(q);
+    const double f = __dsub_rn(q, t);
+    if (fabs(q) < 1.0e6 && f > 1.0e-9 && f < 1.0 - 1.0e-9) return t;
+    return floor(__ddiv_rn(d, w));
+}
+__device__ __forceinline__ double wrap_exact(double x, double lo, double L, double iL)
+{
+    const double m = floor_quot(__dsub_rn(x, lo), L, iL);
     return __dsub_rn(x, __dmul_rn(m, L));
 }
-__device__ __forceinline__ int cell_exact(double x, double lo, double w, int n)
+__device__ __forceinline__ int cell_exact(double x, double lo, double w, double iw, int n)
 {
-    double t = floor(__ddiv_rn(__dsub_rn(x, lo), w));
+    const double t = floor_quot(__dsub_rn(x, lo), w, iw);
     if (!(t >= 0.0)) return 0;
     if (t > (double)(n - 1)) return n - 1;
     return (int)t;
@@ -406,6 +417,15 @@ __global__ void k_zero_i32(int32_t *p, int n)
 }
 
 // wrap into the periodic box, FP64 cell coordinates, cell key, histogram
+// Cell of every atom.  The exact result is cell_exact(wrap_exact(x)) in FP64.  When pos4
+// holds the current positions (pos4_ok: k_verlet1 of the mixed path keeps it current,
+// k_copyback writes it) the same result comes from the FP32 cell-relative position p
+// about the old cell's centre: an atom farther than pad32 from every face of its old cell
+// or of a face-adjacent cell is in that cell (pad32 bounds the w32 frame's drift from the
+// FP64 grid plus the rounding of p), and a crossing of a periodic face moves x by exactly
+// -+L, which is what wrap_exact computes there.  Every other atom (within pad32 of a face,
+// moved by more than one cell, leaving a non-periodic domain, or not finite) takes the
+// FP64 path.
 __global__ void k_bin(DevArgs a)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -415,26 +435,62 @@ __global__ void k_bin(DevArgs a)
     const RepDev &R = a.rep[r];
     if (s - R.slot_off >= R.n_atoms) return;
     int c[3];
-    bool lost = false;
+    bool done = false;
+    if (*(volatile int32_t *)&a.st->pos4_ok) {
+        const float4 p = a.pos4[s];
+        const int pc = __float_as_int(p.w);
+        const float pr[3] = {p.x, p.y, p.z};
+        const int cc[3] = {cell_x(pc), cell_y(pc), cell_z(pc)};
+        int wrap[3];
+        bool ok = true;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        double xk = a.x[(size_t)k * a.S + s];
-        if (xk != xk) lost = true;
-        if (R.per[k]) {
-            xk = wrap_exact(xk, R.lo[k], R.L[k]);
-            a.x[(size_t)k * a.S + s] = xk;
-        } else if (xk < R.lo[k] || xk > R.hi[k]) {
-            lost = true;
+        for (int k = 0; k < 3; ++k) {
+            const float hw = 0.5f * R.w32[k], pad = R.pad32[k], q = pr[k];
+            int d = 0;
+            if (fabsf(q) < hw - pad) d = 0;
+            else if (q > hw + pad && q < 3.0f * hw - pad) d = 1;
+            else if (q < -hw - pad && q > pad - 3.0f * hw) d = -1;
+            else ok = false;
+            int cn = cc[k] + d;
+            wrap[k] = 0;
+            if (cn < 0 || cn >= R.nc[k]) {
+                if (!R.per[k]) ok = false;
+                wrap[k] = cn < 0 ? -1 : 1;
+                cn -= wrap[k] * R.nc[k];
+            }
+            c[k] = cn;
         }
-        c[k] = cell_exact(xk, R.lo[k], R.w[k], R.nc[k]);
+        if (ok) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (wrap[k]) {
+                    const double xk = a.x[(size_t)k * a.S + s];
+                    a.x[(size_t)k * a.S + s] = wrap[k] > 0 ? __dsub_rn(xk, R.L[k]) : __dadd_rn(xk, R.L[k]);
+                }
+            done = true;
+        }
     }
-    if (lost) atomicOr(&a.st->err, MDE_LOST);
+    if (!done) {
+        bool lost = false;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double xk = a.x[(size_t)k * a.S + s];
+            if (xk != xk) lost = true;
+            if (R.per[k]) {
+                xk = wrap_exact(xk, R.lo[k], R.L[k], R.iL[k]);
+                a.x[(size_t)k * a.S + s] = xk;
+            } else if (xk < R.lo[k] || xk > R.hi[k]) {
+                lost = true;
+            }
+            c[k] = cell_exact(xk, R.lo[k], R.w[k], R.iw[k], R.nc[k]);
+        }
+        if (lost) atomicOr(&a.st->err, MDE_LOST);
+    }
     int key = R.cell_off + (c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0];
     a.key[s] = key;
     atomicAdd(&a.cell_count[key], 1);
 }
 
-// exclusive scan, phase 1: per-CTA scan of 2 * blockDim elements, CTA totals to blk
 __global__ void k_scan1(const int32_t *in, int32_t *out, int32_t *blk, int n)
 {
     extern __shared__ int32_t sh[];
@@ -536,18 +592,18 @@ __global__ void k_gather(DevArgs a)
 }
 
 // FP32 position of slot s about its cell centre lo + (c + 1/2) w32 (see RepDev)
-__device__ __forceinline__ float4 rel_pos3(const RepDev &R, int pc, double x0, double x1, double x2)
+__device__ __forceinline__ float4 rel_pos3(const DevArgs &a, const RepDev &R, int pc, double x0, double x1, double x2)
 {
-    double c0 = fma((double)cell_x(pc) + 0.5, R.wc[0], R.lo[0]);
-    double c1 = fma((double)cell_y(pc) + 0.5, R.wc[1], R.lo[1]);
-    double c2 = fma((double)cell_z(pc) + 0.5, R.wc[2], R.lo[2]);
+    const double c0 = __ldg(&a.cen[R.cen_off[0] + cell_x(pc)]);
+    const double c1 = __ldg(&a.cen[R.cen_off[1] + cell_y(pc)]);
+    const double c2 = __ldg(&a.cen[R.cen_off[2] + cell_z(pc)]);
     return make_float4((float)(x0 - c0), (float)(x1 - c1), (float)(x2 - c2), __int_as_float(pc));
 }
 
 __device__ __forceinline__ float4 rel_pos(const DevArgs &a, const RepDev &R, int s)
 {
     size_t S = a.S;
-    return rel_pos3(R, a.cellc[s], a.x[s], a.x[S + s], a.x[2 * S + s]);
+    return rel_pos3(a, R, a.cellc[s], a.x[s], a.x[S + s], a.x[2 * S + s]);
 }
 
 __global__ void k_copyback(DevArgs a)
@@ -568,6 +624,7 @@ __global__ void k_copyback(DevArgs a)
     a.orig[s] = a.sorig[s];
     a.fixed[s] = a.sfixed[s];
     a.pos4[s] = rel_pos(a, R, s);   // also used by the FP32 prefilter of k_nbr
+    if (s == 0) a.st->pos4_ok = 1;
 }
 
 // full Cr-Cr Verlet list: every slot j != i in the 27-cell stencil with |x_j - x_i|^2 <
@@ -575,6 +632,13 @@ __global__ void k_copyback(DevArgs a)
 // than 1e-5 (relative) from the cut-off is decided by the FP32 value (its error is below
 // 2e-6 relative for atoms inside their cells); the rest take the exact FP64 test, so the
 // set equals the all-FP64 set bit for bit.
+//
+// With no lost atom (k_bin ran first and raised no MDE_LOST) every atom lies in its cell's
+// box up to rounding, the box being off the w32-frame cell by at most pad32 (the frame's
+// drift c |w - w32| plus 1e-4 A), so (i) a stencil cell whose widened box is farther than
+// the cut-off from atom i holds no neighbour and is skipped, and (ii) every candidate is an
+// in-cell atom.  Otherwise (an atom clamped into an edge cell from outside the domain) no
+// cell is skipped and every candidate takes the FP64 test.
 __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -588,44 +652,56 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
     const float cut2 = (float)a.cut2;
     const float lo2 = cut2 * (1.0f - 1e-5f), hi2 = cut2 * (1.0f + 1e-5f);
     const float wx = R.w32[0], wy = R.w32[1], wz = R.w32[2];
-    const float lim = 0.75f * fminf(wx, fminf(wy, wz));   // beyond: atom clamped outside its cell
-    const bool ifar = fabsf(pi.x) > lim || fabsf(pi.y) > lim || fabsf(pi.z) > lim;
+    const bool exact_all = (*(volatile int *)&a.st->err & MDE_LOST) != 0;
+    const float hx = fmaf(0.5f, wx, R.pad32[0]), hy = fmaf(0.5f, wy, R.pad32[1]), hz = fmaf(0.5f, wz, R.pad32[2]);
     int m = 0;
     for (int dz = -1; dz <= 1; ++dz) {
         int q2 = c2 + dz;
         if (q2 < 0 || q2 >= R.nc[2]) { if (!R.per[2]) continue; q2 = (q2 + R.nc[2]) % R.nc[2]; }
+        const float oz = fmaf((float)(c2 + dz != q2) * dz, R.dL32[2], dz * wz);
+        const float gz = fmaxf(fabsf(oz - pi.z) - hz, 0.0f);
         for (int dy = -1; dy <= 1; ++dy) {
             int q1 = c1 + dy;
             if (q1 < 0 || q1 >= R.nc[1]) { if (!R.per[1]) continue; q1 = (q1 + R.nc[1]) % R.nc[1]; }
+            const float oy = fmaf((float)(c1 + dy != q1) * dy, R.dL32[1], dy * wy);
+            const float gy = fmaxf(fabsf(oy - pi.y) - hy, 0.0f);
+            const float gyz = fmaf(gy, gy, gz * gz);
             for (int dx = -1; dx <= 1; ++dx) {
                 int q0 = c0 + dx;
                 if (q0 < 0 || q0 >= R.nc[0]) { if (!R.per[0]) continue; q0 = (q0 + R.nc[0]) % R.nc[0]; }
+                // centre offset of the stencil cell: d w32, plus d dL32 through a periodic face
+                const float ox = fmaf((float)(c0 + dx != q0) * dx, R.dL32[0], dx * wx);
+                const float gx = fmaxf(fabsf(ox - pi.x) - hx, 0.0f);
+                if (!exact_all && fmaf(gx, gx, gyz) > hi2) continue;
                 int key = R.cell_off + (q2 * R.nc[1] + q1) * R.nc[0] + q0;
                 int b = a.cell_start[key], e = b + a.cell_count[key];
                 const unsigned dir = (dx < 0 ? 1u : 0u) | (dx > 0 ? 2u : 0u) | (dy < 0 ? 4u : 0u) | (dy > 0 ? 8u : 0u) |
                                      (dz < 0 ? 16u : 0u) | (dz > 0 ? 32u : 0u);
-                // centre offset of the stencil cell: d w32, plus d dL32 through a periodic face
-                const float ox = fmaf((float)(c0 + dx != q0) * dx, R.dL32[0], dx * wx);
-                const float oy = fmaf((float)(c1 + dy != q1) * dy, R.dL32[1], dy * wy);
-                const float oz = fmaf((float)(c2 + dz != q2) * dz, R.dL32[2], dz * wz);
-                for (int t = b; t < e; ++t) {
-                    if (t == s) continue;
-                    const float4 pj = a.pos4[t];
-                    const float fx = ox + (pj.x - pi.x), fy = oy + (pj.y - pi.y), fz = oz + (pj.z - pi.z);
+                const float tx = ox - pi.x, ty = oy - pi.y, tz = oz - pi.z;
+                for (int t0 = b; t0 < e; t0 += 4) {
+                  // four candidate positions are loaded before any test or list store
+                  float4 pjv[4];
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) pjv[u] = __ldg(&a.pos4[min(t0 + u, e - 1)]);
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) {
+                    const int t = t0 + u;
+                    const bool valid = t < e && t != s;
+                    const float4 pj = pjv[u];
+                    const float fx = pj.x + tx, fy = pj.y + ty, fz = pj.z + tz;
                     const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
-                    bool in;
-                    if (!ifar && fabsf(pj.x) <= lim && fabsf(pj.y) <= lim && fabsf(pj.z) <= lim && (r2f < lo2 || r2f > hi2)) {
-                        in = r2f < lo2;
-                    } else {
+                    bool in = r2f < lo2;
+                    if (valid && (exact_all || (!in && !(r2f > hi2)))) {
                         double ddx = mi_exact(__dsub_rn(a.x[t], a.x[s]), R.per[0], R.L[0]);
                         double ddy = mi_exact(__dsub_rn(a.x[S + t], a.x[S + s]), R.per[1], R.L[1]);
                         double ddz = mi_exact(__dsub_rn(a.x[2 * S + t], a.x[2 * S + s]), R.per[2], R.L[2]);
                         in = norm2_exact(ddx, ddy, ddz) < a.cut2;
                     }
-                    if (in) {
+                    if (in && valid) {
                         if (m < a.kmax) a.nbr[(size_t)m * S + s] = (int32_t)((unsigned)t | (dir << MD_J_BITS));
                         ++m;
                     }
+                  }
                 }
             }
         }
@@ -657,13 +733,33 @@ __global__ void __launch_bounds__(128) k_nbrc(DevArgs a)
     const RepDev &R = a.rep[r];
     if (s - R.slot_off >= R.n_atoms) return;
     if (R.n_c == 0) { a.cntc[s] = 0; return; }
+    {
+        // FP32 rejection: the atom's distance (minimum image) from the indenter grid's box
+        // exceeds the reach on some axis.  x is rebuilt from the cell centre and the
+        // cell-relative position with an error below 1e-4 A for coordinates below ~1e3 A;
+        // the 0.01 A margin keeps every atom the exact test below could accept.
+        const float4 p = a.pos4[s];
+        const int pc = __float_as_int(p.w);
+        const float pr[3] = {p.x, p.y, p.z};
+        const int cc[3] = {cell_x(pc), cell_y(pc), cell_z(pc)};
+        const float zi32 = (float)a.rs[r].z_ind;
+        const float lim = (float)a.cutc + 0.01f;
+        bool far = false;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float d = fmaf((float)cc[k] + 0.5f, R.w32[k], R.lo32[k]) + pr[k] - (k == 2 ? zi32 : 0.0f) - R.cg_ctr32[k];
+            if (R.per[k]) d = fmaf(-R.L32[k], rintf(d * R.iL32[k]), d);
+            far |= fabsf(d) > R.cg_half32[k] + lim;
+        }
+        if (far) { a.cntc[s] = 0; return; }
+    }
     size_t S = a.S, C = a.C;
     double z_ind = a.rs[r].z_ind;
     double xi[3] = {a.x[s], a.x[S + s], a.x[2 * S + s]};
     if (!(isfinite(xi[0]) && isfinite(xi[1]) && isfinite(xi[2]))) { a.cntc[s] = 0; return; }   // reported by k_bin
     unsigned long long mask[3];
     double reach = a.cutc * (1.0 + 1e-9) + 1e-9;
-    float q32[3], L32[3];
+    float q32[3];
     for (int k = 0; k < 3; ++k) {
         double q = xi[k] - (k == 2 ? z_ind : 0.0);
         double ctr = R.cg_lo[k] + 0.5 * R.cg_n[k] * R.cg_w[k];
@@ -676,7 +772,6 @@ __global__ void __launch_bounds__(128) k_nbrc(DevArgs a)
         mask[k] |= cell_bits(q, reach, R.cg_lo[k], R.cg_w[k], R.cg_n[k]);
         if (!mask[k]) { a.cntc[s] = 0; return; }
         q32[k] = (float)(q - R.cg_lo[k]);
-        L32[k] = (float)R.L[k];
     }
     // FP32 prefilter (indenter frame, positions below ~100 A: error < 1e-4 A^2 on y^2); the
     // exact FP64 test decides every candidate within 1e-4 (relative) of the cut-off
@@ -690,11 +785,19 @@ __global__ void __launch_bounds__(128) k_nbrc(DevArgs a)
                 int q0 = __ffsll((long long)m0) - 1;
                 int key = R.ccell_off + (q2 * R.cg_n[1] + q1) * R.cg_n[0] + q0;
                 int b = a.ccell_start[key], e = b + a.ccell_count[key];
-                for (int c = b; c < e; ++c) {
-                    const float4 pc = __ldg(&a.xc32[c]);
+                for (int c0 = b; c0 < e; c0 += 4) {
+                  float4 pcv[4];
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) pcv[u] = __ldg(&a.xc32[min(c0 + u, e - 1)]);
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) {
+                    const int c = c0 + u;
+                    if (c >= e) continue;
+                    const float4 pc = pcv[u];
                     float fx = pc.x - q32[0], fy = pc.y - q32[1], fz = pc.z - q32[2];
-                    if (R.per[0]) fx -= L32[0] * rintf(fx / L32[0]);
-                    if (R.per[1]) fy -= L32[1] * rintf(fy / L32[1]);
+                    if (R.per[0]) fx = fmaf(-R.L32[0], rintf(fx * R.iL32[0]), fx);
+                    if (R.per[1]) fy = fmaf(-R.L32[1], rintf(fy * R.iL32[1]), fy);
+                    if (R.per[2]) fz = fmaf(-R.L32[2], rintf(fz * R.iL32[2]), fz);
                     const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
                     if (r2f > hi2) continue;
                     bool in = r2f < lo2;
@@ -709,6 +812,7 @@ __global__ void __launch_bounds__(128) k_nbrc(DevArgs a)
                         if (m < a.kcmax) a.nbrc[(size_t)m * S + s] = c;
                         ++m;
                     }
+                  }
                 }
             }
         }
@@ -737,14 +841,17 @@ __global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
     if (s == R.slot_off) {   // Task 2: the rigid indenter moves by v_ind dt
         RepState &st = a.rs[r];
         st.z_ind = __dadd_rn(st.z_ind, __dmul_rn(R.v_ind, R.dt));
-        if (s == 0) { a.st->step += 1; a.st->since_build += 1; }   // after this step's Task 1 decision
+        if (s == 0) {   // after this step's Task 1 decision
+            a.st->step += 1; a.st->since_build += 1;
+            if (!a.mixed) a.st->pos4_ok = 0;   // the FP64 path does not keep pos4 current
+        }
     }
     unsigned long long d2bits = 0ull;
     if (s - R.slot_off < R.n_atoms) {
         const size_t S = a.S;
         double x0 = a.x[s], x1 = a.x[S + s], x2 = a.x[2 * S + s];
         if (!a.fixed[s]) {
-            const double hk = 0.5 * R.dt * R.acc_per_f;
+            const double hk = R.hk;
             double v0 = fma(hk, a.F[s], a.v[s]);                    // Eq. A12
             double v1 = fma(hk, a.F[S + s], a.v[S + s]);
             double v2 = fma(hk, a.F[2 * S + s], a.v[2 * S + s]);
@@ -755,7 +862,7 @@ __global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
         double d2 = norm2_exact(__dsub_rn(x0, a.xb[s]), __dsub_rn(x1, a.xb[S + s]), __dsub_rn(x2, a.xb[2 * S + s]));
         if (d2 != d2) d2 = 1e300;   // NaN position: force a rebuild, which reports it
         d2bits = (unsigned long long)__double_as_longlong(d2);   // d2 >= 0: bit order = value order
-        if (a.mixed) a.pos4[s] = rel_pos3(R, a.cellc[s], x0, x1, x2);
+        if (a.mixed) a.pos4[s] = rel_pos3(a, R, a.cellc[s], x0, x1, x2);
     }
     for (int o = 16; o > 0; o >>= 1) {
         unsigned long long t = __shfl_xor_sync(0xffffffffu, d2bits, o);
@@ -1047,7 +1154,7 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
         a.F[s] = Fx; a.F[S + s] = Fy; a.F[2 * S + s] = Fz;
         double vx = a.v[s], vy = a.v[S + s], vz = a.v[2 * S + s];
         if (integrate && !a.fixed[s]) {   // Task 5: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2 (FP64)
-            const double hk = 0.5 * R.dt * R.acc_per_f;
+            const double hk = R.hk;
             vx = fma(hk, Fx, vx); vy = fma(hk, Fy, vy); vz = fma(hk, Fz, vz);
             a.v[s] = vx; a.v[S + s] = vy; a.v[2 * S + s] = vz;
         }

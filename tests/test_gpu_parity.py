@@ -60,6 +60,84 @@ def test_cells_and_lists_bit_exact(md, params, precision):
     sim.close()
 
 
+def test_cells_on_cell_faces_bit_exact(md, params):
+    """Coordinates exactly on cell faces and one ulp either side, and periodic coordinates
+    shifted by whole periods (the cases where the quotient floors of the binning are decided
+    by rounding): cell coordinates and neighbour sets equal the oracle's."""
+    rep = tiny(amp=0.12, gap=1.0)
+    skin = 0.3
+    cut = params["rc"] + skin
+    lo, hi, per = rep.box_lo, rep.box_hi, rep.periodic
+    L = hi - lo
+    n = np.maximum(1, np.floor(L / cut)).astype(int)
+    w = L / n
+    x = rep.x_cr.copy()
+    rng = np.random.default_rng(7)
+    moved = 0
+    for i in range(len(x)):
+        for k in range(3):
+            q = (x[i, k] - lo[k]) / w[k]
+            kb = np.round(q)
+            if abs(q - kb) * w[k] < 0.2 and 0 < kb < n[k]:
+                b = lo[k] + kb * w[k]
+                x[i, k] = (b, np.nextafter(b, np.inf), np.nextafter(b, -np.inf))[rng.integers(3)]
+                moved += 1
+            elif per[k] and rng.random() < 0.1:
+                x[i, k] += L[k] * rng.choice([-2.0, -1.0, 1.0, 3.0])
+    assert moved > 50
+    rep.x_cr = x
+    sim = md.MD([rep], params, precision="mixed", skin=skin)
+    cell, cnt, nbr = sim.neighbors(0, 0)
+    assert np.array_equal(cell, oracle.cell_coords(x, lo, hi, per, cut))
+    # the oracle's cell-list build wraps the positions first (its brute-force form takes a
+    # single minimum-image shift, so it wants positions within one period)
+    off, idx = oracle.neighbors(x, lo, hi, per, cut, method=1)
+    xw = np.where(per == 1, x - np.floor((x - lo) / L) * L, x)
+    near = lambda i, j: abs(min_image_r(xw, i, j, lo, hi, per) - cut) < 1e-12
+    assert compare_sets(cnt, nbr, off, idx, near) == []
+    sim.close()
+
+
+def test_cr_c_list_periodic_z_tall_indenter(md, params):
+    """Periodic z with an indenter taller than half the period minus the Morse reach: the
+    Cr-C candidates are found through either z image (the list equals the oracle's)."""
+    rep = mi.make_replica("pz", 8, 8, 6, 10.0, 300.0, seed=3, gap=1.0, periodic_z=True)
+    rep = jitter(rep, 0.1, 3)
+    skin = 0.3
+    cutc = params["rc_m"] + skin
+    L = rep.box_hi - rep.box_lo
+    assert 0.5 * (rep.x_c[:, 2].max() - rep.x_c[:, 2].min()) + cutc > 0.5 * L[2]
+    sim = md.MD([rep], params, precision="mixed", skin=skin)
+    _, cntc, nbrc = sim.neighbors(0, 1)
+    offc, idxc = oracle.cneighbors(rep.x_cr, rep.x_c, rep.box_lo, rep.box_hi, rep.periodic, cutc)
+    assert offc[-1] > 0
+    assert compare_sets(cntc, nbrc, offc, idxc, lambda i, j: False) == []
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_rebuild_after_steps_bit_exact(md, params, precision):
+    """Cells and lists of a rebuild after time steps (the mixed path bins from the FP32
+    cell-relative positions it keeps current; atoms cross cells and periodic faces) equal
+    the oracle's on the positions of that moment."""
+    rep = tiny(amp=0.12, gap=2.0, T=900.0)
+    skin = 0.3
+    sim = md.MD([rep], params, precision=precision, skin=skin)
+    cut = params["rc"] + skin
+    lo, hi, per = rep.box_lo, rep.box_hi, rep.periodic
+    for _ in range(3):
+        sim.step(40)
+        sim.build_neighbors()
+        x = sim.state(0)[0]
+        cell, cnt, nbr = sim.neighbors(0, 0)
+        assert np.array_equal(cell, oracle.cell_coords(x, lo, hi, per, cut))
+        off, idx = oracle.neighbors(x, lo, hi, per, cut, method=1)
+        near = lambda i, j: abs(min_image_r(x, i, j, lo, hi, per) - cut) < 1e-12
+        assert compare_sets(cnt, nbr, off, idx, near) == []
+    assert sim.energy(0)["rebuilds"] >= 3
+    sim.close()
+
+
 @pytest.mark.parametrize("tab,shifted", [(1, 1), (0, 1), (1, 0), (0, 0)])
 def test_forces_fp64(md, params, tab, shifted):
     rep = tiny(amp=0.12, gap=1.0)
