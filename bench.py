@@ -335,7 +335,7 @@ def run_gpu(args):
         "phases_ms_per_step": phases,
         "clocks": clk.summary(),
         "e2e": e2e,
-        "gpu_launches": int(4 * args.steps + 13 * rebuilds + 1),
+        "gpu_launches": int((5 if args.precision == "mixed" else 4) * args.steps + 14 * rebuilds + 1),
         "variants": variants,
     }
     if cpu is not None:

@@ -454,6 +454,9 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     INIT_FAIL(dalloc(h, &a.icnt, S));
     INIT_FAIL(dalloc(h, &a.nbrc, (size_t)a.kcmax * S));
     INIT_FAIL(dalloc(h, &a.cntc, S));
+    INIT_FAIL(dalloc(h, &a.cand, S));
+    INIT_FAIL(dalloc(h, &a.near, S));
+    INIT_FAIL(dalloc(h, &a.fmorse, S));
     INIT_FAIL(dalloc(h, &a.key, S));
     INIT_FAIL(dalloc(h, &a.perm, S));
     INIT_FAIL(dalloc(h, &a.cell_count, cells));

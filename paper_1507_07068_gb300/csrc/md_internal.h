@@ -128,6 +128,8 @@ struct DevStatus {
     int32_t any_rebuild;    // rebuild decided this step (host-readable)
     int32_t max_cnt, max_cntc;
     int32_t pos4_ok;        // pos4 holds every atom's current position about its cell's centre
+    int32_t n_cand;         // atoms queued for the Cr-C list search (set by k_nbrc)
+    int32_t n_near;         // atoms with Cr-C neighbours (set by k_nbrc_near)
     int32_t pad_;
     int64_t step, rebuilds, since_build;
 };
@@ -158,6 +160,8 @@ struct DevArgs {
     int32_t *cellc, *orig;
     uint8_t *fixed;
     int32_t *nbr, *cnt, *nbrc, *cntc;
+    int32_t *cand, *near;        // Cr-C: atoms within reach of an indenter grid / with neighbours
+    float4 *fmorse;              // mixed precision: Morse force and energy of each atom in near
     // rebuild scratch
     int32_t *key, *perm, *cell_count, *cell_start, *cell_fill, *scan_blk;
     double *sx, *sv, *sF;        // [3][S] gather scratch

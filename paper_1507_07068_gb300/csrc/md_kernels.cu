@@ -27,6 +27,8 @@
 #include "md_internal.h"
 
 #define MD_UNROLL 4   // neighbour entries per lane whose loads are issued together
+#define MD_NEAR_BLOCKS 304   // CTAs (8 warps each) of the one-warp-per-atom Cr-C kernels
+#define MD_SORT_MAX 2048     // largest cell k_cellsort orders
 
 // ============================================================================ host:
 // potential forms used to fill the tables (FP64), restated from the Appendix.
@@ -429,7 +431,7 @@ __global__ void k_zero_i32(int32_t *p, int n)
 __global__ void k_bin(DevArgs a)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s == 0) { a.st->max_cnt = 0; a.st->max_cntc = 0; }
+    if (s == 0) { a.st->max_cnt = 0; a.st->max_cntc = 0; a.st->n_cand = 0; a.st->n_near = 0; }
     if (s >= a.S) return;
     int r = a.tile_rep[s / MD_TILE];
     const RepDev &R = a.rep[r];
@@ -556,11 +558,17 @@ __global__ void k_scatter(DevArgs a)
 }
 
 // deterministic order within a cell: ascending caller id (insertion sort, ~10 atoms)
+// Atoms of a cell in ascending original index (one thread per cell, insertion sort), so
+// the slot order and every list order are reproducible.  Skipped when an atom is lost (the
+// step ends with MD_ERR_LOST_ATOM; non-finite positions all land in cell 0) and for a cell
+// holding more than MD_SORT_MAX atoms (lists stay correct, their order is then the arrival
+// order): neither case then costs quadratic time.
 __global__ void k_cellsort(DevArgs a)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= a.total_cells) return;
     int b = a.cell_start[c], n = a.cell_count[c];
+    if (n > MD_SORT_MAX || (*(volatile int32_t *)&a.st->err & MDE_LOST)) return;
     for (int i = 1; i < n; ++i) {
         int p = a.perm[b + i];
         int key = a.orig[p];
@@ -633,18 +641,19 @@ __global__ void k_copyback(DevArgs a)
 // 2e-6 relative for atoms inside their cells); the rest take the exact FP64 test, so the
 // set equals the all-FP64 set bit for bit.
 //
-// With no lost atom (k_bin ran first and raised no MDE_LOST) every atom lies in its cell's
-// box up to rounding, the box being off the w32-frame cell by at most pad32 (the frame's
-// drift c |w - w32| plus 1e-4 A), so (i) a stencil cell whose widened box is farther than
-// the cut-off from atom i holds no neighbour and is skipped, and (ii) every candidate is an
-// in-cell atom.  Otherwise (an atom clamped into an edge cell from outside the domain) no
-// cell is skipped and every candidate takes the FP64 test.
+// A lost atom (MDE_LOST from k_bin: outside a non-periodic domain or not finite) ends the
+// step with MD_ERR_LOST_ATOM; the lists are then left empty rather than built around
+// clamped atoms.  Otherwise every atom lies in its cell's box up to rounding, the box being
+// off the w32-frame cell by at most pad32 (the frame's drift c |w - w32| plus 1e-4 A), so
+// (i) a stencil cell whose widened box is farther than the cut-off from atom i holds no
+// neighbour and is skipped, and (ii) every candidate is an in-cell atom.
 __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.S) return;
     const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
     if (s - R.slot_off >= R.n_atoms) return;
+    if (*(volatile int32_t *)&a.st->err & MDE_LOST) { a.cnt[s] = 0; return; }
     size_t S = a.S;
     const float4 pi = a.pos4[s];
     int pc = __float_as_int(pi.w);
@@ -652,7 +661,6 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
     const float cut2 = (float)a.cut2;
     const float lo2 = cut2 * (1.0f - 1e-5f), hi2 = cut2 * (1.0f + 1e-5f);
     const float wx = R.w32[0], wy = R.w32[1], wz = R.w32[2];
-    const bool exact_all = (*(volatile int *)&a.st->err & MDE_LOST) != 0;
     const float hx = fmaf(0.5f, wx, R.pad32[0]), hy = fmaf(0.5f, wy, R.pad32[1]), hz = fmaf(0.5f, wz, R.pad32[2]);
     int m = 0;
     for (int dz = -1; dz <= 1; ++dz) {
@@ -672,7 +680,7 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
                 // centre offset of the stencil cell: d w32, plus d dL32 through a periodic face
                 const float ox = fmaf((float)(c0 + dx != q0) * dx, R.dL32[0], dx * wx);
                 const float gx = fmaxf(fabsf(ox - pi.x) - hx, 0.0f);
-                if (!exact_all && fmaf(gx, gx, gyz) > hi2) continue;
+                if (fmaf(gx, gx, gyz) > hi2) continue;
                 int key = R.cell_off + (q2 * R.nc[1] + q1) * R.nc[0] + q0;
                 int b = a.cell_start[key], e = b + a.cell_count[key];
                 const unsigned dir = (dx < 0 ? 1u : 0u) | (dx > 0 ? 2u : 0u) | (dy < 0 ? 4u : 0u) | (dy > 0 ? 8u : 0u) |
@@ -691,7 +699,7 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
                     const float fx = pj.x + tx, fy = pj.y + ty, fz = pj.z + tz;
                     const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
                     bool in = r2f < lo2;
-                    if (valid && (exact_all || (!in && !(r2f > hi2)))) {
+                    if (valid && !in && !(r2f > hi2)) {
                         double ddx = mi_exact(__dsub_rn(a.x[t], a.x[s]), R.per[0], R.L[0]);
                         double ddy = mi_exact(__dsub_rn(a.x[S + t], a.x[S + s]), R.per[1], R.L[1]);
                         double ddz = mi_exact(__dsub_rn(a.x[2 * S + t], a.x[2 * S + s]), R.per[2], R.L[2]);
@@ -711,7 +719,11 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
     atomicMax(&a.st->max_cnt, m);
 }
 
-// Cr-C list through the indenter's own cell grid (indenter frame = positions at z_ind = 0).
+// Cr-C list through the indenter's own cell grid (indenter frame = positions at z_ind = 0),
+// in two kernels.  k_nbrc: per atom, an FP32 rejection test against the grid's box; the
+// few atoms it keeps (those under the indenter) are queued.  k_nbrc_near: one warp per
+// queued atom, the lanes over the candidates of its cells, entries appended in candidate
+// order (ballot), so the atoms under the indenter do not serialise in a few threads.
 // Along a periodic axis both images of the film atom that can reach the indenter are
 // searched: the cells of the two reach intervals are merged into one bit set per axis
 // (indenter grids have at most 64 cells per axis), so every cell is visited once.
@@ -732,94 +744,108 @@ __global__ void __launch_bounds__(128) k_nbrc(DevArgs a)
     int r = a.tile_rep[s / MD_TILE];
     const RepDev &R = a.rep[r];
     if (s - R.slot_off >= R.n_atoms) return;
-    if (R.n_c == 0) { a.cntc[s] = 0; return; }
-    {
-        // FP32 rejection: the atom's distance (minimum image) from the indenter grid's box
-        // exceeds the reach on some axis.  x is rebuilt from the cell centre and the
-        // cell-relative position with an error below 1e-4 A for coordinates below ~1e3 A;
-        // the 0.01 A margin keeps every atom the exact test below could accept.
-        const float4 p = a.pos4[s];
-        const int pc = __float_as_int(p.w);
-        const float pr[3] = {p.x, p.y, p.z};
-        const int cc[3] = {cell_x(pc), cell_y(pc), cell_z(pc)};
-        const float zi32 = (float)a.rs[r].z_ind;
-        const float lim = (float)a.cutc + 0.01f;
-        bool far = false;
+    a.cntc[s] = 0;
+    if (R.n_c == 0 || (*(volatile int32_t *)&a.st->err & MDE_LOST)) return;
+    // FP32 rejection: the atom's distance (minimum image) from the indenter grid's box
+    // exceeds the reach on some axis.  x is rebuilt from the cell centre and the
+    // cell-relative position with an error below 1e-4 A for coordinates below ~1e3 A;
+    // the 0.01 A margin keeps every atom the exact test of k_nbrc_near could accept.
+    // A non-finite position is queued (and then skipped: k_bin reports it).
+    const float4 p = a.pos4[s];
+    const int pc = __float_as_int(p.w);
+    const float pr[3] = {p.x, p.y, p.z};
+    const int cc[3] = {cell_x(pc), cell_y(pc), cell_z(pc)};
+    const float zi32 = (float)a.rs[r].z_ind;
+    const float lim = (float)a.cutc + 0.01f;
+    bool far = false;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float d = fmaf((float)cc[k] + 0.5f, R.w32[k], R.lo32[k]) + pr[k] - (k == 2 ? zi32 : 0.0f) - R.cg_ctr32[k];
-            if (R.per[k]) d = fmaf(-R.L32[k], rintf(d * R.iL32[k]), d);
-            far |= fabsf(d) > R.cg_half32[k] + lim;
-        }
-        if (far) { a.cntc[s] = 0; return; }
-    }
-    size_t S = a.S, C = a.C;
-    double z_ind = a.rs[r].z_ind;
-    double xi[3] = {a.x[s], a.x[S + s], a.x[2 * S + s]};
-    if (!(isfinite(xi[0]) && isfinite(xi[1]) && isfinite(xi[2]))) { a.cntc[s] = 0; return; }   // reported by k_bin
-    unsigned long long mask[3];
-    double reach = a.cutc * (1.0 + 1e-9) + 1e-9;
-    float q32[3];
     for (int k = 0; k < 3; ++k) {
-        double q = xi[k] - (k == 2 ? z_ind : 0.0);
-        double ctr = R.cg_lo[k] + 0.5 * R.cg_n[k] * R.cg_w[k];
-        mask[k] = 0ull;
-        if (R.per[k]) {
-            q = ctr + mi64(q - ctr, 1, R.L[k]);
-            double q2 = q > ctr ? q - R.L[k] : q + R.L[k];
-            mask[k] = cell_bits(q2, reach, R.cg_lo[k], R.cg_w[k], R.cg_n[k]);
-        }
-        mask[k] |= cell_bits(q, reach, R.cg_lo[k], R.cg_w[k], R.cg_n[k]);
-        if (!mask[k]) { a.cntc[s] = 0; return; }
-        q32[k] = (float)(q - R.cg_lo[k]);
+        float d = fmaf((float)cc[k] + 0.5f, R.w32[k], R.lo32[k]) + pr[k] - (k == 2 ? zi32 : 0.0f) - R.cg_ctr32[k];
+        if (R.per[k]) d = fmaf(-R.L32[k], rintf(d * R.iL32[k]), d);
+        far |= fabsf(d) > R.cg_half32[k] + lim;
     }
-    // FP32 prefilter (indenter frame, positions below ~100 A: error < 1e-4 A^2 on y^2); the
-    // exact FP64 test decides every candidate within 1e-4 (relative) of the cut-off
+    if (!far) a.cand[atomicAdd(&a.st->n_cand, 1)] = s;
+}
+
+__global__ void __launch_bounds__(256) k_nbrc_near(DevArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int n_cand = a.st->n_cand;
+    const size_t S = a.S, C = a.C;
     const float cut2f = (float)a.cutc2, lo2 = cut2f * (1.0f - 1e-4f), hi2 = cut2f * (1.0f + 1e-4f);
-    int m = 0;
-    for (unsigned long long m2 = mask[2]; m2; m2 &= m2 - 1) {
-        int q2 = __ffsll((long long)m2) - 1;
-        for (unsigned long long m1 = mask[1]; m1; m1 &= m1 - 1) {
-            int q1 = __ffsll((long long)m1) - 1;
-            for (unsigned long long m0 = mask[0]; m0; m0 &= m0 - 1) {
-                int q0 = __ffsll((long long)m0) - 1;
-                int key = R.ccell_off + (q2 * R.cg_n[1] + q1) * R.cg_n[0] + q0;
-                int b = a.ccell_start[key], e = b + a.ccell_count[key];
-                for (int c0 = b; c0 < e; c0 += 4) {
-                  float4 pcv[4];
-#pragma unroll
-                  for (int u = 0; u < 4; ++u) pcv[u] = __ldg(&a.xc32[min(c0 + u, e - 1)]);
-#pragma unroll
-                  for (int u = 0; u < 4; ++u) {
-                    const int c = c0 + u;
-                    if (c >= e) continue;
-                    const float4 pc = pcv[u];
-                    float fx = pc.x - q32[0], fy = pc.y - q32[1], fz = pc.z - q32[2];
-                    if (R.per[0]) fx = fmaf(-R.L32[0], rintf(fx * R.iL32[0]), fx);
-                    if (R.per[1]) fy = fmaf(-R.L32[1], rintf(fy * R.iL32[1]), fy);
-                    if (R.per[2]) fz = fmaf(-R.L32[2], rintf(fz * R.iL32[2]), fz);
-                    const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
-                    if (r2f > hi2) continue;
-                    bool in = r2f < lo2;
-                    if (!in) {
-                        double ddx = mi_exact(__dsub_rn(a.xc0[c], xi[0]), R.per[0], R.L[0]);
-                        double ddy = mi_exact(__dsub_rn(a.xc0[C + c], xi[1]), R.per[1], R.L[1]);
-                        double zc = __dadd_rn(a.xc0[2 * C + c], z_ind);
-                        double ddz = mi_exact(__dsub_rn(zc, xi[2]), R.per[2], R.L[2]);
-                        in = norm2_exact(ddx, ddy, ddz) < a.cutc2;
+    const double reach = a.cutc * (1.0 + 1e-9) + 1e-9;
+    for (int qi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; qi < n_cand; qi += nw) {
+        const int s = a.cand[qi];
+        const int r = a.tile_rep[s / MD_TILE];
+        const RepDev &R = a.rep[r];
+        const double z_ind = a.rs[r].z_ind;
+        const double xi[3] = {a.x[s], a.x[S + s], a.x[2 * S + s]};
+        if (!(isfinite(xi[0]) && isfinite(xi[1]) && isfinite(xi[2]))) continue;   // reported by k_bin
+        unsigned long long mask[3];
+        float q32[3];
+        bool none = false;
+        for (int k = 0; k < 3; ++k) {
+            double q = xi[k] - (k == 2 ? z_ind : 0.0);
+            double ctr = R.cg_lo[k] + 0.5 * R.cg_n[k] * R.cg_w[k];
+            mask[k] = 0ull;
+            if (R.per[k]) {
+                q = ctr + mi64(q - ctr, 1, R.L[k]);
+                double q2 = q > ctr ? q - R.L[k] : q + R.L[k];
+                mask[k] = cell_bits(q2, reach, R.cg_lo[k], R.cg_w[k], R.cg_n[k]);
+            }
+            mask[k] |= cell_bits(q, reach, R.cg_lo[k], R.cg_w[k], R.cg_n[k]);
+            none |= !mask[k];
+            q32[k] = (float)(q - R.cg_lo[k]);
+        }
+        if (none) continue;
+        // FP32 prefilter (indenter frame, positions below ~100 A: error < 1e-4 A^2 on y^2);
+        // the exact FP64 test decides every candidate within 1e-4 (relative) of the cut-off
+        int m = 0;
+        for (unsigned long long m2 = mask[2]; m2; m2 &= m2 - 1) {
+            const int q2 = __ffsll((long long)m2) - 1;
+            for (unsigned long long m1 = mask[1]; m1; m1 &= m1 - 1) {
+                const int q1 = __ffsll((long long)m1) - 1;
+                for (unsigned long long m0 = mask[0]; m0; m0 &= m0 - 1) {
+                    const int q0 = __ffsll((long long)m0) - 1;
+                    const int key = R.ccell_off + (q2 * R.cg_n[1] + q1) * R.cg_n[0] + q0;
+                    const int b = a.ccell_start[key], e = b + a.ccell_count[key];
+                    for (int c0 = b; c0 < e; c0 += 32) {
+                        const int c = c0 + lane;
+                        bool in = false;
+                        if (c < e) {
+                            const float4 pc = __ldg(&a.xc32[c]);
+                            float fx = pc.x - q32[0], fy = pc.y - q32[1], fz = pc.z - q32[2];
+                            if (R.per[0]) fx = fmaf(-R.L32[0], rintf(fx * R.iL32[0]), fx);
+                            if (R.per[1]) fy = fmaf(-R.L32[1], rintf(fy * R.iL32[1]), fy);
+                            if (R.per[2]) fz = fmaf(-R.L32[2], rintf(fz * R.iL32[2]), fz);
+                            const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+                            in = r2f < lo2;
+                            if (!in && !(r2f > hi2)) {
+                                double ddx = mi_exact(__dsub_rn(a.xc0[c], xi[0]), R.per[0], R.L[0]);
+                                double ddy = mi_exact(__dsub_rn(a.xc0[C + c], xi[1]), R.per[1], R.L[1]);
+                                double zc = __dadd_rn(a.xc0[2 * C + c], z_ind);
+                                double ddz = mi_exact(__dsub_rn(zc, xi[2]), R.per[2], R.L[2]);
+                                in = norm2_exact(ddx, ddy, ddz) < a.cutc2;
+                            }
+                        }
+                        const unsigned bal = __ballot_sync(0xffffffffu, in);
+                        if (in) {
+                            const int pos = m + __popc(bal & ((1u << lane) - 1u));
+                            if (pos < a.kcmax) a.nbrc[(size_t)pos * S + s] = c;
+                        }
+                        m += __popc(bal);
                     }
-                    if (in) {
-                        if (m < a.kcmax) a.nbrc[(size_t)m * S + s] = c;
-                        ++m;
-                    }
-                  }
                 }
             }
         }
+        if (lane == 0) {
+            a.cntc[s] = m < a.kcmax ? m : a.kcmax;
+            if (m > a.kcmax) atomicOr(&a.st->err, MDE_COVERFLOW);
+            atomicMax(&a.st->max_cntc, m);
+            if (m > 0) a.near[atomicAdd(&a.st->n_near, 1)] = s;
+        }
     }
-    a.cntc[s] = m < a.kcmax ? m : a.kcmax;
-    if (m > a.kcmax) atomicOr(&a.st->err, MDE_COVERFLOW);
-    atomicMax(&a.st->max_cntc, m);
 }
 
 __global__ void k_build_done(DevArgs a)
@@ -1073,7 +1099,7 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
     __syncthreads();
     const Pot32 &Q = static_cast<const Pot32 &>(P.q);
     const bool real = (s - R.slot_off) < R.n_atoms;
-    const size_t S = a.S, C = a.C;
+    const size_t S = a.S;
     float gx = 0.f, gy = 0.f, gz = 0.f, ep = 0.f;
     float mx = 0.f, my = 0.f, mz = 0.f, em = 0.f;
     if (real) {
@@ -1113,28 +1139,10 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
                 }
             }
         }
-        // Cr-C (Morse): FP64 geometry of the few near-indenter pairs, FP32 potential
-        const int nc = a.cntc[s];
-        if (nc > 0) {
-            const double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
-            const double z_ind = a.rs[r].z_ind;
-            for (int k = lane; k < nc; k += TPA) {
-                const int c = __ldg(&a.nbrc[(size_t)k * S + s]);
-                const double ddx = mi64(a.xc0[c] - xi, R.per[0], R.L[0]);
-                const double ddy = mi64(a.xc0[C + c] - yi, R.per[1], R.L[1]);
-                const double ddz = mi64(a.xc0[2 * C + c] + z_ind - zi, R.per[2], R.L[2]);
-                const double y2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                if (y2 < P.rcm2) {
-                    const float yinv = rsqrtf((float)y2);
-                    float v, dv;
-                    Q.morse((float)y2 * yinv, v, dv);
-                    const float c1 = dv * yinv;
-                    mx = fmaf(c1, (float)ddx, mx);
-                    my = fmaf(c1, (float)ddy, my);
-                    mz = fmaf(c1, (float)ddz, mz);
-                    em += v;
-                }
-            }
+        // Cr-C (Morse): summed by k_morse_mixed for the atoms with Cr-C neighbours
+        if (lane == 0 && a.cntc[s] > 0) {
+            const float4 fmo = a.fmorse[s];
+            mx = fmo.x; my = fmo.y; mz = fmo.z; em = fmo.w;
         }
     }
 #pragma unroll
@@ -1163,6 +1171,47 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
         acc[3] = (float)(0.5 / MD_ACC) * (float)R.mass * (ux * ux + uy * uy + uz * uz);
     }
     cta_partials<4>(acc, a.part + 2 * (size_t)a.max_blocks, a.max_blocks, blockIdx.x);
+}
+
+// Task 4c for the mixed path (Eqs. A5, A9): one warp per atom with Cr-C neighbours (the
+// queue built with the list), lanes over its entries; FP64 geometry of each pair, FP32
+// potential; the atom's Morse force and energy go to fmorse[s], which k_force_mixed adds.
+// The sums depend on the atom only, not on its place in the queue.
+__global__ void __launch_bounds__(256) k_morse_mixed(DevArgs a, PotDev P)
+{
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int n_near = a.st->n_near;
+    const Pot32 &Q = static_cast<const Pot32 &>(P.q);
+    const size_t S = a.S, C = a.C;
+    for (int qi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; qi < n_near; qi += nw) {
+        const int s = a.near[qi];
+        const int r = a.tile_rep[s / MD_TILE];
+        const RepDev &R = a.rep[r];
+        const int nc = a.cntc[s];
+        const double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
+        const double z_ind = a.rs[r].z_ind;
+        float mx = 0.f, my = 0.f, mz = 0.f, em = 0.f;
+        for (int k = lane; k < nc; k += 32) {
+            const int c = __ldg(&a.nbrc[(size_t)k * S + s]);
+            const double ddx = mi64(a.xc0[c] - xi, R.per[0], R.L[0]);
+            const double ddy = mi64(a.xc0[C + c] - yi, R.per[1], R.L[1]);
+            const double ddz = mi64(a.xc0[2 * C + c] + z_ind - zi, R.per[2], R.L[2]);
+            const double y2 = ddx * ddx + ddy * ddy + ddz * ddz;
+            if (y2 < P.rcm2) {
+                const float yinv = rsqrtf((float)y2);
+                float v, dv;
+                Q.morse((float)y2 * yinv, v, dv);
+                const float c1 = dv * yinv;
+                mx = fmaf(c1, (float)ddx, mx);
+                my = fmaf(c1, (float)ddy, my);
+                mz = fmaf(c1, (float)ddz, mz);
+                em += v;
+            }
+        }
+        mx = warp_sum(mx); my = warp_sum(my); mz = warp_sum(mz); em = warp_sum(em);
+        if (lane == 0) a.fmorse[s] = make_float4(mx, my, mz, em);
+    }
 }
 
 // ============================================================================ Task 4, FP64
@@ -1346,6 +1395,7 @@ cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s)
     k_copyback<<<nblk(a.S, B), B, 0, s>>>(a);
     k_nbr<<<nblk(a.S, 128), 128, 0, s>>>(a);
     k_nbrc<<<nblk(a.S, 128), 128, 0, s>>>(a);
+    k_nbrc_near<<<MD_NEAR_BLOCKS, 256, 0, s>>>(a);
     k_build_done<<<1, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -1391,6 +1441,7 @@ cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c
 
 cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, cudaStream_t s)
 {
+    if (a.mixed) k_morse_mixed<<<MD_NEAR_BLOCKS, 256, 0, s>>>(a, p);
     switch (c.tpa) {
     case 1: force_t<1>(a, p, c.block, integrate, s); break;
     case 2: force_t<2>(a, p, c.block, integrate, s); break;

@@ -338,6 +338,22 @@ def test_lost_atom_reported(md, params):
     assert ei.value.code == md.MD_ERR_LOST_ATOM
 
 
+def test_blown_up_state_reported_without_quadratic_rebuild(md, params):
+    """Every position non-finite (a blown-up run): all atoms bin into one cell; the rebuild
+    must still be linear in the atoms and the call must end with MD_ERR_LOST_ATOM."""
+    import time
+    rep = mi.make_workload("64k").replicas[0]
+    sim = md.MD([rep], params, precision="mixed")
+    sim.step(5)
+    x = np.full_like(rep.x_cr, np.nan)
+    t0 = time.perf_counter()
+    with pytest.raises(md.MDError) as ei:
+        sim.set_state(0, x, None, 0.0, 5)
+    assert ei.value.code == md.MD_ERR_LOST_ATOM
+    assert time.perf_counter() - t0 < 10.0
+    sim.close()
+
+
 def test_neighbour_capacity_grows_at_build(md, params):
     rep = tiny(amp=0.05)
     sim = md.MD([rep], params, precision="mixed", kmax=20, kcmax=8)
