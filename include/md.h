@@ -30,6 +30,7 @@
 #ifndef MD_H
 #define MD_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -226,6 +227,56 @@ void md_free(md_t *h);
 
 /* ABI version of this header (incremented on incompatible change). */
 int md_version(void);
+
+/* ------------------------------------------------------------ allocation-free evaluation
+ *
+ * The paper has no counterpart of this call.  It serves callers that must not allocate
+ * device memory where they need forces: an engine whose device memory is all held by its
+ * own pool allocator, or a per-step loop in which cudaMalloc / cudaFree (which may
+ * synchronise the whole device) cannot be afforded.  It evaluates, for one small system
+ * and without a handle, the forces and energies that md_init + md_compute_forces give in
+ * MD_FP64 mode with params->tabulated = 0: the forms of Eqs. A1-A5 in FP64, summed over
+ * all pairs (no cell grid, no Verlet list).
+ *
+ * Scratch: one static device array inside the library, MD_SMALL_SCRATCH_BYTES long
+ * (about 260 KB), holding F'(rho_i), M'(P_i) of every atom and per-block energy sums.  No
+ * scratch word has to start at zero: each call writes every word before it reads it.
+ * Apart from the set-up below, a call allocates nothing, on the device or on the host,
+ * and calls nothing that does (no cudaMalloc / cudaFree, no allocating library routine).
+ *
+ * Set-up: the first call on a device (the current device at the call) looks up the
+ * scratch address (cudaGetSymbolAddress, checked) and loads the three kernels, then
+ * caches the address for that device; if the CUDA runtime has not yet been used on that
+ * device, this also creates its context.  Make this first call -- n_cr = 0 does only the
+ * set-up -- before any stream capture begins.
+ *
+ * Concurrency: every call on a device uses the same scratch.  Calls whose kernels overlap
+ * in time (two streams, or two host threads) race on it and return wrong results; order
+ * them on one stream or with events.
+ *
+ * Arguments.  Arrays marked (dev) are DEVICE pointers owned by the caller, row-major
+ * n x 3 doubles in Angstrom; the rest are host pointers.
+ *   params            potential; params->tabulated must be 0
+ *   n_cr, x_cr (dev)  film atoms, 0 <= n_cr <= MD_SMALL_MAX_ATOMS (0: set-up only)
+ *   n_c, x_c (dev)    indenter atoms at their current positions, 0 <= n_c <=
+ *                     MD_SMALL_MAX_ATOMS (x_c may be NULL when n_c = 0)
+ *   box_lo, box_hi, periodic   3 each; along a periodic axis the length must exceed twice
+ *                     the larger cut-off (every pair is taken at its minimum image)
+ *   F (dev)           out: force on each film atom (n_cr x 3, eV/A)
+ *   energy (dev)      out: 4 doubles, sum_i F(rho_i), sum_{i<j} Phi, sum_i M(P_i),
+ *                     sum_{i,c} phi(y_ic) (eV) -- md_energy's embed, pair, mterm, morse
+ *   stream            cudaStream_t of the launches (NULL: the legacy default stream)
+ *   errbuf, errlen    optional host buffer for the message of a rejected call
+ * Returns MD_OK once the kernels are queued (they run asynchronously on stream), else
+ * MD_ERR_ARG (a size above the maximum, a bad box or potential: nothing launched) or
+ * MD_ERR_CUDA.
+ */
+#define MD_SMALL_MAX_ATOMS 16384
+#define MD_SMALL_SCRATCH_BYTES (8 * (2 * MD_SMALL_MAX_ATOMS + 4 * (MD_SMALL_MAX_ATOMS / 128)))
+int md_forces_small(const md_params *params, int32_t n_cr, const double *x_cr, int32_t n_c,
+                    const double *x_c, const double box_lo[3], const double box_hi[3],
+                    const int32_t periodic[3], double *F, double *energy, void *stream,
+                    char *errbuf, size_t errlen);
 
 #ifdef __cplusplus
 }

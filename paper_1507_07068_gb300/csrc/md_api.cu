@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -816,3 +817,79 @@ int md_get_info(md_t *h, int64_t *out9)
 }
 
 }  // extern "C"
+
+// ============================================================================ md_forces_small
+
+namespace {
+
+constexpr int SMALL_MAX_DEVICES = 64;
+std::atomic<double *> g_small_scratch_ptr[SMALL_MAX_DEVICES];   // per device, set on first use
+
+int small_reject(char *errbuf, size_t errlen, int code, const char *fmt, ...)
+{
+    if (errbuf && errlen) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(errbuf, errlen, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+}  // namespace
+
+extern "C" int md_forces_small(const md_params *params, int32_t n_cr, const double *x_cr, int32_t n_c,
+                               const double *x_c, const double box_lo[3], const double box_hi[3],
+                               const int32_t periodic[3], double *F, double *energy, void *stream,
+                               char *errbuf, size_t errlen)
+{
+    if (errbuf && errlen) errbuf[0] = '\0';
+    if (!params || !box_lo || !box_hi || !periodic)
+        return small_reject(errbuf, errlen, MD_ERR_ARG, "md_forces_small: params, box_lo, box_hi, periodic are required");
+    if (n_cr < 0 || n_cr > MD_SMALL_MAX_ATOMS || n_c < 0 || n_c > MD_SMALL_MAX_ATOMS)
+        return small_reject(errbuf, errlen, MD_ERR_ARG,
+                            "md_forces_small: n_cr = %d, n_c = %d; each must be in 0..%d (the size of its static scratch)",
+                            (int)n_cr, (int)n_c, MD_SMALL_MAX_ATOMS);
+    if (n_cr > 0 && (!x_cr || !F || !energy))
+        return small_reject(errbuf, errlen, MD_ERR_ARG, "md_forces_small: x_cr, F and energy are required when n_cr > 0");
+    if (n_c > 0 && !x_c)
+        return small_reject(errbuf, errlen, MD_ERR_ARG, "md_forces_small: x_c is required when n_c > 0");
+    PotDev P;
+    char pmsg[160];
+    int rc = md_pot_forms(params, &P, pmsg, sizeof pmsg);
+    if (rc != MD_OK) return small_reject(errbuf, errlen, rc, "md_forces_small: %s", pmsg);
+    SmallArgs g;
+    memset(&g, 0, sizeof g);
+    const double reach = std::max(params->rc, params->rc_morse);
+    for (int k = 0; k < 3; ++k) {
+        g.L[k] = box_hi[k] - box_lo[k];
+        g.per[k] = periodic[k] ? 1 : 0;
+        if (g.per[k] && !(g.L[k] > 2.0 * reach))
+            return small_reject(errbuf, errlen, MD_ERR_ARG,
+                                "md_forces_small: periodic axis %d is %.3f A; it must exceed twice the cut-off %.3f A", k, g.L[k], reach);
+        g.iL[k] = g.per[k] ? 1.0 / g.L[k] : 0.0;
+    }
+    // set-up, once per device: the scratch address
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return small_reject(errbuf, errlen, MD_ERR_CUDA, "md_forces_small: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= SMALL_MAX_DEVICES)
+        return small_reject(errbuf, errlen, MD_ERR_ARG, "md_forces_small: device %d beyond the %d supported", dev, SMALL_MAX_DEVICES);
+    double *scratch = g_small_scratch_ptr[dev].load();
+    if (!scratch) {
+        size_t nd = 0;
+        e = small_setup(&scratch, &nd);
+        if (e != cudaSuccess || !scratch)
+            return small_reject(errbuf, errlen, MD_ERR_CUDA, "md_forces_small: scratch look-up failed: %s", cudaGetErrorString(e));
+        g_small_scratch_ptr[dev].store(scratch);
+    }
+    if (n_cr == 0) return MD_OK;
+    g.n = n_cr; g.n_c = n_c;
+    g.nb = (n_cr + MD_SMALL_BLOCK - 1) / MD_SMALL_BLOCK;
+    g.x = x_cr; g.xc = x_c; g.F = F; g.energy = energy;
+    g.fm = scratch;
+    g.part = scratch + 2 * (size_t)MD_SMALL_MAX_ATOMS;
+    e = launch_small(g, P, (cudaStream_t)stream);
+    if (e != cudaSuccess) return small_reject(errbuf, errlen, MD_ERR_CUDA, "md_forces_small: launch failed: %s", cudaGetErrorString(e));
+    return MD_OK;
+}

@@ -193,3 +193,21 @@ cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c
 cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, cudaStream_t s);
 cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_refresh_pos4(const DevArgs &a, cudaStream_t s);
+
+// ---- allocation-free small-system evaluation (md_forces_small): all pairs, FP64 forms
+enum { MD_SMALL_BLOCK = 128, MD_SMALL_MAX_BLOCKS = MD_SMALL_MAX_ATOMS / MD_SMALL_BLOCK };
+struct SmallArgs {
+    int32_t n, n_c, nb;                  // film atoms, indenter atoms, CTAs
+    const double *x, *xc;                // caller's AoS positions (n x 3, n_c x 3)
+    double L[3], iL[3];
+    int32_t per[3];
+    double *F, *energy;                  // caller's outputs
+    double *fm;                          // scratch: F'(rho_i), M'(P_i) interleaved (2n)
+    double *part;                        // scratch: per-CTA energy sums [4][nb]
+};
+// analytic FP64 forms of md_params into P (no tables; allocates nothing)
+int md_pot_forms(const md_params *p, PotDev *P, char *err, size_t errlen);
+// address and length (doubles) of the static scratch on the current device; also loads
+// the three kernels of launch_small
+cudaError_t small_setup(double **scratch, size_t *n_doubles);
+cudaError_t launch_small(const SmallArgs &g, const PotDev &P, cudaStream_t s);

@@ -1456,3 +1456,162 @@ cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s)
     k_reduce<<<a.n_rep, 1024, 0, s>>>(a, c.block / c.tpa);
     return cudaGetLastError();
 }
+
+// ============================================================================ md_forces_small
+
+// Analytic part of md_build_pot: the same fields, no tables.
+int md_pot_forms(const md_params *p, PotDev *P, char *err, size_t errlen)
+{
+    memset(P, 0, sizeof(*P));
+    if (!(p->r_e > 0 && p->f_e > 0 && p->rho_e > 0 && p->P_e > 0 && p->y_eq > 0 && p->rc > 0 && p->rc_morse > 0)) {
+        snprintf(err, errlen, "md_params: r_e, f_e, rho_e, P_e, y_eq, rc, rc_morse must be > 0");
+        return MD_ERR_ARG;
+    }
+    if (p->tabulated) {
+        snprintf(err, errlen, "md_forces_small evaluates the analytic forms: params->tabulated must be 0");
+        return MD_ERR_ARG;
+    }
+    HostPot H;
+    H.p = *p;
+    const long double a0 = p->a[0], a1 = p->a[1], a2 = p->a[2], a3 = p->a[3], d = p->d;
+    H.e[0] = ((a3 * d + a2) * d + a1) * d + a0;
+    H.e[1] = (3.0L * a3 * d + 2.0L * a2) * d + a1;
+    H.e[2] = 3.0L * a3 * d + a2;
+    H.e[3] = a3;
+    if (p->shifted) {
+        H.f_rc = H.f_raw(p->rc);
+        H.df_rc = H.df_raw(p->rc);
+        H.morse_raw(p->rc_morse, H.m_rc, H.dm_rc);
+    }
+    P->f_e = p->f_e; P->r_e = p->r_e; P->beta = p->beta;
+    P->lf0 = log2(p->f_e) + p->beta * log2(p->r_e);
+    P->F_o = p->F_o; P->n = p->n; P->rho_e = p->rho_e; P->alpha = p->alpha; P->P_e = p->P_e;
+    for (int k = 0; k < 4; ++k) P->b[k] = (double)H.e[k];
+    P->d = p->d;
+    P->D_o = p->D_o; P->half_ax = 0.5 * p->alpha_x; P->inv_yeq = 1.0 / p->y_eq;
+    P->rc = p->rc; P->rc_m = p->rc_morse; P->rc2 = p->rc * p->rc; P->rcm2 = p->rc_morse * p->rc_morse;
+    P->f_rc = (double)H.f_rc; P->df_rc = (double)H.df_rc; P->m_rc = (double)H.m_rc; P->dm_rc = (double)H.dm_rc;
+    P->shifted = p->shifted; P->tabulated = 0;
+    return MD_OK;
+}
+
+namespace {
+
+constexpr size_t SMALL_SCRATCH_DOUBLES = 2 * (size_t)MD_SMALL_MAX_ATOMS + 4 * (size_t)MD_SMALL_MAX_BLOCKS;
+static_assert(SMALL_SCRATCH_DOUBLES * 8 == MD_SMALL_SCRATCH_BYTES, "scratch size in md.h");
+
+// the scratch of md_forces_small (one per device; see md.h for sharing rules)
+static __device__ __align__(256) double g_small_scratch[SMALL_SCRATCH_DOUBLES];
+
+__device__ __forceinline__ double mi_any(double d, int per, double L, double iL)
+{
+    return per ? d - L * rint(d * iL) : d;
+}
+
+// rho_i, P_i over all j != i within rc (Eqs. A2, A3); F'(rho_i), M'(P_i) to scratch,
+// F(rho_i), M(P_i) into the CTA's sums
+__global__ void __launch_bounds__(MD_SMALL_BLOCK) k_small_density(SmallArgs g, PotDev P)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[2] = {0.0, 0.0};
+    if (i < g.n) {
+        const double xi = g.x[3 * i], yi = g.x[3 * i + 1], zi = g.x[3 * i + 2];
+        double rho = 0.0, Ps = 0.0;
+        for (int j = 0; j < g.n; ++j) {
+            if (j == i) continue;
+            const double dx = mi_any(g.x[3 * j] - xi, g.per[0], g.L[0], g.iL[0]);
+            const double dy = mi_any(g.x[3 * j + 1] - yi, g.per[1], g.L[1], g.iL[1]);
+            const double dz = mi_any(g.x[3 * j + 2] - zi, g.per[2], g.L[2], g.iL[2]);
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < P.rc2) {
+                double f, df;
+                f_64(P, sqrt(r2), f, df);
+                rho += f;
+                Ps += f * f;
+            }
+        }
+        double F, Fp, M, Mp;
+        embed_64(P, rho, F, Fp);
+        mterm_64(P, Ps, M, Mp);
+        g.fm[2 * i] = Fp;
+        g.fm[2 * i + 1] = Mp;
+        acc[0] = F; acc[1] = M;
+    }
+    cta_partials<2>(acc, g.part, g.nb, blockIdx.x);
+}
+
+// forces (Eq. (1) with the M term, Morse Eq. A5) and the pair / Morse energies
+__global__ void __launch_bounds__(MD_SMALL_BLOCK) k_small_force(SmallArgs g, PotDev P)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[2] = {0.0, 0.0};
+    if (i < g.n) {
+        const double xi = g.x[3 * i], yi = g.x[3 * i + 1], zi = g.x[3 * i + 2];
+        const double fpi = g.fm[2 * i], mpi = g.fm[2 * i + 1];
+        double gx = 0.0, gy = 0.0, gz = 0.0, ep = 0.0, em = 0.0;
+        for (int j = 0; j < g.n; ++j) {
+            if (j == i) continue;
+            const double dx = mi_any(g.x[3 * j] - xi, g.per[0], g.L[0], g.iL[0]);
+            const double dy = mi_any(g.x[3 * j + 1] - yi, g.per[1], g.L[1], g.iL[1]);
+            const double dz = mi_any(g.x[3 * j + 2] - zi, g.per[2], g.L[2], g.iL[2]);
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < P.rc2) {
+                const double rr = sqrt(r2);
+                double f, df, ph, dph;
+                f_64(P, rr, f, df);
+                phi_64(P, rr, ph, dph);
+                const double coef = ((fpi + g.fm[2 * j]) * df + (mpi + g.fm[2 * j + 1]) * 2.0 * f * df + dph) / rr;
+                gx += coef * dx; gy += coef * dy; gz += coef * dz;
+                ep += 0.5 * ph;
+            }
+        }
+        for (int c = 0; c < g.n_c; ++c) {
+            const double dx = mi_any(g.xc[3 * c] - xi, g.per[0], g.L[0], g.iL[0]);
+            const double dy = mi_any(g.xc[3 * c + 1] - yi, g.per[1], g.L[1], g.iL[1]);
+            const double dz = mi_any(g.xc[3 * c + 2] - zi, g.per[2], g.L[2], g.iL[2]);
+            const double y2 = dx * dx + dy * dy + dz * dz;
+            if (y2 < P.rcm2) {
+                const double y = sqrt(y2);
+                double v, dv;
+                morse_64(P, y, v, dv);
+                gx += dv * dx / y; gy += dv * dy / y; gz += dv * dz / y;
+                em += v;
+            }
+        }
+        g.F[3 * i] = gx; g.F[3 * i + 1] = gy; g.F[3 * i + 2] = gz;
+        acc[0] = ep; acc[1] = em;
+    }
+    cta_partials<2>(acc, g.part + 2 * (size_t)g.nb, g.nb, blockIdx.x);
+}
+
+// the four energies: CTA sums added in block order by one thread each
+__global__ void k_small_energy(SmallArgs g)
+{
+    const int t = threadIdx.x;   // 0 embed, 1 mterm, 2 pair, 3 morse in part
+    if (t >= 4) return;
+    double s = 0.0;
+    for (int b = 0; b < g.nb; ++b) s += g.part[(size_t)t * g.nb + b];
+    const int slot[4] = {0, 2, 1, 3};   // -> embed, pair, mterm, morse
+    g.energy[slot[t]] = s;
+}
+
+}  // namespace
+
+cudaError_t small_setup(double **scratch, size_t *n_doubles)
+{
+    *n_doubles = SMALL_SCRATCH_DOUBLES;
+    cudaError_t e = cudaGetSymbolAddress((void **)scratch, g_small_scratch);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, k_small_density)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, k_small_force)) != cudaSuccess) return e;
+    return cudaFuncGetAttributes(&fa, k_small_energy);
+}
+
+cudaError_t launch_small(const SmallArgs &g, const PotDev &P, cudaStream_t s)
+{
+    k_small_density<<<g.nb, MD_SMALL_BLOCK, 0, s>>>(g, P);
+    k_small_force<<<g.nb, MD_SMALL_BLOCK, 0, s>>>(g, P);
+    k_small_energy<<<1, 32, 0, s>>>(g);
+    return cudaGetLastError();
+}

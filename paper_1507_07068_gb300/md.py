@@ -78,7 +78,7 @@ class MDError(RuntimeError):
 _lib = None
 EXPORTS = ["md_init", "md_build_neighbors", "md_compute_forces", "md_step", "md_step_profiled",
            "md_get_energy", "md_get_forces", "md_get_indenter_load", "md_get_state", "md_set_state",
-           "md_get_neighbors", "md_get_info", "md_last_error", "md_free", "md_version"]
+           "md_get_neighbors", "md_get_info", "md_last_error", "md_free", "md_version", "md_forces_small"]
 
 
 def lib(build: bool = True):
@@ -109,6 +109,8 @@ def lib(build: bool = True):
     L.md_free.argtypes = [vp]
     L.md_free.restype = None
     L.md_version.restype = C.c_int
+    L.md_forces_small.argtypes = [C.POINTER(md_params), C.c_int32, vp, C.c_int32, vp, C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double), C.POINTER(C.c_int32), vp, vp, vp, C.c_char_p, C.c_size_t]
     for name in EXPORTS:
         if name not in ("md_last_error", "md_free", "md_version"):
             getattr(L, name).restype = C.c_int
@@ -240,6 +242,23 @@ def md_last_error(h=None) -> str:
 
 def md_version() -> int:
     return int(lib().md_version())
+
+
+MD_SMALL_MAX_ATOMS = 16384
+
+
+def md_forces_small(params: md_params, n_cr: int, x_cr: int, n_c: int, x_c: Optional[int], box_lo, box_hi,
+                    periodic, F: int, energy: int, stream: int = 0):
+    """The allocation-free entry point.  x_cr, x_c, F and energy are device addresses of
+    caller-owned buffers (x_cr, F: n_cr x 3 doubles; x_c: n_c x 3; energy: 4 doubles)."""
+    lo = (C.c_double * 3)(*[float(t) for t in box_lo])
+    hi = (C.c_double * 3)(*[float(t) for t in box_hi])
+    per = (C.c_int32 * 3)(*[int(t) for t in periodic])
+    msg = C.create_string_buffer(256)
+    rc = lib().md_forces_small(C.byref(params), int(n_cr), x_cr, int(n_c), x_c, lo, hi, per, F, energy,
+                               C.c_void_p(stream), msg, len(msg))
+    if rc != MD_OK:
+        raise MDError(rc, msg.value.decode())
 
 
 # ----------------------------------------------------------------------------- convenience
