@@ -145,23 +145,25 @@ def job_value(n_cr_per_rank: int, world: int, steps: int, ms_max: float) -> floa
     return n_cr_per_rank * world * steps / (ms_max * 1e-3)
 
 
-def algorithmic_bytes(kernel: str, kmean: float, kin: float, precision: str) -> float:
-    """Bytes per Cr atom that the kernel must move (int32 lists, neighbour data counted
-    once): K = Verlet-list length, K_in = inner-list length (entries within rc)."""
+def algorithmic_bytes(kernel: str, kmean: float, kin: float, kskin: float, precision: str) -> float:
+    """Bytes per Cr atom that the kernel must move in a step (int32 lists, neighbour data
+    counted once): K = Verlet-list length, K_in = pairs within rc, K_skin = inner-list
+    length (pairs within rc + inner skin)."""
     if precision == "mixed":
         if kernel == "density":
-            # cnt 4 + list 4K + float4 position 16 + (F', M') out 8 + inner list out 4K_in + icnt out 4
-            return 4 * kmean + 4 * kin + 32
-        # icnt 4 + inner 4K_in + position 16 + (F', M') 8 + F out 24 + v in/out 48 + fixed 1 + cntc 4
+            # a step that keeps the inner list: icnt 4 + inner 4K_skin + float4 position 16 +
+            # (F', M') out 8 + row mask 8 (the list rebuilds, every few steps, are extra)
+            return 4 * kskin + 36
+        # rcnt 4 + rc list 4K_in + position 16 + (F', M') 8 + F out 24 + v in/out 48 + fixed 1 + cntc 4
         return 4 * kin + 105
     if kernel == "density":
         return 4 * kmean + 44          # cnt + list + 3 FP64 coordinates 24 + (F', M') out 16
     return 4 * kmean + 121             # cnt + list + coordinates 24 + (F', M') 16 + F 24 + v 48 + fixed + cntc
 
 
-def inner_mean(sim, rep, rc: float, sample: int = 20000, seed: int = 0) -> float:
-    """Mean number of Verlet-list entries within rc at the current positions (the inner
-    list length), from a random sample of atoms of replica 0."""
+def inner_mean(sim, rep, radii, sample: int = 20000, seed: int = 0):
+    """Mean number of Verlet-list entries within each radius at the current positions,
+    from a random sample of atoms of replica 0."""
     x = sim.state(0)[0]
     _, cnt, nbr = sim.neighbors(0, 0)
     rng = np.random.default_rng(seed)
@@ -174,7 +176,7 @@ def inner_mean(sim, rep, rc: float, sample: int = 20000, seed: int = 0) -> float
         if rep.periodic[k]:
             d[..., k] -= np.round(d[..., k] / L[k]) * L[k]
     r2 = (d * d).sum(-1)
-    return float(((r2 < rc * rc) & valid).sum(1).mean())
+    return [float(((r2 < r * r) & valid).sum(1).mean()) for r in radii]
 
 
 def kernel_source_hash() -> str:
@@ -219,7 +221,7 @@ def run_gpu(args):
     n_c = sum(r.n_c for r in reps)
     stream = torch.cuda.current_stream()
     sim = md.MD(reps, params, precision=args.precision, skin=args.skin, rebuild_every=args.rebuild_every,
-                tpa=args.tpa, block=args.block, use_graph=not args.no_graph)
+                tpa=args.tpa, block=args.block, use_graph=not args.no_graph, inner_skin=args.inner_skin)
 
     def barrier():
         if dist is not None:
@@ -246,11 +248,12 @@ def run_gpu(args):
     prof = sim.step_profiled(args.profile_steps)
     _, cnt, _ = sim.neighbors(0, 0, kmax=1)
     kmean = float(cnt.mean())
-    kin = inner_mean(sim, reps[0], params["rc"])
+    inner_skin = args.inner_skin if args.inner_skin > 0 else (0.0 if args.inner_skin < 0 else 0.1)
+    kin, kskin = inner_mean(sim, reps[0], (params["rc"], params["rc"] + inner_skin))
     phases = {k: prof[k] / prof["steps"] for k in ("skin", "rebuild", "verlet1", "density", "force", "reduce")}
     dom = "force" if phases["force"] >= phases["density"] else "density"
     peak, peak_kind = load_peaks()
-    bytes_per_launch = algorithmic_bytes(dom, kmean, kin, args.precision) * n_cr
+    bytes_per_launch = algorithmic_bytes(dom, kmean, kin, kskin, args.precision) * n_cr
     achieved = bytes_per_launch / (phases[dom] * 1e-3) / 1e9
     traffic = dram_traffic(args.workload, args.precision, dom)
 
@@ -323,6 +326,8 @@ def run_gpu(args):
                    "potential": ("analytic FP32 forms in the pair loops, FP64 state" if args.precision == "mixed"
                                  else "cubic Hermite tables (FP64)") + ", shifted-force cut-offs",
                    "skin_A": args.skin,
+                   "inner_list": ("rebuilt every step (radius rc)" if args.inner_skin < 0 else
+                                  "skin %.3g A, rebuilt when an atom moved half of it" % (args.inner_skin or 0.1)),
                    "rebuild": ("every %d steps" % args.rebuild_every) if args.rebuild_every
                    else "displacement rule 2 max|dx| > skin (conditional graph node)",
                    "rebuilds_in_timed_region": rebuilds, "tpa": args.tpa or 1, "block": args.block or 128,
@@ -330,8 +335,9 @@ def run_gpu(args):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
-                     "algorithmic_bytes_per_atom": algorithmic_bytes(dom, kmean, kin, args.precision),
-                     "mean_list_length": kmean, "mean_inner_length": kin, "launch_ms": phases[dom]},
+                     "algorithmic_bytes_per_atom": algorithmic_bytes(dom, kmean, kin, kskin, args.precision),
+                     "mean_list_length": kmean, "mean_pairs_within_rc": kin, "mean_inner_length": kskin,
+                     "launch_ms": phases[dom]},
         "phases_ms_per_step": phases,
         "clocks": clk.summary(),
         "e2e": e2e,
@@ -436,6 +442,8 @@ def main():
     ap.add_argument("--tpa", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--skin", type=float, default=0.3)
+    ap.add_argument("--inner-skin", type=float, default=0.0,
+                    help="skin of the inner list (0 = library default 0.1 A; < 0 = rebuilt every step)")
     ap.add_argument("--rebuild-every", type=int, default=0)
     ap.add_argument("--no-graph", action="store_true",
                     help="direct launches instead of graph replay (for launch-list profiling)")

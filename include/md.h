@@ -119,6 +119,12 @@ typedef struct md_system {
  *   tpa           : threads per atom in the force kernels, 1, 2, 4 or 8 (0 = default)
  *   block         : threads per block in the force kernels (0 = default)
  *   use_graph     : nonzero = md_step replays a captured CUDA graph
+ *   inner_skin    : MD_MIXED only.  The inner list (Sec. 2.6: the Verlet-list entries the
+ *                   density and force loops visit) holds the pairs within rc + inner_skin
+ *                   and is rebuilt from the Verlet list when an atom has moved more than
+ *                   inner_skin / 2 since its last build; 0 = default 0.1 A; < 0 = rebuilt
+ *                   every step with radius rc, as in the paper.  Forces do not depend on
+ *                   it: both loops take exactly the pairs within rc, in Verlet-list order.
  */
 typedef struct md_options {
     const md_params *pot;
@@ -128,6 +134,7 @@ typedef struct md_options {
     int32_t kmax, kcmax;
     int32_t tpa, block;
     int32_t use_graph;
+    double inner_skin;
 } md_options;
 
 /* Energies of one replica after the last force evaluation (eV); FP64 sums. */

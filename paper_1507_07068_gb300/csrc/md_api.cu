@@ -12,7 +12,7 @@
 
 #include "md_internal.h"
 
-#define MD_ABI_VERSION 1
+#define MD_ABI_VERSION 2
 
 namespace {
 
@@ -166,6 +166,8 @@ int rebuild_growing(md_t *h)
             if (h->a.mixed) {
                 if ((rc = dalloc(h, &p, (size_t)k * h->a.S))) return rc;
                 h->a.inner = p;
+                if ((rc = dalloc(h, &p, (size_t)k * h->a.S))) return rc;
+                h->a.rcl = p;
             }
             h->a.kmax = k; grow = true;
         }
@@ -307,8 +309,8 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
         return fail(nullptr, MD_ERR_ARG, "md_init: null argument or n_replicas < 1");
     if (opt->precision != MD_FP64 && opt->precision != MD_MIXED)
         return fail(nullptr, MD_ERR_ARG, "md_init: precision must be MD_FP64 or MD_MIXED");
-    if (!(opt->skin >= 0.0) || opt->rebuild_every < 0)
-        return fail(nullptr, MD_ERR_ARG, "md_init: skin must be >= 0 and rebuild_every >= 0");
+    if (!(opt->skin >= 0.0) || opt->rebuild_every < 0 || !isfinite(opt->inner_skin))
+        return fail(nullptr, MD_ERR_ARG, "md_init: skin must be >= 0, rebuild_every >= 0 and inner_skin finite");
     int tpa = opt->tpa ? opt->tpa : 1;
     int block = opt->block ? opt->block : 128;
     if (!(tpa == 1 || tpa == 2 || tpa == 4 || tpa == 8) || block < 32 || block > 256 || block % 32 ||
@@ -426,6 +428,20 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     a.mixed = opt->precision == MD_MIXED;
     a.rebuild_every = opt->rebuild_every;
     a.skin = opt->skin; a.cut = cut; a.cutc = cutc; a.cut2 = cut * cut; a.cutc2 = cutc * cutc;
+    {
+        // inner list: entries within rc + d (FP32 test); rebuilt once an atom has moved
+        // (FP32 estimate, error < 1e-6 A) more than (d - 1e-4) / 2 since its last build, so
+        // every pair then within rc was within rc + d - 1e-4 + 2e-6 at the build
+        const double d = opt->inner_skin > 0 ? opt->inner_skin : MD_INNER_SKIN;
+        if (opt->inner_skin < 0) {   // every step, radius rc
+            a.rin2 = (float)(h->pot_h.rc * h->pot_h.rc);
+            a.ithr2 = -1.0f;
+        } else {
+            const double rin = h->pot_h.rc + d, half = 0.5 * (d - 1e-4);
+            a.rin2 = (float)(rin * rin);
+            a.ithr2 = (float)(half * half);
+        }
+    }
     a.C = (int)cslots;
     a.max_blocks = S / (block / tpa) + 1;
 
@@ -453,11 +469,15 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     INIT_FAIL(dalloc(h, &a.cnt, S));
     INIT_FAIL(dalloc(h, &a.inner, a.mixed ? (size_t)a.kmax * S : 1));
     INIT_FAIL(dalloc(h, &a.icnt, S));
+    INIT_FAIL(dalloc(h, &a.rcl, a.mixed ? (size_t)a.kmax * S : 1));
+    INIT_FAIL(dalloc(h, &a.rcnt, S));
+    INIT_FAIL(dalloc(h, &a.rmask, S));
     INIT_FAIL(dalloc(h, &a.nbrc, (size_t)a.kcmax * S));
     INIT_FAIL(dalloc(h, &a.cntc, S));
     INIT_FAIL(dalloc(h, &a.cand, S));
     INIT_FAIL(dalloc(h, &a.near, S));
     INIT_FAIL(dalloc(h, &a.fmorse, S));
+    if (a.mixed) INIT_FAIL(dalloc(h, &a.pin, S));
     INIT_FAIL(dalloc(h, &a.key, S));
     INIT_FAIL(dalloc(h, &a.perm, S));
     INIT_FAIL(dalloc(h, &a.cell_count, cells));

@@ -34,6 +34,9 @@
 
 // error bits raised by kernels (device word, read by the host after md_step)
 enum { MDE_OVERFLOW = 1, MDE_LOST = 2, MDE_SKIN = 4, MDE_COVERFLOW = 8 };
+// skin of the inner list (A): rebuilt from the Verlet list when an atom has moved more than
+// half of it since the last rebuild
+#define MD_INNER_SKIN 0.1
 
 // Hermite cubic coefficients of one table interval, c0 + c1 t + c2 t^2 + c3 t^3
 struct alignas(32) Cf64 {
@@ -130,6 +133,9 @@ struct DevStatus {
     int32_t pos4_ok;        // pos4 holds every atom's current position about its cell's centre
     int32_t n_cand;         // atoms queued for the Cr-C list search (set by k_nbrc)
     int32_t n_near;         // atoms with Cr-C neighbours (set by k_nbrc_near)
+    uint32_t imax_bits;     // mixed: max over atoms of |p - p_in|^2 (FP32 bits) after k_verlet1
+    int32_t inner_ok;       // mixed: the inner list is valid for this step's k_density
+    int32_t inner_ok_next;  // set by the k_density that rebuilt it; k_decide moves it over
     int32_t pad_;
     int64_t step, rebuilds, since_build;
 };
@@ -155,8 +161,12 @@ struct DevArgs {
     float4 *pos4;
     double2 *fm64;
     float2 *fm32;
-    int32_t *inner, *icnt;       // mixed precision: entries of the Verlet list within rc at the
-                                 // current positions (the inner list, rebuilt every step)
+    int32_t *inner, *icnt;       // mixed precision: the inner list, entries of the Verlet list
+                                 // within rc + MD_INNER_SKIN when it was last rebuilt
+    float4 *pin;                 // mixed: pos4 of each atom when the inner list was rebuilt
+    int32_t *rcl, *rcnt;         // mixed: the entries of the inner list within rc (k_force's list)
+    unsigned long long *rmask;   // mixed, one thread per atom: which inner rows rcl holds
+    float rin2, ithr2;           // (rc + MD_INNER_SKIN)^2; max |p - p_in|^2 before a rebuild
     int32_t *cellc, *orig;
     uint8_t *fixed;
     int32_t *nbr, *cnt, *nbrc, *cntc;

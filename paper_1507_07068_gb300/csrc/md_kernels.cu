@@ -405,6 +405,8 @@ __global__ void k_decide(DevArgs a, int force, int use_cond, cudaGraphConditiona
     }
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
+        a.st->inner_ok = a.st->inner_ok_next;   // a rebuild of the Verlet list below clears both
+        a.st->imax_bits = 0u;
         a.st->any_rebuild = any;
         if (use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
     }
@@ -851,7 +853,10 @@ __global__ void __launch_bounds__(256) k_nbrc_near(DevArgs a)
 __global__ void k_build_done(DevArgs a)
 {
     for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) a.rs[r].z_build = a.rs[r].z_ind;
-    if (threadIdx.x == 0) { a.st->rebuilds += 1; a.st->since_build = 0; }
+    if (threadIdx.x == 0) {
+        a.st->rebuilds += 1; a.st->since_build = 0;
+        a.st->inner_ok = 0; a.st->inner_ok_next = 0;   // slots were permuted: the inner list is stale
+    }
 }
 
 // ============================================================================ Tasks 2 + 3
@@ -873,6 +878,7 @@ __global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
         }
     }
     unsigned long long d2bits = 0ull;
+    unsigned ibits = 0u;
     if (s - R.slot_off < R.n_atoms) {
         const size_t S = a.S;
         double x0 = a.x[s], x1 = a.x[S + s], x2 = a.x[2 * S + s];
@@ -888,19 +894,33 @@ __global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
         double d2 = norm2_exact(__dsub_rn(x0, a.xb[s]), __dsub_rn(x1, a.xb[S + s]), __dsub_rn(x2, a.xb[2 * S + s]));
         if (d2 != d2) d2 = 1e300;   // NaN position: force a rebuild, which reports it
         d2bits = (unsigned long long)__double_as_longlong(d2);   // d2 >= 0: bit order = value order
-        if (a.mixed) a.pos4[s] = rel_pos3(a, R, a.cellc[s], x0, x1, x2);
+        if (a.mixed) {
+            const float4 p = rel_pos3(a, R, a.cellc[s], x0, x1, x2);
+            a.pos4[s] = p;
+            // displacement since the inner list was rebuilt (same cell frame: a rebuild of the
+            // Verlet list in between invalidates the inner list anyway)
+            const float4 q = a.pin[s];
+            const float ex = p.x - q.x, ey = p.y - q.y, ez = p.z - q.z;
+            float dm2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            if (!(dm2 <= 1e30f)) dm2 = 1e30f;   // not finite: force the rebuild
+            ibits = __float_as_uint(dm2);       // dm2 >= 0: bit order = value order
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         unsigned long long t = __shfl_xor_sync(0xffffffffu, d2bits, o);
         d2bits = t > d2bits ? t : d2bits;
+        ibits = max(ibits, __shfl_xor_sync(0xffffffffu, ibits, o));
     }
     __shared__ unsigned long long sm[MD_TILE / 32];
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = d2bits;
+    __shared__ unsigned smi[MD_TILE / 32];
+    if ((threadIdx.x & 31) == 0) { sm[threadIdx.x >> 5] = d2bits; smi[threadIdx.x >> 5] = ibits; }
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long m = 0ull;
-        for (int w = 0; w < MD_TILE / 32; ++w) m = sm[w] > m ? sm[w] : m;
+        unsigned mi = 0u;
+        for (int w = 0; w < MD_TILE / 32; ++w) { m = sm[w] > m ? sm[w] : m; mi = max(mi, smi[w]); }
         if (m) atomicMax(&a.rs[r].d2max_bits, m);
+        if (mi) atomicMax(&a.st->imax_bits, mi);
     }
 }
 
@@ -1011,11 +1031,24 @@ __device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, flo
     dph = t * fmaf(fmaf(fmaf(5.0f * Q.b3, t, 4.0f * Q.b2), t, 3.0f * Q.b1), t, 2.0f * Q.b0) * Q.inv_re;
 }
 
-// Task 4a (Eqs. A2-A3): rho_i, P_i over the list entries within rc; F'(rho_i), M'(P_i) stored,
+// Task 4a (Eqs. A2-A3): rho_i, P_i over the pairs within rc; F'(rho_i), M'(P_i) stored,
 // F(rho_i), M(P_i) into the CTA's energy partials.  MD_UNROLL entries per lane are loaded
 // (list entry, then position) before any is used.
+//
+// Lists (all in Verlet-list order, so every loop takes the pairs within rc in the same
+// order and the sums do not depend on which list a step uses):
+//  - the inner list (Sec. 2.6): the Verlet-list entries within rc + inner skin at its last
+//    rebuild.  Every pair within rc is in it while no atom has moved more than half the
+//    skin since (k_verlet1 reduces the displacement); then it is rebuilt from the Verlet
+//    list.  With inner skin < 0 it is rebuilt every step with radius rc, as in the paper.
+//  - the rc list: the inner-list entries within rc now, which k_force loops over without a
+//    distance test.  With one thread per atom and at most 64 inner entries, a 64-bit mask
+//    of those rows is kept and the rc list is rewritten only for atoms whose mask changed
+//    (a pair crossed rc since the last step); otherwise it is written as the loop goes.
+// The launch bound caps the kernel at 51 registers (48 used, no spills): with both loops in
+// one kernel the compiler otherwise takes 60-64 and the loss of occupancy costs ~10 %.
 template <int TPA>
-__global__ void __launch_bounds__(256) k_density_mixed(DevArgs a, PotDev P)
+__global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
 {
     __shared__ float4 sm_off[64];
     const int A = blockDim.x / TPA;
@@ -1027,51 +1060,115 @@ __global__ void __launch_bounds__(256) k_density_mixed(DevArgs a, PotDev P)
     const Pot32 &Q = static_cast<const Pot32 &>(P.q);
     const bool real = (s - R.slot_off) < R.n_atoms;
     const size_t S = a.S;
+    // uniform over the launch: nothing below writes inner_ok or imax_bits
+    const bool rebuild = !a.st->inner_ok || !(__uint_as_float(a.st->imax_bits) <= a.ithr2);
     float rho = 0.f, Ps = 0.f;
-    int m = 0;   // inner-list entries of this lane
+    int m = 0, mr = 0;   // inner-list and rc-list entries of this lane
     if (real) {
         const float4 pi = a.pos4[s];
         const PairGeom G = pair_geom(R, __float_as_int(pi.w));
-        const int n = a.cnt[s];
-        for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
-            unsigned e[MD_UNROLL];
+        unsigned long long mask = 0ull;   // inner rows within rc (one thread per atom)
+        if (rebuild) {
+            const int n = a.cnt[s];
+            for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
+                unsigned e[MD_UNROLL];
 #pragma unroll
-            for (int u = 0; u < MD_UNROLL; ++u) {
-                const int k = k0 + u * TPA;
-                e[u] = k < n ? (unsigned)__ldg(&a.nbr[(size_t)k * S + s]) : (unsigned)s;
+                for (int u = 0; u < MD_UNROLL; ++u) {
+                    const int k = k0 + u * TPA;
+                    e[u] = k < n ? (unsigned)__ldg(&a.nbr[(size_t)k * S + s]) : (unsigned)s;
+                }
+                float4 pj[MD_UNROLL];
+#pragma unroll
+                for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&a.pos4[e[u] & MD_J_MASK]);
+#pragma unroll
+                for (int u = 0; u < MD_UNROLL; ++u) {
+                    float dx, dy, dz;
+                    disp(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    if (k0 + u * TPA < n && r2 < a.rin2) {
+                        // lane-interleaved rows: each lane owns rows lane, lane + TPA, ...
+                        a.inner[(size_t)(m * TPA + lane) * S + s] = (int32_t)e[u];
+                        if (r2 < Q.rc2) {
+                            const float f = fa_val(Q, r2);
+                            rho += f;
+                            Ps = fmaf(f, f, Ps);
+                            a.rcl[(size_t)(mr * TPA + lane) * S + s] = (int32_t)e[u];
+                            ++mr;
+                            if (m < 64) mask |= 1ull << m;
+                        }
+                        ++m;
+                    }
+                }
             }
-            float4 pj[MD_UNROLL];
+            if (lane == 0) a.pin[s] = pi;
+            if (TPA == 1) a.rmask[s] = mask;
+        } else {
+            const int n = a.icnt[s];
+            const bool direct = TPA > 1 || n > 64;   // no mask: the rc list is written as we go
+            for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
+                unsigned e[MD_UNROLL], nib = 0u;
 #pragma unroll
-            for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&a.pos4[e[u] & MD_J_MASK]);
+                for (int u = 0; u < MD_UNROLL; ++u) {
+                    const int k = k0 + u * TPA;
+                    e[u] = k < n ? (unsigned)__ldg(&a.inner[(size_t)k * S + s]) : (unsigned)s;
+                }
+                float4 pj[MD_UNROLL];
 #pragma unroll
-            for (int u = 0; u < MD_UNROLL; ++u) {
-                float dx, dy, dz;
-                disp(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (k0 + u * TPA < n && r2 < Q.rc2) {
-                    const float f = fa_val(Q, r2);
+                for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&a.pos4[e[u] & MD_J_MASK]);
+#pragma unroll
+                for (int u = 0; u < MD_UNROLL; ++u) {
+                    float dx, dy, dz;
+                    disp(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    // padding entries (the atom itself) and entries now beyond rc drop out
+                    const bool in = (e[u] & MD_J_MASK) != (unsigned)s && r2 < Q.rc2;
+                    float f = fa_val(Q, in ? r2 : Q.re2);
+                    f = in ? f : 0.0f;
                     rho += f;
                     Ps = fmaf(f, f, Ps);
-                    // the inner list (Sec. 2.6): entries within rc at these positions, in
-                    // lane-interleaved rows so each lane owns rows lane, lane + TPA, ...
-                    a.inner[(size_t)(m * TPA + lane) * S + s] = (int32_t)e[u];
-                    ++m;
+                    nib |= (in ? 1u : 0u) << u;
+                    if (direct && in) {
+                        a.rcl[(size_t)(mr * TPA + lane) * S + s] = (int32_t)e[u];
+                        ++mr;
+                    }
                 }
+                if (!direct) mask |= (unsigned long long)nib << k0;
+            }
+            if (!direct) {
+                const unsigned long long old = a.rmask[s];
+                if (mask != old) {   // a pair crossed rc: rewrite this atom's rc list
+                    for (unsigned long long b = mask; b; b &= b - 1) {
+                        const int k = __ffsll((long long)b) - 1;
+                        a.rcl[(size_t)mr * S + s] = a.inner[(size_t)k * S + s];
+                        ++mr;
+                    }
+                    a.rmask[s] = mask;
+                    a.rcnt[s] = mr;
+                }
+                mr = -1;   // rcnt kept (or just written)
             }
         }
     }
-    int mmax = m;
+    int mmax = m, mrmax = mr;
 #pragma unroll
     for (int o = TPA / 2; o > 0; o >>= 1) {
         rho += __shfl_xor_sync(0xffffffffu, rho, o);
         Ps += __shfl_xor_sync(0xffffffffu, Ps, o);
         mmax = max(mmax, __shfl_xor_sync(0xffffffffu, mmax, o));
+        mrmax = max(mrmax, __shfl_xor_sync(0xffffffffu, mrmax, o));
     }
-    // rows of lanes with fewer entries are padded with the atom itself (skipped by k_force)
     if (real) {
-        for (int k = m; k < mmax; ++k) a.inner[(size_t)(k * TPA + lane) * S + s] = s;
-        if (lane == 0) a.icnt[s] = mmax * TPA;
+        // rows of lanes with fewer entries are padded with the atom itself (skipped)
+        if (rebuild) {
+            for (int k = m; k < mmax; ++k) a.inner[(size_t)(k * TPA + lane) * S + s] = s;
+            if (lane == 0) a.icnt[s] = mmax * TPA;
+        }
+        if (mr >= 0) {
+            for (int k = mr; k < mrmax; ++k) a.rcl[(size_t)(k * TPA + lane) * S + s] = s;
+            if (lane == 0) a.rcnt[s] = mrmax * TPA;
+        }
     }
+    if (rebuild && blockIdx.x == 0 && threadIdx.x == 0) a.st->inner_ok_next = 1;   // read by the next k_decide
     float acc[2] = {0.f, 0.f};
     if (real && lane == 0) {
         float F, Fp, M, Mp;
@@ -1106,13 +1203,13 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
         const float4 pi = a.pos4[s];
         const PairGeom G = pair_geom(R, __float_as_int(pi.w));
         const float2 fmi = a.fm32[s];
-        const int n = a.icnt[s];
+        const int n = a.rcnt[s];
         for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
             unsigned e[MD_UNROLL];
 #pragma unroll
             for (int u = 0; u < MD_UNROLL; ++u) {
                 const int k = k0 + u * TPA;
-                e[u] = k < n ? (unsigned)__ldg(&a.inner[(size_t)k * S + s]) : (unsigned)s;
+                e[u] = k < n ? (unsigned)__ldg(&a.rcl[(size_t)k * S + s]) : (unsigned)s;
             }
             float4 pj[MD_UNROLL];
             float2 fmj[MD_UNROLL];
@@ -1127,7 +1224,7 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
                 float dx, dy, dz;
                 disp(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if ((e[u] & MD_J_MASK) != (unsigned)s) {   // inner entries are within rc; padding is the atom itself
+                if ((e[u] & MD_J_MASK) != (unsigned)s) {   // rc-list entries are within rc; padding is the atom itself
                     const float rinv = rsqrt_nr(r2);
                     float f, df, ph, dph;
                     fa_phi(Q, r2, rinv, f, df, ph, dph);

@@ -49,7 +49,8 @@ class md_system(C.Structure):
 class md_options(C.Structure):
     _fields_ = [("pot", C.POINTER(md_params)), ("precision", C.c_int32), ("skin", C.c_double),
                 ("rebuild_every", C.c_int32), ("kmax", C.c_int32), ("kcmax", C.c_int32),
-                ("tpa", C.c_int32), ("block", C.c_int32), ("use_graph", C.c_int32)]
+                ("tpa", C.c_int32), ("block", C.c_int32), ("use_graph", C.c_int32),
+                ("inner_skin", C.c_double)]
 
 
 class md_energy(C.Structure):
@@ -286,7 +287,8 @@ class MD:
 
     def __init__(self, replicas, params: Optional[dict] = None, precision: str = "mixed", skin: float = 0.3,
                  rebuild_every: int = 0, kmax: int = 0, kcmax: int = 0, tpa: int = 0, block: int = 0,
-                 use_graph: bool = True, stream: Optional[int] = None, **pot_override):
+                 use_graph: bool = True, stream: Optional[int] = None, inner_skin: float = 0.0,
+                 **pot_override):
         self.replicas = list(replicas)
         self.n = [r.n_cr for r in self.replicas]
         self._params = make_params(params or load_params(), **pot_override)
@@ -300,6 +302,7 @@ class MD:
         opt.skin = float(skin); opt.rebuild_every = int(rebuild_every)
         opt.kmax = int(kmax); opt.kcmax = int(kcmax); opt.tpa = int(tpa); opt.block = int(block)
         opt.use_graph = 1 if use_graph else 0
+        opt.inner_skin = float(inner_skin)
         self._opt = opt
         self.stream = current_stream() if stream is None else int(stream)
         self.h = md_init(systems, opt, self.stream)

@@ -222,6 +222,24 @@ def test_trajectory_mixed_tracks_oracle(md, params):
     assert sim.energy(0)["total"] == pytest.approx(o["total"], abs=1e-5 * rep.n_cr)
 
 
+@pytest.mark.parametrize("inner_skin", [0.1, 0.02])
+def test_inner_list_schedule_bitwise_equal(md, params, inner_skin):
+    """The inner list rebuilt every step with radius rc (the paper's schedule) and the
+    inner list with a skin, rebuilt only when an atom has moved half of it: the density and
+    force loops take the same pairs in the same order, so trajectories agree bit for bit."""
+    rep = tiny(amp=0.05, gap=2.0, T=600.0)
+    a = md.MD([rep], params, precision="mixed", inner_skin=-1.0)
+    b = md.MD([rep], params, precision="mixed", inner_skin=inner_skin)
+    for _ in range(4):
+        a.step(50); b.step(50)
+        xa, va, za, _ = a.state(0)
+        xb, vb, zb, _ = b.state(0)
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+        assert np.array_equal(a.forces(0), b.forces(0))
+    assert a.energy(0)["total"] == b.energy(0)["total"]
+    a.close(); b.close()
+
+
 def test_graph_and_direct_launch_bitwise_equal(md, params):
     rep = tiny(amp=0.05)
     a = md.MD([rep], params, precision="mixed", use_graph=True)
