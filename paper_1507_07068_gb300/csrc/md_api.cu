@@ -478,6 +478,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     INIT_FAIL(dalloc(h, &a.near, S));
     INIT_FAIL(dalloc(h, &a.fmorse, S));
     if (a.mixed) INIT_FAIL(dalloc(h, &a.pin, S));
+    if (a.mixed) INIT_FAIL(dalloc(h, &a.pb, S));
     INIT_FAIL(dalloc(h, &a.key, S));
     INIT_FAIL(dalloc(h, &a.perm, S));
     INIT_FAIL(dalloc(h, &a.cell_count, cells));

@@ -117,7 +117,8 @@ struct RepState {
     double z_ind, z_build;
     unsigned long long d2max_bits;       // max |x - x_build|^2 since last decision (bits of a double)
     int32_t need;                        // rebuild decided for this step
-    int32_t pad;
+    float dthr;                          // mixed: displacements below this (A) cannot decide the next
+                                         // rebuild test; k_verlet1 takes them in FP32 (set by k_decide)
 };
 
 // energies of one replica (device copy of md_energy's sums)
@@ -164,6 +165,7 @@ struct DevArgs {
     int32_t *inner, *icnt;       // mixed precision: the inner list, entries of the Verlet list
                                  // within rc + MD_INNER_SKIN when it was last rebuilt
     float4 *pin;                 // mixed: pos4 of each atom when the inner list was rebuilt
+    float4 *pb;                  // mixed: pos4 of each atom when the Verlet list was rebuilt
     int32_t *rcl, *rcnt;         // mixed: the entries of the inner list within rc (k_force's list)
     unsigned long long *rmask;   // mixed, one thread per atom: which inner rows rcl holds
     float rin2, ithr2;           // (rc + MD_INNER_SKIN)^2; max |p - p_in|^2 before a rebuild

@@ -402,6 +402,19 @@ __global__ void k_decide(DevArgs a, int force, int use_cond, cudaGraphConditiona
         }
         S.need = need;
         any |= need;
+        // the next decision compares dmax with skin/2 and, with an indenter in the
+        // displacement mode, with skin - |z_ind - z_build| as they will be after this
+        // step's k_verlet1 (z_ind + v dt; z_build = z_ind if this step rebuilds).  An atom
+        // whose displacement is below both by more than the FP32 error of k_verlet1's
+        // estimate (< 1e-6 A) cannot change that decision.
+        const RepDev &Rr = a.rep[r];
+        double T = 0.5 * a.skin;
+        if (a.rebuild_every == 0 && Rr.n_c > 0) {
+            const double zn = __dadd_rn(S.z_ind, __dmul_rn(Rr.v_ind, Rr.dt));
+            const double zb = need ? S.z_ind : S.z_build;
+            T = fmin(T, a.skin - fabs(zn - zb));
+        }
+        S.dthr = (float)(T - 1e-5);
     }
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
@@ -633,7 +646,9 @@ __global__ void k_copyback(DevArgs a)
     }
     a.orig[s] = a.sorig[s];
     a.fixed[s] = a.sfixed[s];
-    a.pos4[s] = rel_pos(a, R, s);   // also used by the FP32 prefilter of k_nbr
+    const float4 p = rel_pos(a, R, s);
+    a.pos4[s] = p;   // also used by the FP32 prefilter of k_nbr
+    if (a.mixed) a.pb[s] = p;
     if (s == 0) a.st->pos4_ok = 1;
 }
 
@@ -891,12 +906,18 @@ __global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
             x0 = fma(R.dt, v0, x0); x1 = fma(R.dt, v1, x1); x2 = fma(R.dt, v2, x2);   // Eq. A11
             a.x[s] = x0; a.x[S + s] = x1; a.x[2 * S + s] = x2;
         }
-        double d2 = norm2_exact(__dsub_rn(x0, a.xb[s]), __dsub_rn(x1, a.xb[S + s]), __dsub_rn(x2, a.xb[2 * S + s]));
-        if (d2 != d2) d2 = 1e300;   // NaN position: force a rebuild, which reports it
-        d2bits = (unsigned long long)__double_as_longlong(d2);   // d2 >= 0: bit order = value order
+        bool exact = true;
         if (a.mixed) {
             const float4 p = rel_pos3(a, R, a.cellc[s], x0, x1, x2);
             a.pos4[s] = p;
+            // displacement since the Verlet-list build from the cell-relative positions
+            // (same cell frame): when clearly below the threshold k_decide set, it cannot
+            // change the next decision and the exact FP64 value is not needed
+            const float4 b = a.pb[s];
+            const float bx = p.x - b.x, by = p.y - b.y, bz = p.z - b.z;
+            const float d2f = fmaf(bx, bx, fmaf(by, by, bz * bz));
+            const float thr = a.rs[r].dthr;
+            exact = !(thr > 0.0f && d2f < thr * thr);
             // displacement since the inner list was rebuilt (same cell frame: a rebuild of the
             // Verlet list in between invalidates the inner list anyway)
             const float4 q = a.pin[s];
@@ -904,6 +925,11 @@ __global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
             float dm2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
             if (!(dm2 <= 1e30f)) dm2 = 1e30f;   // not finite: force the rebuild
             ibits = __float_as_uint(dm2);       // dm2 >= 0: bit order = value order
+        }
+        if (exact) {
+            double d2 = norm2_exact(__dsub_rn(x0, a.xb[s]), __dsub_rn(x1, a.xb[S + s]), __dsub_rn(x2, a.xb[2 * S + s]));
+            if (d2 != d2) d2 = 1e300;   // NaN position: force a rebuild, which reports it
+            d2bits = (unsigned long long)__double_as_longlong(d2);   // d2 >= 0: bit order = value order
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
