@@ -46,9 +46,10 @@ def _time_steps(sim: "md.MD", warmup: int, steps: int) -> float:
 
 def autotune(replicas: Sequence, params: Optional[dict] = None, precision: str = "mixed",
              shapes: Iterable[Tuple[int, int]] = ((1, 64), (1, 128), (2, 128), (4, 128)),
-             skins: Iterable[float] = (0.2, 0.3, 0.4), steps: int = 60, warmup: int = 5,
+             skins: Iterable[float] = (0.3, 0.6, 1.0), steps: int = 60, warmup: int = 5,
+             base_skin: float = 0.3,
              interval_safety: float = 0.7, log=None) -> Tuned:
-    """Time each (tpa, block) at the default skin, then each skin with the best shape, then
+    """Time each (tpa, block) at base_skin, then each skin with the best shape, then
     a fixed rebuild interval derived from the best skin's observed rebuild rate."""
     params = params or md.load_params()
     table: List[Tuple[dict, float]] = []
@@ -71,12 +72,12 @@ def autotune(replicas: Sequence, params: Optional[dict] = None, precision: str =
             log(f"autotune {opt}: {ms:.4f} ms/step ({time.perf_counter() - t0:.1f} s)")
         return ms
 
-    best_shape = min(shapes, key=lambda sb: trial(tpa=sb[0], block=sb[1], skin=0.3))
+    best_shape = min(shapes, key=lambda sb: trial(tpa=sb[0], block=sb[1], skin=base_skin))
     tpa, block = best_shape
-    best_skin, best_ms = 0.3, None
+    best_skin, best_ms = base_skin, None
     for skin in skins:
-        ms = trial(tpa=tpa, block=block, skin=skin) if skin != 0.3 else \
-            next(m for o, m in table if o.get("tpa") == tpa and o.get("block") == block and o.get("skin") == 0.3)
+        ms = trial(tpa=tpa, block=block, skin=skin) if skin != base_skin else \
+            next(m for o, m in table if o.get("tpa") == tpa and o.get("block") == block and o.get("skin") == base_skin)
         if best_ms is None or ms < best_ms:
             best_skin, best_ms = skin, ms
     # fixed interval from the displacement test's own rebuild rate at the chosen skin

@@ -12,6 +12,8 @@ from gpu_helpers import rel_force_err
 
 pytestmark = pytest.mark.gpu
 
+SKIN = 1.0   # the Verlet skin of the benchmark's configuration
+
 
 @pytest.fixture(scope="module")
 def md():
@@ -32,7 +34,7 @@ def film_1m():
 @pytest.fixture(scope="module")
 def thermal_1m(md, params, film_1m):
     """The 1M film after 100 FP64 steps on the GPU (a thermal configuration)."""
-    sim = md.MD([film_1m], params, precision="fp64")
+    sim = md.MD([film_1m], params, precision="fp64", skin=SKIN)
     sim.step(100)
     x, v, z, st = sim.state(0)
     F64 = sim.forces(0)
@@ -45,12 +47,12 @@ def test_fullsize_fp64_forces_and_lists(md, params, thermal_1m):
     ref = oracle.forces(oracle.Potential(params), rep.x_cr, rep.box_lo, rep.box_hi, rep.periodic,
                         rep.x_c + np.array([0.0, 0.0, rep.z_indenter0]))
     assert rel_force_err(F64, ref["F"]).max() <= 1e-11
-    sim = md.MD([rep], params, precision="fp64")
+    sim = md.MD([rep], params, precision="fp64", skin=SKIN)
     e = sim.energy(0)
     assert e["potential"] == pytest.approx(ref["potential"], rel=1e-12)
     assert e["load"] == pytest.approx(ref["load"], rel=1e-9, abs=1e-9)
     # neighbour sets of a sample of atoms, bit-exact
-    cut = params["rc"] + 0.3
+    cut = params["rc"] + SKIN
     cell, cnt, nbr = sim.neighbors(0, 0)
     ocell = oracle.cell_coords(rep.x_cr, rep.box_lo, rep.box_hi, rep.periodic, cut)
     assert np.array_equal(cell, ocell)
@@ -63,7 +65,7 @@ def test_fullsize_fp64_forces_and_lists(md, params, thermal_1m):
 
 def test_fullsize_mixed_forces(md, params, thermal_1m):
     rep, _ = thermal_1m
-    sim = md.MD([rep], params, precision="mixed")
+    sim = md.MD([rep], params, precision="mixed", skin=SKIN)
     Fm = sim.forces(0)
     ref = oracle.forces(oracle.Potential(params), rep.x_cr, rep.box_lo, rep.box_hi, rep.periodic,
                         rep.x_c + np.array([0.0, 0.0, rep.z_indenter0]))
