@@ -208,8 +208,11 @@ int md_get_indenter_load(md_t *h, int32_t replica, double *load_z, double *depth
 int md_get_state(md_t *h, int32_t replica, double *x3n, double *v3n, double *z_ind, int64_t *step);
 
 /* Replace positions and velocities (caller order; x3n or v3n may be NULL to keep), the
- * indenter displacement and the step count of one replica.  The next md_step first
- * re-checks the lists and re-evaluates forces at the new positions. */
+ * indenter displacement and the step count of one replica, then re-evaluate forces at the
+ * new state.  The neighbour lists are kept when the new positions pass the rebuild test of
+ * md_step (max |x - x_build| and the indenter's travel since the last build against the
+ * skin, Sec. 2.6), else rebuilt (as md_build_neighbors).  Errors: MD_ERR_LOST_ATOM,
+ * MD_ERR_NBR_OVERFLOW, MD_ERR_CUDA. */
 int md_set_state(md_t *h, int32_t replica, const double *x3n, const double *v3n, double z_ind, int64_t step);
 
 /* Test hook.  which = 0: Cr-Cr list, which = 1: Cr-C list, as built at the last rebuild.

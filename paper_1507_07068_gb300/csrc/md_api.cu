@@ -39,10 +39,10 @@ __global__ void k_state_out(const double *src, double *stage, const int32_t *ori
     for (int k = 0; k < 3; ++k) stage[3 * (size_t)o + k] = src[k * S + s];
 }
 
+// z_build is kept: the list test of md_set_state compares z_ind with it
 __global__ void k_set_scalars(RepState *rs, int r, double z_ind, DevStatus *st, long long step, int set_step)
 {
     rs[r].z_ind = z_ind;
-    rs[r].z_build = z_ind;
     if (set_step) st->step = step;
 }
 
@@ -785,7 +785,24 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     k_set_scalars<<<1, 1, 0, h->stream>>>(h->a.rs, r, z_ind, h->a.st, (long long)step, 1);
     CU(cudaGetLastError());
     h->forces_valid = false;
-    return ensure_forces(h);
+    // The lists stay valid when the new state passes the rebuild test md_step applies
+    // (max |x - x_build| and the indenter's travel against the skin): then only the
+    // cell-relative positions are refreshed and the inner list rebuilt.  Otherwise (or
+    // when positions leave their periodic image, become NaN, ...) a full rebuild.
+    int rc2 = clear_err(h);
+    if (rc2) return rc2;
+    CU(launch_state_check(h->a, h->stream));
+    int32_t need = 1;
+    CU(cudaMemcpyAsync(&need, &h->a.st->any_rebuild, sizeof need, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    if (need) return ensure_forces(h);
+    CU(launch_refresh_pos4(h->a, h->stream));   // also marks pos4 current and the inner list stale
+    if ((rc2 = forces_now(h, h->stream))) return rc2;
+    DevStatus st;
+    if ((rc2 = read_status(h, &st))) return rc2;
+    if ((rc2 = status_to_code(h, st))) return rc2;
+    h->forces_valid = true;
+    return MD_OK;
 }
 
 int md_get_neighbors(md_t *h, int32_t r, int32_t which, int32_t *cell_xyz, int32_t *cnt, int32_t *nbr, int32_t kmax)

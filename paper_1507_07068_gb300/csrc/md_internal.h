@@ -205,6 +205,8 @@ cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c
 cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, cudaStream_t s);
 cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_refresh_pos4(const DevArgs &a, cudaStream_t s);
+// d2max of every replica at the current positions and any_rebuild by the displacement rule
+cudaError_t launch_state_check(const DevArgs &a, cudaStream_t s);
 
 // ---- allocation-free small-system evaluation (md_forces_small): all pairs, FP64 forms
 enum { MD_SMALL_BLOCK = 128, MD_SMALL_MAX_BLOCKS = MD_SMALL_MAX_ATOMS / MD_SMALL_BLOCK };

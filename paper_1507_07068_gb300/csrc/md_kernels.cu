@@ -950,9 +950,61 @@ __global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
     }
 }
 
+// List test after positions were replaced (md_set_state): exact FP64 max |x - x_build|^2
+// per replica, as k_verlet1 reduces it for k_decide, then k_state_need applies the
+// displacement rule of k_decide (whatever the rebuild mode: the caller's positions are
+// not integrator steps) and raises any_rebuild.
+__global__ void __launch_bounds__(MD_TILE) k_state_disp(DevArgs a)
+{
+    const int s = blockIdx.x * MD_TILE + threadIdx.x;
+    const int r = a.tile_rep[blockIdx.x];
+    const RepDev &R = a.rep[r];
+    unsigned long long d2bits = 0ull;
+    if (s - R.slot_off < R.n_atoms) {
+        const size_t S = a.S;
+        double d2 = norm2_exact(__dsub_rn(a.x[s], a.xb[s]), __dsub_rn(a.x[S + s], a.xb[S + s]),
+                                __dsub_rn(a.x[2 * S + s], a.xb[2 * S + s]));
+        if (d2 != d2) d2 = 1e300;
+        d2bits = (unsigned long long)__double_as_longlong(d2);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(0xffffffffu, d2bits, o);
+        d2bits = t > d2bits ? t : d2bits;
+    }
+    __shared__ unsigned long long sm[MD_TILE / 32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = d2bits;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long m = 0ull;
+        for (int w = 0; w < MD_TILE / 32; ++w) m = sm[w] > m ? sm[w] : m;
+        if (m) atomicMax(&a.rs[r].d2max_bits, m);
+    }
+}
+
+__global__ void k_state_zero(DevArgs a)
+{
+    for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) a.rs[r].d2max_bits = 0ull;
+}
+
+__global__ void k_state_need(DevArgs a)
+{
+    int any = 0;
+    for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) {
+        const RepState &S = a.rs[r];
+        const double dmax = sqrt(__longlong_as_double((long long)S.d2max_bits));
+        any |= (2.0 * dmax > a.skin) ||
+               (a.rep[r].n_c > 0 && __dadd_rn(dmax, fabs(__dsub_rn(S.z_ind, S.z_build))) > a.skin);
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) a.st->any_rebuild = any;
+}
+
+// pos4 of every atom about its cell's centre at the current positions (cells of the last
+// build); the inner list is marked stale (the next k_density rebuilds it)
 __global__ void k_refresh_pos4(DevArgs a)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s == 0) { a.st->pos4_ok = 1; a.st->inner_ok = 0; a.st->inner_ok_next = 0; }
     if (s >= a.S) return;
     const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
     if (s - R.slot_off >= R.n_atoms) return;
@@ -1526,6 +1578,14 @@ cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s)
 cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s)
 {
     k_verlet1<<<a.S / MD_TILE, MD_TILE, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_check(const DevArgs &a, cudaStream_t s)
+{
+    k_state_zero<<<1, 256, 0, s>>>(a);
+    k_state_disp<<<a.S / MD_TILE, MD_TILE, 0, s>>>(a);
+    k_state_need<<<1, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
