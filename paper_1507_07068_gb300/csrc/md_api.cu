@@ -787,8 +787,9 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     h->forces_valid = false;
     // The lists stay valid when the new state passes the rebuild test md_step applies
     // (max |x - x_build| and the indenter's travel against the skin): then only the
-    // cell-relative positions are refreshed and the inner list rebuilt.  Otherwise (or
-    // when positions leave their periodic image, become NaN, ...) a full rebuild.
+    // cell-relative positions are refreshed (and the inner list rebuilt if its own test
+    // fails).  Otherwise (or when positions leave their periodic image, become NaN, ...)
+    // a full rebuild.
     int rc2 = clear_err(h);
     if (rc2) return rc2;
     CU(launch_state_check(h->a, h->stream));
@@ -796,7 +797,7 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     CU(cudaMemcpyAsync(&need, &h->a.st->any_rebuild, sizeof need, cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     if (need) return ensure_forces(h);
-    CU(launch_refresh_pos4(h->a, h->stream));   // also marks pos4 current and the inner list stale
+    CU(launch_refresh_pos4(h->a, h->stream));   // also the inner list's displacement test
     if ((rc2 = forces_now(h, h->stream))) return rc2;
     DevStatus st;
     if ((rc2 = read_status(h, &st))) return rc2;

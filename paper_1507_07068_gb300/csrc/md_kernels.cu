@@ -984,6 +984,7 @@ __global__ void __launch_bounds__(MD_TILE) k_state_disp(DevArgs a)
 __global__ void k_state_zero(DevArgs a)
 {
     for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) a.rs[r].d2max_bits = 0ull;
+    if (threadIdx.x == 0) a.st->imax_bits = 0u;
 }
 
 __global__ void k_state_need(DevArgs a)
@@ -1000,15 +1001,28 @@ __global__ void k_state_need(DevArgs a)
 }
 
 // pos4 of every atom about its cell's centre at the current positions (cells of the last
-// build); the inner list is marked stale (the next k_density rebuilds it)
-__global__ void k_refresh_pos4(DevArgs a)
+// build), and, in mixed precision, the displacement since the inner list was built (as
+// k_verlet1 reduces it): the next k_density keeps that list if it is still valid.
+// imax_bits must be zero on entry (k_state_zero).
+__global__ void __launch_bounds__(MD_TILE) k_refresh_pos4(DevArgs a)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s == 0) { a.st->pos4_ok = 1; a.st->inner_ok = 0; a.st->inner_ok_next = 0; }
-    if (s >= a.S) return;
-    const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
-    if (s - R.slot_off >= R.n_atoms) return;
-    a.pos4[s] = rel_pos(a, R, s);
+    const int s = blockIdx.x * MD_TILE + threadIdx.x;
+    if (s == 0) { a.st->pos4_ok = 1; a.st->inner_ok = a.st->inner_ok_next; }
+    const RepDev &R = a.rep[a.tile_rep[blockIdx.x]];
+    unsigned ibits = 0u;
+    if (s - R.slot_off < R.n_atoms) {
+        const float4 p = rel_pos(a, R, s);
+        a.pos4[s] = p;
+        if (a.mixed) {
+            const float4 q = a.pin[s];
+            const float ex = p.x - q.x, ey = p.y - q.y, ez = p.z - q.z;
+            float dm2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            if (!(dm2 <= 1e30f)) dm2 = 1e30f;
+            ibits = __float_as_uint(dm2);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) ibits = max(ibits, __shfl_xor_sync(0xffffffffu, ibits, o));
+    if ((threadIdx.x & 31) == 0 && ibits) atomicMax(&a.st->imax_bits, ibits);
 }
 
 // ============================================================================ Task 4, mixed precision
@@ -1591,7 +1605,7 @@ cudaError_t launch_state_check(const DevArgs &a, cudaStream_t s)
 
 cudaError_t launch_refresh_pos4(const DevArgs &a, cudaStream_t s)
 {
-    k_refresh_pos4<<<nblk(a.S, 256), 256, 0, s>>>(a);
+    k_refresh_pos4<<<a.S / MD_TILE, MD_TILE, 0, s>>>(a);
     return cudaGetLastError();
 }
 
