@@ -161,6 +161,12 @@ def algorithmic_bytes(kernel: str, kmean: float, kin: float, kskin: float, preci
     return 4 * kmean + 121             # cnt + list + coordinates 24 + (F', M') 16 + F 24 + v 48 + fixed + cntc
 
 
+def verlet1_bytes(precision: str) -> int:
+    """k_verlet1 per atom: x, v, F in (72), x, v out (48), cell 4, fixed 1; mixed adds the
+    positions at the two list builds in (32) and pos4 out (16), FP64 reads x_build (24)."""
+    return 125 + (48 if precision == "mixed" else 24)
+
+
 def inner_mean(sim, rep, radii, sample: int = 20000, seed: int = 0):
     """Mean number of Verlet-list entries within each radius at the current positions,
     from a random sample of atoms of replica 0."""
@@ -256,6 +262,13 @@ def run_gpu(args):
     bytes_per_launch = algorithmic_bytes(dom, kmean, kin, kskin, args.precision) * n_cr
     achieved = bytes_per_launch / (phases[dom] * 1e-3) / 1e9
     traffic = dram_traffic(args.workload, args.precision, dom)
+    # the whole step: every per-step kernel's algorithmic bytes (rebuilds excluded) over the
+    # measured time per step
+    step_bytes = (algorithmic_bytes("density", kmean, kin, kskin, args.precision)
+                  + algorithmic_bytes("force", kmean, kin, kskin, args.precision) + verlet1_bytes(args.precision)) * n_cr
+    step_gbs = step_bytes / (t_max / args.steps * 1e-3) / 1e9
+    step_roofline = {"bytes_per_atom": step_bytes / n_cr, "achieved": step_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": step_gbs / peak, "kernels": "k_verlet1 + k_density + k_force (rebuilds excluded)"}
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timing
     e2e = None
@@ -342,6 +355,8 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": int((5 if args.precision == "mixed" else 4) * args.steps + 14 * rebuilds + 1),
+        "value_incl_c": (n_cr + n_c) * ws * args.steps / (t_max * 1e-3),
+        "step_roofline": step_roofline,
         "variants": variants,
     }
     if cpu is not None:
