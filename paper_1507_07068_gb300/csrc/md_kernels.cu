@@ -1059,6 +1059,10 @@ __device__ __forceinline__ PairGeom pair_geom(const RepDev &R, int ci)
     return G;
 }
 
+// PER = false: no atom of the warp sits in an edge cell of a periodic axis, so no pair
+// crosses a periodic face and the correction is left out (the caller decides per warp, so
+// the branch between the two forms is uniform)
+template <bool PER>
 __device__ __forceinline__ void disp(const float4 &pi, const float4 &pj, unsigned dir, const float4 *sm_off,
                                      const PairGeom &G, float &dx, float &dy, float &dz)
 {
@@ -1066,31 +1070,37 @@ __device__ __forceinline__ void disp(const float4 &pi, const float4 &pj, unsigne
     dx = (pj.x - pi.x) + o.x;
     dy = (pj.y - pi.y) + o.y;
     dz = (pj.z - pi.z) + o.z;
-    const unsigned c = dir & G.xmask;
-    if (c) {   // through a periodic face: the period is nc w32 + dL
-        dx += (c & 1 ? -G.dL0 : 0.f) + (c & 2 ? G.dL0 : 0.f);
-        dy += (c & 4 ? -G.dL1 : 0.f) + (c & 8 ? G.dL1 : 0.f);
-        dz += (c & 16 ? -G.dL2 : 0.f) + (c & 32 ? G.dL2 : 0.f);
+    if (PER) {
+        const unsigned c = dir & G.xmask;
+        if (c) {   // through a periodic face: the period is nc w32 + dL
+            dx += (c & 1 ? -G.dL0 : 0.f) + (c & 2 ? G.dL0 : 0.f);
+            dy += (c & 4 ? -G.dL1 : 0.f) + (c & 8 ? G.dL1 : 0.f);
+            dz += (c & 16 ? -G.dL2 : 0.f) + (c & 32 ? G.dL2 : 0.f);
+        }
     }
 }
+
+template <bool B> struct BoolC { static constexpr bool value = B; };
 
 // The pair loops of the mixed path evaluate the forms of Eqs. A2 and A4 directly in FP32
 // (no table gather: at FP32 resolution a Hermite table adds nothing but 32 bytes of memory
 // traffic per pair; its deviation from the forms is below 1e-11).  f: for an even integer
 // beta the power is (r_e^2/r^2)^(beta/2) by multiplication; Phi: Taylor form about the
 // double root, with t = r/r_e - d formed with the rounding of 1/r_e and d compensated.
-// r_e^2 / r^2 from one reciprocal refined by a Newton step (about 1 ulp, no IEEE divide)
+// r_e^2 / r^2 from one reciprocal refined by a Newton step (about 1 ulp, no IEEE divide).
+// IPOW > 0: beta = 2 IPOW known at compile time; IPOW = 0: from Q.ipow (or exp2/log2).
+template <int IPOW>
 __device__ __forceinline__ float f_direct(const Pot32 &Q, float r2, float r)
 {
-    if (Q.ipow > 0) {
+    if (IPOW > 0 || Q.ipow > 0) {
         const float rcp = __fdividef(1.0f, r2);
         float q = Q.re2 * rcp;
         q = fmaf(rcp, fmaf(-q, r2, Q.re2), q);
-        float fr;
-        if (Q.ipow == 3) {
-            fr = q * q * q;
+        float fr = q;
+        if (IPOW > 0) {
+#pragma unroll
+            for (int k = 1; k < IPOW; ++k) fr *= q;
         } else {
-            fr = q;
             for (int k = 1; k < Q.ipow; ++k) fr *= q;
         }
         return fr * Q.f_e;
@@ -1105,20 +1115,23 @@ __device__ __forceinline__ float rsqrt_nr(float r2)
     return y * fmaf(-0.5f * r2 * y, y, 1.5f);
 }
 
+template <int IPOW>
 __device__ __forceinline__ float fa_val(const Pot32 &Q, float r2)
 {
     const float r = r2 * rsqrt_nr(r2);
-    return f_direct(Q, r2, r) - Q.f_rc - (r - Q.rc) * Q.df_rc;
+    return f_direct<IPOW>(Q, r2, r) - Q.f_rc - (r - Q.rc) * Q.df_rc;
 }
 
+// Phi beyond its double root (t > 0) is zero with its slope; t is clamped to 0 there,
+// where the Taylor form gives exactly 0 for both
+template <int IPOW>
 __device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, float &f, float &df, float &ph, float &dph)
 {
     const float r = r2 * rinv;
-    const float fr = f_direct(Q, r2, r);
+    const float fr = f_direct<IPOW>(Q, r2, r);
     f = fr - Q.f_rc - (r - Q.rc) * Q.df_rc;
     df = -Q.beta * fr * rinv - Q.df_rc;
-    const float t = fmaf(r, Q.inv_re, -Q.d) + fmaf(r, Q.inv_re_lo, -Q.d_lo);
-    if (t > 0.0f) { ph = dph = 0.0f; return; }
+    const float t = fminf(fmaf(r, Q.inv_re, -Q.d) + fmaf(r, Q.inv_re_lo, -Q.d_lo), 0.0f);
     ph = t * t * fmaf(fmaf(fmaf(Q.b3, t, Q.b2), t, Q.b1), t, Q.b0);
     dph = t * fmaf(fmaf(fmaf(5.0f * Q.b3, t, 4.0f * Q.b2), t, 3.0f * Q.b1), t, 2.0f * Q.b0) * Q.inv_re;
 }
@@ -1139,7 +1152,7 @@ __device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, flo
 //    (a pair crossed rc since the last step); otherwise it is written as the loop goes.
 // The launch bound caps the kernel at 51 registers (48 used, no spills): with both loops in
 // one kernel the compiler otherwise takes 60-64 and the loss of occupancy costs ~10 %.
-template <int TPA>
+template <int TPA, int IPOW>
 __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
 {
     __shared__ float4 sm_off[64];
@@ -1156,9 +1169,12 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
     const bool rebuild = !a.st->inner_ok || !(__uint_as_float(a.st->imax_bits) <= a.ithr2);
     float rho = 0.f, Ps = 0.f;
     int m = 0, mr = 0;   // inner-list and rc-list entries of this lane
-    if (real) {
-        const float4 pi = a.pos4[s];
-        const PairGeom G = pair_geom(R, __float_as_int(pi.w));
+    const float4 pi = a.pos4[s];
+    const PairGeom G = pair_geom(R, __float_as_int(pi.w));
+    const bool per = __any_sync(0xffffffffu, real && G.xmask != 0u);
+    auto work = [&](auto PERC) {
+        constexpr bool PER = decltype(PERC)::value;
+        if (!real) return;
         unsigned long long mask = 0ull;   // inner rows within rc (one thread per atom)
         if (rebuild) {
             const int n = a.cnt[s];
@@ -1175,13 +1191,13 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
 #pragma unroll
                 for (int u = 0; u < MD_UNROLL; ++u) {
                     float dx, dy, dz;
-                    disp(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
+                    disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     if (k0 + u * TPA < n && r2 < a.rin2) {
                         // lane-interleaved rows: each lane owns rows lane, lane + TPA, ...
                         a.inner[(size_t)(m * TPA + lane) * S + s] = (int32_t)e[u];
                         if (r2 < Q.rc2) {
-                            const float f = fa_val(Q, r2);
+                            const float f = fa_val<IPOW>(Q, r2);
                             rho += f;
                             Ps = fmaf(f, f, Ps);
                             a.rcl[(size_t)(mr * TPA + lane) * S + s] = (int32_t)e[u];
@@ -1210,11 +1226,11 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
 #pragma unroll
                 for (int u = 0; u < MD_UNROLL; ++u) {
                     float dx, dy, dz;
-                    disp(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
+                    disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     // padding entries (the atom itself) and entries now beyond rc drop out
                     const bool in = (e[u] & MD_J_MASK) != (unsigned)s && r2 < Q.rc2;
-                    float f = fa_val(Q, in ? r2 : Q.re2);
+                    float f = fa_val<IPOW>(Q, in ? r2 : Q.re2);
                     f = in ? f : 0.0f;
                     rho += f;
                     Ps = fmaf(f, f, Ps);
@@ -1240,7 +1256,8 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
                 mr = -1;   // rcnt kept (or just written)
             }
         }
-    }
+    };
+    if (per) work(BoolC<true>{}); else work(BoolC<false>{});
     int mmax = m, mrmax = mr;
 #pragma unroll
     for (int o = TPA / 2; o > 0; o >>= 1) {
@@ -1275,7 +1292,7 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
 // Task 4b,c (Eq. (1) with the M term, Eqs. A6-A10; Morse Eqs. A5, A9) and Task 5 (the
 // closing half kick, FP64).  The force on i from j is coef * (x_j - x_i), coef = [(F'_i +
 // F'_j) f' + (M'_i + M'_j) 2 f f' + Phi'] / r.
-template <int TPA>
+template <int TPA, int IPOW>
 __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int integrate)
 {
     __shared__ float4 sm_off[64];
@@ -1291,9 +1308,12 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
     const size_t S = a.S;
     float gx = 0.f, gy = 0.f, gz = 0.f, ep = 0.f;
     float mx = 0.f, my = 0.f, mz = 0.f, em = 0.f;
-    if (real) {
-        const float4 pi = a.pos4[s];
-        const PairGeom G = pair_geom(R, __float_as_int(pi.w));
+    const float4 pi = a.pos4[s];
+    const PairGeom G = pair_geom(R, __float_as_int(pi.w));
+    const bool per = __any_sync(0xffffffffu, real && G.xmask != 0u);
+    auto work = [&](auto PERC) {
+        constexpr bool PER = decltype(PERC)::value;
+        if (!real) return;
         const float2 fmi = a.fm32[s];
         const int n = a.rcnt[s];
         for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
@@ -1314,12 +1334,12 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
 #pragma unroll
             for (int u = 0; u < MD_UNROLL; ++u) {
                 float dx, dy, dz;
-                disp(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
+                disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 if ((e[u] & MD_J_MASK) != (unsigned)s) {   // rc-list entries are within rc; padding is the atom itself
                     const float rinv = rsqrt_nr(r2);
                     float f, df, ph, dph;
-                    fa_phi(Q, r2, rinv, f, df, ph, dph);
+                    fa_phi<IPOW>(Q, r2, rinv, f, df, ph, dph);
                     const float coef = fmaf(fmi.x + fmj[u].x, df, fmaf((fmi.y + fmj[u].y) * 2.0f * f, df, dph)) * rinv;
                     gx = fmaf(coef, dx, gx);
                     gy = fmaf(coef, dy, gy);
@@ -1328,11 +1348,12 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
                 }
             }
         }
-        // Cr-C (Morse): summed by k_morse_mixed for the atoms with Cr-C neighbours
-        if (lane == 0 && a.cntc[s] > 0) {
-            const float4 fmo = a.fmorse[s];
-            mx = fmo.x; my = fmo.y; mz = fmo.z; em = fmo.w;
-        }
+    };
+    if (per) work(BoolC<true>{}); else work(BoolC<false>{});
+    // Cr-C (Morse): summed by k_morse_mixed for the atoms with Cr-C neighbours
+    if (real && lane == 0 && a.cntc[s] > 0) {
+        const float4 fmo = a.fmorse[s];
+        mx = fmo.x; my = fmo.y; mz = fmo.z; em = fmo.w;
     }
 #pragma unroll
     for (int o = TPA / 2; o > 0; o >>= 1) {
@@ -1613,16 +1634,26 @@ template <int TPA>
 static void dens_t(const DevArgs &a, const PotDev &p, int block, cudaStream_t s)
 {
     int A = block / TPA;
-    if (a.mixed) k_density_mixed<TPA><<<a.S / A, block, 0, s>>>(a, p);
-    else k_density_fp64<TPA><<<a.S / A, block, 0, s>>>(a, p);
+    if (a.mixed) {
+        if (p.q.ipow == 3) k_density_mixed<TPA, 3><<<a.S / A, block, 0, s>>>(a, p);   // beta = 6
+        else k_density_mixed<TPA, 0><<<a.S / A, block, 0, s>>>(a, p);
+    }
+    else {
+        k_density_fp64<TPA><<<a.S / A, block, 0, s>>>(a, p);
+    }
 }
 
 template <int TPA>
 static void force_t(const DevArgs &a, const PotDev &p, int block, int integ, cudaStream_t s)
 {
     int A = block / TPA;
-    if (a.mixed) k_force_mixed<TPA><<<a.S / A, block, 0, s>>>(a, p, integ);
-    else k_force_fp64<TPA><<<a.S / A, block, 0, s>>>(a, p, integ);
+    if (a.mixed) {
+        if (p.q.ipow == 3) k_force_mixed<TPA, 3><<<a.S / A, block, 0, s>>>(a, p, integ);
+        else k_force_mixed<TPA, 0><<<a.S / A, block, 0, s>>>(a, p, integ);
+    }
+    else {
+        k_force_fp64<TPA><<<a.S / A, block, 0, s>>>(a, p, integ);
+    }
 }
 
 cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c, cudaStream_t s)
