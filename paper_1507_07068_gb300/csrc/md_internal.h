@@ -47,6 +47,7 @@ struct alignas(32) Cf64 {
 struct PotF32 {
     float rmin_s_f, inv_hf, rmin_s_m, inv_hm, lf0, beta, f_rc, df_rc, rc;
     float inv_re, d, b0, b1, b2, b3;
+    float c0, c1, c2, c3;   // (k + 2) b_k / r_e: dPhi/dr = t (c0 + c1 t + c2 t^2 + c3 t^3)
     float D_o, half_ax, inv_yeq, m_rc, dm_rc, rc_m;
     float F_o, n, inv_rho_e, alpha, inv_P_e, rc2;
     int32_t tabulated, nf, nm;

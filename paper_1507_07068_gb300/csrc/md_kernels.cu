@@ -172,6 +172,8 @@ int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs
     q.lf0 = (float)P->lf0; q.beta = (float)P->beta; q.f_rc = (float)P->f_rc; q.df_rc = (float)P->df_rc;
     q.rc = (float)P->rc; q.inv_re = (float)(1.0 / P->r_e); q.d = (float)P->d;
     q.b0 = (float)P->b[0]; q.b1 = (float)P->b[1]; q.b2 = (float)P->b[2]; q.b3 = (float)P->b[3];
+    q.c0 = (float)(2.0 * P->b[0] / P->r_e); q.c1 = (float)(3.0 * P->b[1] / P->r_e);
+    q.c2 = (float)(4.0 * P->b[2] / P->r_e); q.c3 = (float)(5.0 * P->b[3] / P->r_e);
     q.D_o = (float)P->D_o; q.half_ax = (float)P->half_ax; q.inv_yeq = (float)P->inv_yeq;
     q.m_rc = (float)P->m_rc; q.dm_rc = (float)P->dm_rc; q.rc_m = (float)P->rc_m;
     q.F_o = (float)P->F_o; q.n = (float)P->n; q.inv_rho_e = (float)(1.0 / P->rho_e); q.alpha = (float)P->alpha;
@@ -1133,7 +1135,7 @@ __device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, flo
     df = -Q.beta * fr * rinv - Q.df_rc;
     const float t = fminf(fmaf(r, Q.inv_re, -Q.d) + fmaf(r, Q.inv_re_lo, -Q.d_lo), 0.0f);
     ph = t * t * fmaf(fmaf(fmaf(Q.b3, t, Q.b2), t, Q.b1), t, Q.b0);
-    dph = t * fmaf(fmaf(fmaf(5.0f * Q.b3, t, 4.0f * Q.b2), t, 3.0f * Q.b1), t, 2.0f * Q.b0) * Q.inv_re;
+    dph = t * fmaf(fmaf(fmaf(Q.c3, t, Q.c2), t, Q.c1), t, Q.c0);
 }
 
 // Task 4a (Eqs. A2-A3): rho_i, P_i over the pairs within rc; F'(rho_i), M'(P_i) stored,

@@ -164,6 +164,18 @@ def test_forces_mixed(md, params, tab):
     sim.close()
 
 
+@pytest.mark.parametrize("beta", [5.5, 8.0])
+def test_forces_mixed_other_exponents(md, params, beta):
+    """beta other than 6: the pair loops' generic form of f (exp2/log2 for a non-even beta,
+    the runtime integer power for an even one) against the oracle."""
+    rep = tiny(amp=0.12, gap=1.0)
+    sim = md.MD([rep], params, precision="mixed", beta=beta, tabulated=0)
+    o = oracle_eval(params, rep, beta=beta, tabulated=0)
+    assert rel_force_err(sim.forces(0), o["F"]).max() <= MIXED_TOL
+    energy_close(sim.energy(0), o, 1e-5, 1e-4)
+    sim.close()
+
+
 @pytest.mark.parametrize("tpa,block", [(1, 128), (2, 256), (4, 128), (8, 256), (8, 64)])
 def test_launch_shapes_agree(md, params, tpa, block):
     rep = tiny(amp=0.1)
