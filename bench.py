@@ -326,7 +326,7 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.workload, params, args.cpu_seconds)
+        cpu = cpu_baseline(args.workload, params, args.cpu_seconds, args.skin)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -391,16 +391,16 @@ def oracle_sample_replica(workload: str, target_atoms: int):
     return rep, f"{nx}x{ny}x{nz_s}-cell slab of the {workload} film ({rep.n_cr} Cr), same indenter"
 
 
-def oracle_rate(params, rep, steps: int):
+def oracle_rate(params, rep, steps: int, skin: float = 0.3):
     import oracle
     pot = oracle.Potential(params)
-    sim = oracle.Sim(pot, rep, skin=0.3)
+    sim = oracle.Sim(pot, rep, skin=skin)
     t0 = time.perf_counter()
     sim.step(steps)
     return rep.n_cr * steps / (time.perf_counter() - t0)
 
 
-def cpu_baseline(workload: str, params, seconds: float):
+def cpu_baseline(workload: str, params, seconds: float, skin: float = 0.3):
     import oracle
     cores = oracle.set_threads(os.cpu_count() or 1)
     probe = mi.make_replica("probe", 24, 24, 10, 6.0, 300.0, seed=3)
@@ -408,7 +408,7 @@ def cpu_baseline(workload: str, params, seconds: float):
     target = int(rate * seconds / 6)
     rep, desc = oracle_sample_replica(workload, max(target, 20000))
     n = max(2, min(6, int(rate * seconds / max(rep.n_cr, 1))))
-    v = oracle_rate(params, rep, n)
+    v = oracle_rate(params, rep, n, skin)
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} FP64 oracle time steps (list build excluded) on {desc}, OpenMP over {cores} threads"}
 
@@ -428,7 +428,7 @@ def run_reference(args):
     per_step = budget / max(args.steps + args.warmup, 1)
     rep, desc = oracle_sample_replica(args.workload, max(int(rate * per_step), 5000))
     pot = oracle.Potential(params)
-    sim = oracle.Sim(pot, rep, skin=0.3)
+    sim = oracle.Sim(pot, rep, skin=args.skin, rebuild_every=args.rebuild_every)
     sim.step(args.warmup)
     t0 = time.perf_counter()
     sim.step(args.steps)
@@ -436,9 +436,10 @@ def run_reference(args):
     value = rep.n_cr * args.steps / dt
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded BCC film + diamond hemisphere, Maxwell-Boltzmann velocities)",
            "config": {"workload": WORKLOAD_TEXT[args.workload], "precision": "fp64 (oracle)",
-                      "sample": desc},
+                      "skin_A": args.skin, "n_cr": rep.n_cr, "sample": desc},
            "impl": "reference",
            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
                             "sample": f"each step one FP64 oracle time step on {desc}"},
