@@ -51,6 +51,8 @@ __global__ void k_set_scalars(RepState *rs, int r, double z_ind, DevStatus *st, 
 struct md_handle {
     cudaStream_t stream = nullptr;       // caller's stream
     cudaStream_t cap = nullptr;          // private stream used only for graph capture
+    cudaStream_t cap2 = nullptr;         // second capture stream: k_morse_mixed beside k_density
+    cudaEvent_t fork = nullptr, join = nullptr;
     md_options opt{};
     md_params pot_h{};
     PotDev pot{};
@@ -224,8 +226,18 @@ int capture(md_t *h, int nsteps, cudaGraphExec_t *out)
         CU(cudaStreamEndCapture(h->cap, &body));
         CU(cudaStreamBeginCaptureToGraph(h->cap, g, &cn, nullptr, 1, mode));
         CU(launch_verlet1(h->a, h->cap));
-        CU(launch_density(h->a, h->pot, h->cfg, h->cap));
-        CU(launch_force(h->a, h->pot, h->cfg, 1, h->cap));
+        if (h->a.mixed) {   // the Morse sums need only this step's positions: beside k_density
+            CU(cudaEventRecord(h->fork, h->cap));
+            CU(cudaStreamWaitEvent(h->cap2, h->fork, 0));
+            CU(launch_morse(h->a, h->pot, h->cap2));
+            CU(cudaEventRecord(h->join, h->cap2));
+            CU(launch_density(h->a, h->pot, h->cfg, h->cap));
+            CU(cudaStreamWaitEvent(h->cap, h->join, 0));
+            CU(launch_force_split(h->a, h->pot, h->cfg, 1, 0, h->cap));
+        } else {
+            CU(launch_density(h->a, h->pot, h->cfg, h->cap));
+            CU(launch_force(h->a, h->pot, h->cfg, 1, h->cap));
+        }
         CU(cudaStreamGetCaptureInfo(h->cap, &cs, nullptr, nullptr, &d, nullptr, &nd));
         deps.assign(d, d + nd);
         CU(cudaStreamEndCapture(h->cap, &g));
@@ -298,6 +310,9 @@ void md_free(md_t *h)
     if (h->tab64) cudaFree(h->tab64);
     if (h->tab32) cudaFree(h->tab32);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->cap2) cudaStreamDestroy(h->cap2);
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
     delete h;
 }
 
@@ -580,6 +595,9 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
         }
     }
     CUI(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    CUI(cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking));
+    CUI(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
+    CUI(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
     h->ev.resize(8);
     for (auto &e : h->ev) CUI(cudaEventCreate(&e));
     h->unroll = real < 200000 ? 8 : 1;

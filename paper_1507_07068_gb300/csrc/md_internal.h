@@ -204,6 +204,10 @@ cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s);
 cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s);
 cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, cudaStream_t s);
+// the Morse sums alone (mixed precision), and the force kernel with or without them first
+cudaError_t launch_morse(const DevArgs &a, const PotDev &p, cudaStream_t s);
+cudaError_t launch_force_split(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int with_morse,
+                               cudaStream_t s);
 cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_refresh_pos4(const DevArgs &a, cudaStream_t s);
 // d2max of every replica at the current positions and any_rebuild by the displacement rule

@@ -1669,9 +1669,21 @@ cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c
     return cudaGetLastError();
 }
 
-cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, cudaStream_t s)
+cudaError_t launch_morse(const DevArgs &a, const PotDev &p, cudaStream_t s)
 {
     if (a.mixed) k_morse_mixed<<<MD_NEAR_BLOCKS, 256, 0, s>>>(a, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, cudaStream_t s)
+{
+    return launch_force_split(a, p, c, integrate, 1, s);
+}
+
+cudaError_t launch_force_split(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int with_morse,
+                               cudaStream_t s)
+{
+    if (with_morse && a.mixed) k_morse_mixed<<<MD_NEAR_BLOCKS, 256, 0, s>>>(a, p);
     switch (c.tpa) {
     case 1: force_t<1>(a, p, c.block, integrate, s); break;
     case 2: force_t<2>(a, p, c.block, integrate, s); break;
