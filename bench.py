@@ -152,10 +152,10 @@ def algorithmic_bytes(kernel: str, kmean: float, kin: float, kskin: float, preci
     if precision == "mixed":
         if kernel == "density":
             # a step that keeps the inner list: icnt 4 + inner 4K_skin + float4 position 16 +
-            # (F', M') out 8 + row mask 8 (the list rebuilds, every few steps, are extra)
-            return 4 * kskin + 36
-        # rcnt 4 + rc list 4K_in + position 16 + (F', M') 8 + F out 24 + v in/out 48 + fixed 1 + cntc 4
-        return 4 * kin + 105
+            # (F', M') out 8 (the list rebuilds, every few steps, are extra)
+            return 4 * kskin + 28
+        # icnt 4 + inner list 4K_skin + position 16 + (F', M') 8 + F out 24 + v in/out 48 + fixed 1 + cntc 4
+        return 4 * kskin + 105
     if kernel == "density":
         return 4 * kmean + 44          # cnt + list + 3 FP64 coordinates 24 + (F', M') out 16
     return 4 * kmean + 121             # cnt + list + coordinates 24 + (F', M') 16 + F 24 + v 48 + fixed + cntc

@@ -168,8 +168,6 @@ int rebuild_growing(md_t *h)
             if (h->a.mixed) {
                 if ((rc = dalloc(h, &p, (size_t)k * h->a.S))) return rc;
                 h->a.inner = p;
-                if ((rc = dalloc(h, &p, (size_t)k * h->a.S))) return rc;
-                h->a.rcl = p;
             }
             h->a.kmax = k; grow = true;
         }
@@ -484,9 +482,6 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     INIT_FAIL(dalloc(h, &a.cnt, S));
     INIT_FAIL(dalloc(h, &a.inner, a.mixed ? (size_t)a.kmax * S : 1));
     INIT_FAIL(dalloc(h, &a.icnt, S));
-    INIT_FAIL(dalloc(h, &a.rcl, a.mixed ? (size_t)a.kmax * S : 1));
-    INIT_FAIL(dalloc(h, &a.rcnt, S));
-    INIT_FAIL(dalloc(h, &a.rmask, S));
     INIT_FAIL(dalloc(h, &a.nbrc, (size_t)a.kcmax * S));
     INIT_FAIL(dalloc(h, &a.cntc, S));
     INIT_FAIL(dalloc(h, &a.cand, S));

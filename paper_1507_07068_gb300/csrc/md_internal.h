@@ -167,8 +167,6 @@ struct DevArgs {
                                  // within rc + MD_INNER_SKIN when it was last rebuilt
     float4 *pin;                 // mixed: pos4 of each atom when the inner list was rebuilt
     float4 *pb;                  // mixed: pos4 of each atom when the Verlet list was rebuilt
-    int32_t *rcl, *rcnt;         // mixed: the entries of the inner list within rc (k_force's list)
-    unsigned long long *rmask;   // mixed, one thread per atom: which inner rows rcl holds
     float rin2, ithr2;           // (rc + MD_INNER_SKIN)^2; max |p - p_in|^2 before a rebuild
     int32_t *cellc, *orig;
     uint8_t *fixed;

@@ -1142,18 +1142,14 @@ __device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, flo
 // F(rho_i), M(P_i) into the CTA's energy partials.  MD_UNROLL entries per lane are loaded
 // (list entry, then position) before any is used.
 //
-// Lists (all in Verlet-list order, so every loop takes the pairs within rc in the same
-// order and the sums do not depend on which list a step uses):
-//  - the inner list (Sec. 2.6): the Verlet-list entries within rc + inner skin at its last
-//    rebuild.  Every pair within rc is in it while no atom has moved more than half the
-//    skin since (k_verlet1 reduces the displacement); then it is rebuilt from the Verlet
-//    list.  With inner skin < 0 it is rebuilt every step with radius rc, as in the paper.
-//  - the rc list: the inner-list entries within rc now, which k_force loops over without a
-//    distance test.  With one thread per atom and at most 64 inner entries, a 64-bit mask
-//    of those rows is kept and the rc list is rewritten only for atoms whose mask changed
-//    (a pair crossed rc since the last step); otherwise it is written as the loop goes.
-// The launch bound caps the kernel at 51 registers (48 used, no spills): with both loops in
-// one kernel the compiler otherwise takes 60-64 and the loss of occupancy costs ~10 %.
+// The inner list (Sec. 2.6) holds the Verlet-list entries within rc + inner skin at its
+// last rebuild, in Verlet-list order.  Every pair within rc is in it while no atom has
+// moved more than half the skin since (k_verlet1 reduces the displacement); then this
+// kernel rebuilds it from the Verlet list.  With inner skin < 0 it is rebuilt every step
+// with radius rc, as in the paper.  Both loops take the pairs within rc in Verlet-list
+// order, so the sums do not depend on which list a step uses.
+// The launch bound caps the kernel at 51 registers: with both loops in one kernel the
+// compiler otherwise takes 60-64 and the loss of occupancy costs ~10 %.
 template <int TPA, int IPOW>
 __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
 {
@@ -1170,14 +1166,13 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
     // uniform over the launch: nothing below writes inner_ok or imax_bits
     const bool rebuild = !a.st->inner_ok || !(__uint_as_float(a.st->imax_bits) <= a.ithr2);
     float rho = 0.f, Ps = 0.f;
-    int m = 0, mr = 0;   // inner-list and rc-list entries of this lane
+    int m = 0;   // inner-list entries of this lane
     const float4 pi = a.pos4[s];
     const PairGeom G = pair_geom(R, __float_as_int(pi.w));
     const bool per = __any_sync(0xffffffffu, real && G.xmask != 0u);
     auto work = [&](auto PERC) {
         constexpr bool PER = decltype(PERC)::value;
         if (!real) return;
-        unsigned long long mask = 0ull;   // inner rows within rc (one thread per atom)
         if (rebuild) {
             const int n = a.cnt[s];
             for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
@@ -1202,21 +1197,16 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
                             const float f = fa_val<IPOW>(Q, r2);
                             rho += f;
                             Ps = fmaf(f, f, Ps);
-                            a.rcl[(size_t)(mr * TPA + lane) * S + s] = (int32_t)e[u];
-                            ++mr;
-                            if (m < 64) mask |= 1ull << m;
                         }
                         ++m;
                     }
                 }
             }
             if (lane == 0) a.pin[s] = pi;
-            if (TPA == 1) a.rmask[s] = mask;
         } else {
             const int n = a.icnt[s];
-            const bool direct = TPA > 1 || n > 64;   // no mask: the rc list is written as we go
             for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
-                unsigned e[MD_UNROLL], nib = 0u;
+                unsigned e[MD_UNROLL];
 #pragma unroll
                 for (int u = 0; u < MD_UNROLL; ++u) {
                     const int k = k0 + u * TPA;
@@ -1236,48 +1226,22 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
                     f = in ? f : 0.0f;
                     rho += f;
                     Ps = fmaf(f, f, Ps);
-                    nib |= (in ? 1u : 0u) << u;
-                    if (direct && in) {
-                        a.rcl[(size_t)(mr * TPA + lane) * S + s] = (int32_t)e[u];
-                        ++mr;
-                    }
                 }
-                if (!direct) mask |= (unsigned long long)nib << k0;
-            }
-            if (!direct) {
-                const unsigned long long old = a.rmask[s];
-                if (mask != old) {   // a pair crossed rc: rewrite this atom's rc list
-                    for (unsigned long long b = mask; b; b &= b - 1) {
-                        const int k = __ffsll((long long)b) - 1;
-                        a.rcl[(size_t)mr * S + s] = a.inner[(size_t)k * S + s];
-                        ++mr;
-                    }
-                    a.rmask[s] = mask;
-                    a.rcnt[s] = mr;
-                }
-                mr = -1;   // rcnt kept (or just written)
             }
         }
     };
     if (per) work(BoolC<true>{}); else work(BoolC<false>{});
-    int mmax = m, mrmax = mr;
+    int mmax = m;
 #pragma unroll
     for (int o = TPA / 2; o > 0; o >>= 1) {
         rho += __shfl_xor_sync(0xffffffffu, rho, o);
         Ps += __shfl_xor_sync(0xffffffffu, Ps, o);
         mmax = max(mmax, __shfl_xor_sync(0xffffffffu, mmax, o));
-        mrmax = max(mrmax, __shfl_xor_sync(0xffffffffu, mrmax, o));
     }
-    if (real) {
+    if (real && rebuild) {
         // rows of lanes with fewer entries are padded with the atom itself (skipped)
-        if (rebuild) {
-            for (int k = m; k < mmax; ++k) a.inner[(size_t)(k * TPA + lane) * S + s] = s;
-            if (lane == 0) a.icnt[s] = mmax * TPA;
-        }
-        if (mr >= 0) {
-            for (int k = mr; k < mrmax; ++k) a.rcl[(size_t)(k * TPA + lane) * S + s] = s;
-            if (lane == 0) a.rcnt[s] = mrmax * TPA;
-        }
+        for (int k = m; k < mmax; ++k) a.inner[(size_t)(k * TPA + lane) * S + s] = s;
+        if (lane == 0) a.icnt[s] = mmax * TPA;
     }
     if (rebuild && blockIdx.x == 0 && threadIdx.x == 0) a.st->inner_ok_next = 1;   // read by the next k_decide
     float acc[2] = {0.f, 0.f};
@@ -1293,7 +1257,8 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
 
 // Task 4b,c (Eq. (1) with the M term, Eqs. A6-A10; Morse Eqs. A5, A9) and Task 5 (the
 // closing half kick, FP64).  The force on i from j is coef * (x_j - x_i), coef = [(F'_i +
-// F'_j) f' + (M'_i + M'_j) 2 f f' + Phi'] / r.
+// F'_j) f' + (M'_i + M'_j) 2 f f' + Phi'] / r, over the inner list; its entries beyond rc
+// (~3 %) get weight 0 by a select (a branch on the distance measured 10 % slower).
 template <int TPA, int IPOW>
 __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int integrate)
 {
@@ -1317,13 +1282,13 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
         constexpr bool PER = decltype(PERC)::value;
         if (!real) return;
         const float2 fmi = a.fm32[s];
-        const int n = a.rcnt[s];
+        const int n = a.icnt[s];
         for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
             unsigned e[MD_UNROLL];
 #pragma unroll
             for (int u = 0; u < MD_UNROLL; ++u) {
                 const int k = k0 + u * TPA;
-                e[u] = k < n ? (unsigned)__ldg(&a.rcl[(size_t)k * S + s]) : (unsigned)s;
+                e[u] = k < n ? (unsigned)__ldg(&a.inner[(size_t)k * S + s]) : (unsigned)s;
             }
             float4 pj[MD_UNROLL];
             float2 fmj[MD_UNROLL];
@@ -1338,15 +1303,19 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
                 float dx, dy, dz;
                 disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if ((e[u] & MD_J_MASK) != (unsigned)s) {   // rc-list entries are within rc; padding is the atom itself
+                if ((e[u] & MD_J_MASK) != (unsigned)s) {   // padding is the atom itself
+                    // inner-list entries beyond rc (at most rc + inner skin) get weight 0:
+                    // their terms are finite and drop out exactly
+                    const float w = r2 < Q.rc2 ? 0.5f : 0.0f;
                     const float rinv = rsqrt_nr(r2);
                     float f, df, ph, dph;
                     fa_phi<IPOW>(Q, r2, rinv, f, df, ph, dph);
                     const float coef = fmaf(fmi.x + fmj[u].x, df, fmaf((fmi.y + fmj[u].y) * 2.0f * f, df, dph)) * rinv;
-                    gx = fmaf(coef, dx, gx);
-                    gy = fmaf(coef, dy, gy);
-                    gz = fmaf(coef, dz, gz);
-                    ep = fmaf(0.5f, ph, ep);
+                    const float cw = coef * (w + w);
+                    gx = fmaf(cw, dx, gx);
+                    gy = fmaf(cw, dy, gy);
+                    gz = fmaf(cw, dz, gz);
+                    ep = fmaf(w, ph, ep);
                 }
             }
         }
