@@ -302,24 +302,24 @@ def run_gpu(args):
     variants = {}
     if not args.no_variants and rank == 0:
         if args.precision != "fp64":
-            s64 = md.MD(reps, params, precision="fp64", skin=0.3)
+            s64 = md.MD(reps, params, precision="fp64", skin=0.3)   # the FP64 loops walk the Verlet list: a thin skin
             s64.step(3)
             torch.cuda.synchronize()
             a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
             k64 = max(5, min(args.steps, args.fp64_steps))
             a0.record(stream); s64.step(k64); a1.record(stream); torch.cuda.synchronize()
-            variants["fp64"] = {"value": n_cr * k64 / (a0.elapsed_time(a1) * 1e-3), "steps": k64,
+            variants["fp64"] = {"value": n_cr * k64 / (a0.elapsed_time(a1) * 1e-3), "steps": k64, "skin_A": 0.3,
                                 "ms_per_step": a0.elapsed_time(a1) / k64}
             s64.close()
         if args.workload != "batched":
             bw = mi.make_workload("batched")
-            sb = md.MD(bw.replicas, params, precision="mixed", skin=0.3)
+            sb = md.MD(bw.replicas, params, precision="mixed", skin=args.skin)
             sb.step(10)
             torch.cuda.synchronize()
             b0 = torch.cuda.Event(enable_timing=True); b1 = torch.cuda.Event(enable_timing=True)
             kb = max(10, min(args.steps, args.batched_steps))
             b0.record(stream); sb.step(kb); b1.record(stream); torch.cuda.synchronize()
-            variants["batched_mixed"] = {"value": bw.n_cr * kb / (b0.elapsed_time(b1) * 1e-3), "steps": kb,
+            variants["batched_mixed"] = {"value": bw.n_cr * kb / (b0.elapsed_time(b1) * 1e-3), "steps": kb, "skin_A": args.skin,
                                          "replicas": len(bw.replicas), "n_cr": bw.n_cr,
                                          "ms_per_step": b0.elapsed_time(b1) / kb}
             sb.close()
