@@ -154,16 +154,21 @@ def algorithmic_bytes(kernel: str, kmean: float, kin: float, kskin: float, preci
             # a step that keeps the inner list: icnt 4 + inner 4K_skin + float4 position 16 +
             # (F', M') out 8 (the list rebuilds, every few steps, are extra)
             return 4 * kskin + 28
-        # icnt 4 + inner list 4K_skin + position 16 + (F', M') 8 + F out 24 + v in/out 48 + fixed 1 + cntc 4
-        return 4 * kskin + 105
+        # icnt 4 + inner list 4K_skin + position 16 + (F', M') 8 + F out 24 + v(t+dt/2) in 24 +
+        # v out 24 + fixed 1 + cntc 4, and the next step's drift made in the epilogue: x in 24,
+        # x, v(t+3dt/2) out 48, cell-relative position out 16, the positions at the two list
+        # builds in 32, cell 4
+        return 4 * kskin + 229
     if kernel == "density":
         return 4 * kmean + 44          # cnt + list + 3 FP64 coordinates 24 + (F', M') out 16
     return 4 * kmean + 121             # cnt + list + coordinates 24 + (F', M') 16 + F 24 + v 48 + fixed + cntc
 
 
 def verlet1_bytes(precision: str) -> int:
-    """k_verlet1 per atom: x, v, F in (72), x, v out (48), cell 4, fixed 1; mixed adds the
-    positions at the two list builds in (32) and pos4 out (16), FP64 reads x_build (24)."""
+    """k_verlet1 per atom: x, v, F in (72), x, v(t+dt/2) out (48), cell 4, fixed 1; mixed adds
+    the positions at the two list builds in (32) and pos4 out (16), FP64 reads x_build (24).
+    In mixed precision it runs only on steps that rebuild the lists (the force epilogue makes
+    the drift otherwise)."""
     return 125 + (48 if precision == "mixed" else 24)
 
 
@@ -264,11 +269,16 @@ def run_gpu(args):
     traffic = dram_traffic(args.workload, args.precision, dom)
     # the whole step: every per-step kernel's algorithmic bytes (rebuilds excluded) over the
     # measured time per step
+    every_step_v1 = args.precision != "mixed"
     step_bytes = (algorithmic_bytes("density", kmean, kin, kskin, args.precision)
-                  + algorithmic_bytes("force", kmean, kin, kskin, args.precision) + verlet1_bytes(args.precision)) * n_cr
+                  + algorithmic_bytes("force", kmean, kin, kskin, args.precision)
+                  + (verlet1_bytes(args.precision) if every_step_v1 else 0)) * n_cr
     step_gbs = step_bytes / (t_max / args.steps * 1e-3) / 1e9
     step_roofline = {"bytes_per_atom": step_bytes / n_cr, "achieved": step_gbs, "peak": peak, "unit": "GB/s",
-                     "frac": step_gbs / peak, "kernels": "k_verlet1 + k_density + k_force (rebuilds excluded)"}
+                     "frac": step_gbs / peak,
+                     "kernels": ("k_verlet1 + k_density + k_force" if every_step_v1 else
+                                 "k_density + k_force (drift fused; k_verlet1 only on list-build steps)")
+                     + " (rebuilds excluded)"}
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timing
     e2e = None
@@ -354,7 +364,9 @@ def run_gpu(args):
         "phases_ms_per_step": phases,
         "clocks": clk.summary(),
         "e2e": e2e,
-        "gpu_launches": int((5 if args.precision == "mixed" else 4) * args.steps + 14 * rebuilds + 1),
+        # per step: k_decide, k_density, k_force, and k_morse_mixed (mixed) or k_verlet1 (FP64);
+        # per list build 14 kernels, and in mixed precision k_verlet1; one k_reduce
+        "gpu_launches": int(4 * args.steps + (15 if args.precision == "mixed" else 14) * rebuilds + 1),
         "value_incl_c": (n_cr + n_c) * ws * args.steps / (t_max * 1e-3),
         "step_roofline": step_roofline,
         "variants": variants,

@@ -18,21 +18,26 @@ namespace {
 
 thread_local std::string g_init_error;
 
-// device-side state transfer between the caller's AoS order and the slot order
-__global__ void k_state_in(const double *stage, double *dst, const int32_t *orig, int slot_off, int n, size_t S)
+// device-side state transfer between the caller's AoS order and the slot order; the
+// positions live in one of two buffers (d0, d1), chosen by the buffer counter st->ph
+__global__ void k_state_in(const double *stage, double *d0, double *d1, const DevStatus *st, const int32_t *orig,
+                           int slot_off, int n, size_t S)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    double *dst = (st->ph & 1) ? d1 : d0;
     int s = slot_off + i;
     int o = orig[s];
 #pragma unroll
     for (int k = 0; k < 3; ++k) dst[k * S + s] = stage[3 * (size_t)o + k];
 }
 
-__global__ void k_state_out(const double *src, double *stage, const int32_t *orig, int slot_off, int n, size_t S)
+__global__ void k_state_out(const double *s0, const double *s1, const DevStatus *st, double *stage,
+                            const int32_t *orig, int slot_off, int n, size_t S)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double *src = (st->ph & 1) ? s1 : s0;
     int s = slot_off + i;
     int o = orig[s];
 #pragma unroll
@@ -66,7 +71,12 @@ struct md_handle {
     float4 *tab32 = nullptr;
     double *stage = nullptr;              // 3 * max replica atoms doubles
     std::vector<void *> allocs;
-    cudaGraphExec_t exec1 = nullptr, execU = nullptr;
+    // step graphs: exec1 / execU one / `unroll` steps after a step (mixed: drift made), execE
+    // the same single step with the energies (the last step of an md_step call); execF /
+    // execFE mixed precision's single step that runs k_verlet1, without / with the energies
+    cudaGraphExec_t exec1 = nullptr, execU = nullptr, execE = nullptr;
+    cudaGraphExec_t execF = nullptr, execFE = nullptr;
+    bool drift = false;   // mixed: the last force kernel made the next step's Task 3 (mirrors drift_ok)
     int unroll = 1;
     bool forces_valid = false;
     std::vector<cudaEvent_t> ev;
@@ -126,6 +136,7 @@ int status_to_code(md_t *h, const DevStatus &st)
     if (st.err & MDE_OVERFLOW) return fail(h, MD_ERR_NBR_OVERFLOW, "Cr-Cr neighbour list overflow: %d > kmax %d", st.max_cnt, h->a.kmax);
     if (st.err & MDE_COVERFLOW) return fail(h, MD_ERR_NBR_OVERFLOW, "Cr-C neighbour list overflow: %d > kcmax %d", st.max_cntc, h->a.kcmax);
     if (st.err & MDE_SKIN) return fail(h, MD_ERR_SKIN_VIOLATION, "an atom moved more than skin/2 between fixed-interval rebuilds");
+    if (st.err & MDE_SCHED) return fail(h, MD_ERR_STATE, "internal: a step found no drift from the last force kernel");
     return MD_OK;
 }
 
@@ -137,15 +148,17 @@ int clear_err(md_t *h)
 
 int forces_now(md_t *h, cudaStream_t s)
 {
+    h->drift = false;   // the force kernel without Task 5 makes no drift
     CU(launch_density(h->a, h->pot, h->cfg, s));
-    CU(launch_force(h->a, h->pot, h->cfg, 0, s));
+    CU(launch_force(h->a, h->pot, h->cfg, 0, 1, s));
     CU(launch_reduce(h->a, h->cfg, s));
     return MD_OK;
 }
 
 int rebuild_now(md_t *h)
 {
-    CU(launch_decide(h->a, 1, 0, 0, h->stream));
+    h->drift = false;   // k_build_done voids a drift made before the build
+    CU(launch_decide(h->a, DEC_BUILD, 0, 0, h->stream));
     CU(launch_rebuild(h->a, h->stream));
     return MD_OK;
 }
@@ -186,23 +199,32 @@ void destroy_graphs(md_t *h)
 {
     if (h->exec1) cudaGraphExecDestroy(h->exec1);
     if (h->execU) cudaGraphExecDestroy(h->execU);
-    h->exec1 = h->execU = nullptr;
+    if (h->execE) cudaGraphExecDestroy(h->execE);
+    if (h->execF) cudaGraphExecDestroy(h->execF);
+    if (h->execFE) cudaGraphExecDestroy(h->execFE);
+    h->exec1 = h->execU = h->execE = h->execF = h->execFE = nullptr;
 }
 
-// One graph of `nsteps` whole time steps: per step k_decide -> IF(rebuild) ->
-// [k_verlet1 -> k_density -> k_force].  k_decide sets the step's conditional.  The energy
-// sums (k_reduce) run once after the last step of an md_step call.
-int capture(md_t *h, int nsteps, cudaGraphExec_t *out)
+// One graph of `nsteps` whole time steps: per step k_decide -> IF(rebuild) [list build] ->
+// k_verlet1 -> k_density (beside k_morse) -> k_force; k_decide sets the step's conditional.
+// In mixed precision the force kernel drifts the positions for the next step, and k_verlet1
+// runs only after a rebuild (inside the IF), except in a first step with first_full set
+// (after md_init, md_set_state, ...).  The energy sums (k_reduce) run once after the last
+// step of an md_step call; with last_energy the graph's last force kernel writes the
+// partials they add.
+int capture(md_t *h, int nsteps, bool first_full, bool last_energy, cudaGraphExec_t *out)
 {
     cudaGraph_t g = nullptr;
     CU(cudaGraphCreate(&g, 0));
     std::vector<cudaGraphNode_t> deps;
     const cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
     for (int k = 0; k < nsteps; ++k) {
+        const int dm = (h->a.mixed && !(first_full && k == 0)) ? DEC_DRIFT : DEC_FULL;
+        const int en = last_energy && k == nsteps - 1;
         cudaGraphConditionalHandle hc;
         CU(cudaGraphConditionalHandleCreate(&hc, g, 0, cudaGraphCondAssignDefault));
         CU(cudaStreamBeginCaptureToGraph(h->cap, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), mode));
-        CU(launch_decide(h->a, 0, 1, hc, h->cap));
+        CU(launch_decide(h->a, dm, 1, hc, h->cap));
         cudaStreamCaptureStatus cs;
         const cudaGraphNode_t *d = nullptr;
         size_t nd = 0;
@@ -221,9 +243,10 @@ int capture(md_t *h, int nsteps, cudaGraphExec_t *out)
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         CU(cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, mode));
         CU(launch_rebuild(h->a, h->cap));
+        if (dm == DEC_DRIFT) CU(launch_verlet1(h->a, h->cap));   // the drift was made before the build
         CU(cudaStreamEndCapture(h->cap, &body));
         CU(cudaStreamBeginCaptureToGraph(h->cap, g, &cn, nullptr, 1, mode));
-        CU(launch_verlet1(h->a, h->cap));
+        if (dm == DEC_FULL) CU(launch_verlet1(h->a, h->cap));
         if (h->a.mixed) {   // the Morse sums need only this step's positions: beside k_density
             CU(cudaEventRecord(h->fork, h->cap));
             CU(cudaStreamWaitEvent(h->cap2, h->fork, 0));
@@ -231,10 +254,10 @@ int capture(md_t *h, int nsteps, cudaGraphExec_t *out)
             CU(cudaEventRecord(h->join, h->cap2));
             CU(launch_density(h->a, h->pot, h->cfg, h->cap));
             CU(cudaStreamWaitEvent(h->cap, h->join, 0));
-            CU(launch_force_split(h->a, h->pot, h->cfg, 1, 0, h->cap));
+            CU(launch_force_split(h->a, h->pot, h->cfg, 1, en, 0, h->cap));
         } else {
             CU(launch_density(h->a, h->pot, h->cfg, h->cap));
-            CU(launch_force(h->a, h->pot, h->cfg, 1, h->cap));
+            CU(launch_force(h->a, h->pot, h->cfg, 1, en, h->cap));
         }
         CU(cudaStreamGetCaptureInfo(h->cap, &cs, nullptr, nullptr, &d, nullptr, &nd));
         deps.assign(d, d + nd);
@@ -250,31 +273,39 @@ int build_graphs(md_t *h)
 {
     destroy_graphs(h);
     if (!h->opt.use_graph) return MD_OK;
-    int rc = capture(h, 1, &h->exec1);
-    if (rc) return rc;
-    if (h->unroll > 1) rc = capture(h, h->unroll, &h->execU);
-    return rc;
+    int rc;
+    if ((rc = capture(h, 1, false, false, &h->exec1))) return rc;
+    if ((rc = capture(h, 1, false, true, &h->execE))) return rc;
+    if (h->unroll > 1 && (rc = capture(h, h->unroll, false, false, &h->execU))) return rc;
+    if (h->a.mixed) {
+        if ((rc = capture(h, 1, true, false, &h->execF))) return rc;
+        if ((rc = capture(h, 1, true, true, &h->execFE))) return rc;
+    }
+    return MD_OK;
 }
 
-// the per-step sequence with direct launches (no graph); the host reads the rebuild flag
-int step_direct(md_t *h, cudaEvent_t *ev, bool *rebuilt)
+// the per-step sequence with direct launches (no graph); the host reads the rebuild flag.
+// energies: the force kernel writes the energy partials (needed by the step k_reduce follows)
+int step_direct(md_t *h, cudaEvent_t *ev, bool *rebuilt, bool energies)
 {
     cudaStream_t s = h->stream;
     if (ev) CU(cudaEventRecord(ev[0], s));
-    CU(launch_decide(h->a, 0, 0, 0, s));
+    CU(launch_decide(h->a, h->drift ? DEC_DRIFT : DEC_FULL, 0, 0, s));
     if (ev) CU(cudaEventRecord(ev[1], s));
-    int32_t flag = 0;
+    int32_t flag = 0, verlet = 1;
     CU(cudaMemcpyAsync(&flag, &h->a.st->any_rebuild, sizeof flag, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(&verlet, &h->a.st->run_verlet, sizeof verlet, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (ev) CU(cudaEventRecord(ev[2], s));
     if (flag) CU(launch_rebuild(h->a, s));
     if (ev) CU(cudaEventRecord(ev[3], s));
-    CU(launch_verlet1(h->a, s));
+    if (verlet) CU(launch_verlet1(h->a, s));
     if (ev) CU(cudaEventRecord(ev[4], s));
     CU(launch_density(h->a, h->pot, h->cfg, s));
     if (ev) CU(cudaEventRecord(ev[5], s));
-    CU(launch_force(h->a, h->pot, h->cfg, 1, s));
+    CU(launch_force(h->a, h->pot, h->cfg, 1, energies ? 1 : 0, s));
     if (ev) CU(cudaEventRecord(ev[6], s));
+    h->drift = h->a.mixed != 0;
     if (rebuilt) *rebuilt = flag != 0;
     return MD_OK;
 }
@@ -468,11 +499,16 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     INIT_FAIL(dalloc(h, &d_tile_rep, S / MD_TILE));
     INIT_FAIL(dalloc(h, &d_cell_rep, cells));
     a.rep = d_rep; a.rs = d_rs; a.en = d_en; a.st = d_st; a.tile_rep = d_tile_rep; a.cell_rep = d_cell_rep;
-    INIT_FAIL(dalloc(h, &a.x, 3 * (size_t)S));
+    // two position buffers in mixed precision: the force epilogue drifts the positions it
+    // has just used to the other one (one buffer in FP64, where k_verlet1 runs every step)
+    INIT_FAIL(dalloc(h, &a.xs[0], 3 * (size_t)S));
+    if (a.mixed) INIT_FAIL(dalloc(h, &a.xs[1], 3 * (size_t)S)); else a.xs[1] = a.xs[0];
     INIT_FAIL(dalloc(h, &a.v, 3 * (size_t)S));
+    INIT_FAIL(dalloc(h, &a.vh, 3 * (size_t)S));
     INIT_FAIL(dalloc(h, &a.F, 3 * (size_t)S));
     INIT_FAIL(dalloc(h, &a.xb, 3 * (size_t)S));
-    INIT_FAIL(dalloc(h, &a.pos4, S));
+    INIT_FAIL(dalloc(h, &a.p4[0], S));
+    if (a.mixed) INIT_FAIL(dalloc(h, &a.p4[1], S)); else a.p4[1] = a.p4[0];
     INIT_FAIL(dalloc(h, &a.fm64, S));
     INIT_FAIL(dalloc(h, &a.fm32, S));
     INIT_FAIL(dalloc(h, &a.cellc, S));
@@ -574,7 +610,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
             hrs[r].z_ind = y.z_indenter0;
             hrs[r].z_build = y.z_indenter0;
         }
-        CUI(cudaMemcpy(a.x, hx.data(), hx.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CUI(cudaMemcpy(a.xs[0], hx.data(), hx.size() * sizeof(double), cudaMemcpyHostToDevice));   // ph = 0
         CUI(cudaMemcpy(a.v, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice));
         CUI(cudaMemcpy(a.orig, horig.data(), S * sizeof(int32_t), cudaMemcpyHostToDevice));
         CUI(cudaMemcpy(a.fixed, hfix.data(), S, cudaMemcpyHostToDevice));
@@ -657,14 +693,21 @@ int md_step(md_t *h, int64_t n)
     int rc = ensure_forces(h);
     if (rc) return rc;
     if ((rc = clear_err(h))) return rc;
-    if (h->opt.use_graph && h->exec1) {
+    if (h->opt.use_graph && h->exec1 && n > 0) {
+        // steps 0 .. n-2 without the energies, step n-1 with them (k_reduce follows)
         int64_t k = 0;
+        if (h->a.mixed && !h->drift) {
+            CU(cudaGraphLaunch(n == 1 ? h->execFE : h->execF, h->stream));
+            k = 1;
+        }
+        h->drift = h->a.mixed != 0;
         if (h->execU)
-            for (; k + h->unroll <= n; k += h->unroll) CU(cudaGraphLaunch(h->execU, h->stream));
-        for (; k < n; ++k) CU(cudaGraphLaunch(h->exec1, h->stream));
+            for (; k + h->unroll <= n - 1; k += h->unroll) CU(cudaGraphLaunch(h->execU, h->stream));
+        for (; k < n - 1; ++k) CU(cudaGraphLaunch(h->exec1, h->stream));
+        if (k < n) CU(cudaGraphLaunch(h->execE, h->stream));
     } else {
         for (int64_t k = 0; k < n; ++k)
-            if ((rc = step_direct(h, nullptr, nullptr))) return rc;
+            if ((rc = step_direct(h, nullptr, nullptr, k == n - 1))) return rc;
     }
     if (n > 0) CU(launch_reduce(h->a, h->cfg, h->stream));
     DevStatus st;
@@ -681,7 +724,7 @@ int md_step_profiled(md_t *h, int64_t n, md_phase_times *out)
     memset(out, 0, sizeof *out);
     for (int64_t k = 0; k < n; ++k) {
         bool rebuilt = false;
-        if ((rc = step_direct(h, h->ev.data(), &rebuilt))) return rc;
+        if ((rc = step_direct(h, h->ev.data(), &rebuilt, k == n - 1))) return rc;
         CU(cudaEventSynchronize(h->ev[6]));
         float ms[6];
         for (int p = 0; p < 6; ++p) CU(cudaEventElapsedTime(&ms[p], h->ev[p], h->ev[p + 1]));
@@ -731,11 +774,11 @@ int md_get_energy(md_t *h, int32_t r, md_energy *out)
     return MD_OK;
 }
 
-static int fetch(md_t *h, int32_t r, const double *src, double *out3n)
+static int fetch(md_t *h, int32_t r, const double *s0, const double *s1, double *out3n)
 {
     const RepDev &R = h->rep[r];
     int n = R.n_atoms;
-    k_state_out<<<(n + 255) / 256, 256, 0, h->stream>>>(src, h->stage, h->a.orig, R.slot_off, n, h->a.S);
+    k_state_out<<<(n + 255) / 256, 256, 0, h->stream>>>(s0, s1, h->a.st, h->stage, h->a.orig, R.slot_off, n, h->a.S);
     CU(cudaGetLastError());
     CU(cudaMemcpyAsync(out3n, h->stage, 3 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
@@ -747,7 +790,7 @@ int md_get_forces(md_t *h, int32_t r, double *out3n)
     int rc = check_replica(h, r);
     if (rc) return rc;
     if (!out3n) return fail(h, MD_ERR_ARG, "md_get_forces: null output");
-    return fetch(h, r, h->a.F, out3n);
+    return fetch(h, r, h->a.F, h->a.F, out3n);
 }
 
 int md_get_indenter_load(md_t *h, int32_t r, double *load_z, double *depth)
@@ -764,8 +807,8 @@ int md_get_state(md_t *h, int32_t r, double *x3n, double *v3n, double *z_ind, in
 {
     int rc = check_replica(h, r);
     if (rc) return rc;
-    if (x3n && (rc = fetch(h, r, h->a.x, x3n))) return rc;
-    if (v3n && (rc = fetch(h, r, h->a.v, v3n))) return rc;
+    if (x3n && (rc = fetch(h, r, h->a.xs[0], h->a.xs[1], x3n))) return rc;
+    if (v3n && (rc = fetch(h, r, h->a.v, h->a.v, v3n))) return rc;
     if (z_ind || step) {
         RepState rs; DevStatus st;
         CU(cudaMemcpyAsync(&rs, h->a.rs + r, sizeof rs, cudaMemcpyDeviceToHost, h->stream));
@@ -783,16 +826,19 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     if (rc) return rc;
     const RepDev &R = h->rep[r];
     int n = R.n_atoms;
+    h->drift = false;   // k_state_zero voids the drift made from the old state
     if (x3n) {
         CU(cudaMemcpyAsync(h->stage, x3n, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        k_state_in<<<(n + 255) / 256, 256, 0, h->stream>>>(h->stage, h->a.x, h->a.orig, R.slot_off, n, h->a.S);
+        k_state_in<<<(n + 255) / 256, 256, 0, h->stream>>>(h->stage, h->a.xs[0], h->a.xs[1], h->a.st, h->a.orig,
+                                                           R.slot_off, n, h->a.S);
         CU(cudaGetLastError());
         CU(cudaMemsetAsync(&h->a.st->pos4_ok, 0, sizeof(int32_t), h->stream));   // pos4 is stale now
     }
     if (v3n) {
         double *st2 = h->stage + 3 * (size_t)n;
         CU(cudaMemcpyAsync(st2, v3n, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        k_state_in<<<(n + 255) / 256, 256, 0, h->stream>>>(st2, h->a.v, h->a.orig, R.slot_off, n, h->a.S);
+        k_state_in<<<(n + 255) / 256, 256, 0, h->stream>>>(st2, h->a.v, h->a.v, h->a.st, h->a.orig, R.slot_off, n,
+                                                           h->a.S);
         CU(cudaGetLastError());
     }
     k_set_scalars<<<1, 1, 0, h->stream>>>(h->a.rs, r, z_ind, h->a.st, (long long)step, 1);

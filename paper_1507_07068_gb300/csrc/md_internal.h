@@ -33,7 +33,12 @@
 #define MD_J_MASK ((1u << MD_J_BITS) - 1u)
 
 // error bits raised by kernels (device word, read by the host after md_step)
-enum { MDE_OVERFLOW = 1, MDE_LOST = 2, MDE_SKIN = 4, MDE_COVERFLOW = 8 };
+// (MDE_SCHED: a step launched without k_verlet1 found no drift ready - a host bookkeeping error)
+enum { MDE_OVERFLOW = 1, MDE_LOST = 2, MDE_SKIN = 4, MDE_COVERFLOW = 8, MDE_SCHED = 16 };
+// what k_decide is launched for: an explicit list build (no step), a step whose Task 3 the
+// last step's force epilogue made (k_verlet1 runs only if the lists are rebuilt), or a step
+// that runs k_verlet1
+enum { DEC_BUILD = 0, DEC_DRIFT = 1, DEC_FULL = 2 };
 // skin of the inner list (A): rebuilt from the Verlet list when an atom has moved more than
 // half of it since the last rebuild
 #define MD_INNER_SKIN 0.1
@@ -115,11 +120,14 @@ struct RepDev {
 
 // mutable per-replica scalars
 struct RepState {
-    double z_ind, z_build;
-    unsigned long long d2max_bits;       // max |x - x_build|^2 since last decision (bits of a double)
+    double z_ind, z_build;               // indenter displacement at the state's time; at the last build
+    double z_cur;                        // z_ind at the start of the current step (what a rebuild uses)
+    unsigned long long d2b[2];           // max |x - x_build|^2 of the positions in position buffer k
+                                         // (bits of a double), for the rebuild test of their time
     int32_t need;                        // rebuild decided for this step
-    float dthr;                          // mixed: displacements below this (A) cannot decide the next
-                                         // rebuild test; k_verlet1 takes them in FP32 (set by k_decide)
+    float dthr, dthr2;                   // mixed: displacements below these (A) cannot decide the rebuild
+                                         // test of the positions k_verlet1 / the force epilogue produce
+    int32_t pad;
 };
 
 // energies of one replica (device copy of md_energy's sums)
@@ -135,11 +143,18 @@ struct DevStatus {
     int32_t pos4_ok;        // pos4 holds every atom's current position about its cell's centre
     int32_t n_cand;         // atoms queued for the Cr-C list search (set by k_nbrc)
     int32_t n_near;         // atoms with Cr-C neighbours (set by k_nbrc_near)
-    uint32_t imax_bits;     // mixed: max over atoms of |p - p_in|^2 (FP32 bits) after k_verlet1
+    uint32_t imax_bits;     // mixed: max over atoms of |p - p_in|^2 (FP32 bits) at the positions
+                            // this step's k_density uses
+    uint32_t imax_next;     // the same for the positions the force epilogue drifted to
     int32_t inner_ok;       // mixed: the inner list is valid for this step's k_density
     int32_t inner_ok_next;  // set by the k_density that rebuilt it; k_decide moves it over
-    int32_t pad_;
+    int32_t drift_ok;       // mixed: the force epilogue already made the next step's Tasks 2-3
+    int32_t run_verlet;     // k_verlet1 runs this step (a rebuild, or a step launched as DEC_FULL)
     int64_t step, rebuilds, since_build;
+    // position buffers xs[], p4[] in use: the state is in buffer ph & 1 (during a step, from
+    // k_decide on, the positions the pair kernels evaluate); the state a step started from
+    // is in buffer ph_cur & 1.  k_decide advances ph; md_set_state keeps it.
+    int64_t ph, ph_cur;
 };
 
 // everything the kernels need, by value
@@ -158,9 +173,14 @@ struct DevArgs {
     const int32_t *tile_rep;     // replica of each tile
     const double *cen;           // cell-centre coordinates per axis (see RepDev::cen_off)
     const int32_t *cell_rep;     // replica of each cell
-    // per-atom
-    double *x, *v, *F, *xb;      // [3][S]
-    float4 *pos4;
+    // per-atom.  Positions and their FP32 cell-relative copies live in two buffers: during a
+    // step, buffer (cur & 1) holds the state the step starts from and buffer (step & 1) the
+    // positions the pair kernels use (outside a step both indices name the state).  FP64
+    // mode keeps one buffer (both pointers equal).
+    double *xs[2];               // [3][S] each
+    float4 *p4[2];
+    double *v, *F, *xb;          // [3][S]: velocity and force at the state's time, x at the build
+    double *vh;                  // [3][S]: v(t + dt/2) of the current step
     double2 *fm64;
     float2 *fm32;
     int32_t *inner, *icnt;       // mixed precision: the inner list, entries of the Verlet list
@@ -197,15 +217,18 @@ struct LaunchCfg {
 int md_build_pot(const md_params *p, PotDev *out, Cf64 **d_tabs64, float4 **d_tabs32, char *err, size_t errlen);
 
 // ---- launchers (all enqueue on `s`; return cudaError_t of the launch)
-cudaError_t launch_decide(const DevArgs &a, int force, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_decide(const DevArgs &a, int mode, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s);
 cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s);
 cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c, cudaStream_t s);
-cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, cudaStream_t s);
+// energies = 0: the mixed-precision force kernel leaves the energy partials alone (k_reduce
+// must follow a launch with energies = 1); the FP64 one always writes them
+cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int energies,
+                         cudaStream_t s);
 // the Morse sums alone (mixed precision), and the force kernel with or without them first
 cudaError_t launch_morse(const DevArgs &a, const PotDev &p, cudaStream_t s);
-cudaError_t launch_force_split(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int with_morse,
-                               cudaStream_t s);
+cudaError_t launch_force_split(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int energies,
+                               int with_morse, cudaStream_t s);
 cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_refresh_pos4(const DevArgs &a, cudaStream_t s);
 // d2max of every replica at the current positions and any_rebuild by the displacement rule

@@ -385,13 +385,24 @@ __device__ __forceinline__ void cta_partials(T (&v)[NV], double *part, int strid
 
 // ============================================================================ Task 1 decision
 
-__global__ void k_decide(DevArgs a, int force, int use_cond, cudaGraphConditionalHandle h)
+// the position buffer of the state a step started from, and of the positions it evaluates
+__device__ __forceinline__ int buf_cur(const DevArgs &a) { return (int)(*(volatile long long *)&a.st->ph_cur & 1); }
+__device__ __forceinline__ int buf_step(const DevArgs &a) { return (int)(*(volatile long long *)&a.st->ph & 1); }
+
+// Task 1 of a step (mode DEC_DRIFT or DEC_FULL) or of an explicit list build (DEC_BUILD),
+// and for a step also Task 2: the indenter moves by v dt, and the step count and the buffer
+// counter advance (the pair kernels of this step find their positions in buffer ph & 1).
+// The graph's conditional (use_cond) gets the rebuild decision.
+__global__ void k_decide(DevArgs a, int mode, int use_cond, cudaGraphConditionalHandle h)
 {
+    const int force = mode == DEC_BUILD;
+    const long long T = a.st->ph;   // buffer counter of the state this step starts from
+    const int bs = (int)(T & 1);
     int any = 0;
     for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) {
         RepState &S = a.rs[r];
-        double dmax = sqrt(__longlong_as_double((long long)S.d2max_bits));
-        S.d2max_bits = 0ull;
+        double dmax = sqrt(__longlong_as_double((long long)S.d2b[bs]));
+        S.d2b[bs] = 0ull;   // refilled by the force epilogue's drift to t + 2 dt
         int need;
         if (force) {
             need = 1;   // explicit build: no displacement test against a previous list
@@ -404,31 +415,43 @@ __global__ void k_decide(DevArgs a, int force, int use_cond, cudaGraphConditiona
         }
         S.need = need;
         any |= need;
-        // the next decision compares dmax with skin/2 and, with an indenter in the
-        // displacement mode, with skin - |z_ind - z_build| as they will be after this
-        // step's k_verlet1 (z_ind + v dt; z_build = z_ind if this step rebuilds).  An atom
-        // whose displacement is below both by more than the FP32 error of k_verlet1's
-        // estimate (< 1e-6 A) cannot change that decision.
-        const RepDev &Rr = a.rep[r];
-        double T = 0.5 * a.skin;
-        if (a.rebuild_every == 0 && Rr.n_c > 0) {
-            const double zn = __dadd_rn(S.z_ind, __dmul_rn(Rr.v_ind, Rr.dt));
+        S.z_cur = S.z_ind;
+        if (!force) {
+            // the rebuild tests of t + dt and t + 2 dt compare dmax with skin/2 and, with an
+            // indenter in the displacement mode, with skin - |z_ind - z_build| as they will
+            // be then (z_build = z_ind(t) if this step rebuilds).  A displacement below the
+            // limit by more than the FP32 error of the estimate (< 1e-6 A) cannot change
+            // that decision.
+            const RepDev &Rr = a.rep[r];
+            const double z1 = __dadd_rn(S.z_ind, __dmul_rn(Rr.v_ind, Rr.dt));
+            const double z2 = __dadd_rn(z1, __dmul_rn(Rr.v_ind, Rr.dt));
             const double zb = need ? S.z_ind : S.z_build;
-            T = fmin(T, a.skin - fabs(zn - zb));
+            double T1 = 0.5 * a.skin, T2 = 0.5 * a.skin;
+            if (a.rebuild_every == 0 && Rr.n_c > 0) {
+                T1 = fmin(T1, a.skin - fabs(z1 - zb));
+                T2 = fmin(T2, a.skin - fabs(z2 - zb));
+            }
+            S.dthr = (float)(T1 - 1e-5);
+            S.dthr2 = (float)(T2 - 1e-5);
+            S.z_ind = z1;   // Task 2
         }
-        S.dthr = (float)(T - 1e-5);
     }
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
+        const int run_verlet = mode == DEC_FULL || (mode == DEC_DRIFT && any);
+        if (mode == DEC_DRIFT && !any && !a.st->drift_ok) atomicOr(&a.st->err, MDE_SCHED);
+        a.st->ph_cur = T;
+        if (!force) { a.st->ph = T + 1; a.st->step += 1; }
         a.st->inner_ok = a.st->inner_ok_next;   // a rebuild of the Verlet list below clears both
-        a.st->imax_bits = 0u;
+        a.st->imax_bits = run_verlet ? 0u : a.st->imax_next;
+        a.st->imax_next = 0u;
+        if (run_verlet)   // k_verlet1 fills the accumulator of the positions it makes
+            for (int r = 0; r < a.n_rep; ++r) a.rs[r].d2b[bs ^ 1] = 0ull;
         a.st->any_rebuild = any;
+        a.st->run_verlet = run_verlet;
         if (use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
     }
 }
-
-// ============================================================================ Task 1: rebuild
-
 __global__ void k_zero_i32(int32_t *p, int n)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -455,8 +478,10 @@ __global__ void k_bin(DevArgs a)
     if (s - R.slot_off >= R.n_atoms) return;
     int c[3];
     bool done = false;
+    const int b = buf_cur(a);
+    double *x = a.xs[b];
     if (*(volatile int32_t *)&a.st->pos4_ok) {
-        const float4 p = a.pos4[s];
+        const float4 p = a.p4[b][s];
         const int pc = __float_as_int(p.w);
         const float pr[3] = {p.x, p.y, p.z};
         const int cc[3] = {cell_x(pc), cell_y(pc), cell_z(pc)};
@@ -483,8 +508,8 @@ __global__ void k_bin(DevArgs a)
 #pragma unroll
             for (int k = 0; k < 3; ++k)
                 if (wrap[k]) {
-                    const double xk = a.x[(size_t)k * a.S + s];
-                    a.x[(size_t)k * a.S + s] = wrap[k] > 0 ? __dsub_rn(xk, R.L[k]) : __dadd_rn(xk, R.L[k]);
+                    const double xk = x[(size_t)k * a.S + s];
+                    x[(size_t)k * a.S + s] = wrap[k] > 0 ? __dsub_rn(xk, R.L[k]) : __dadd_rn(xk, R.L[k]);
                 }
             done = true;
         }
@@ -493,11 +518,11 @@ __global__ void k_bin(DevArgs a)
         bool lost = false;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            double xk = a.x[(size_t)k * a.S + s];
+            double xk = x[(size_t)k * a.S + s];
             if (xk != xk) lost = true;
             if (R.per[k]) {
                 xk = wrap_exact(xk, R.lo[k], R.L[k], R.iL[k]);
-                a.x[(size_t)k * a.S + s] = xk;
+                x[(size_t)k * a.S + s] = xk;
             } else if (xk < R.lo[k] || xk > R.hi[k]) {
                 lost = true;
             }
@@ -603,9 +628,10 @@ __global__ void k_gather(DevArgs a)
     if (s - R.slot_off >= R.n_atoms) return;
     int o = a.perm[s];
     size_t S = a.S;
+    const double *x = a.xs[buf_cur(a)];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        a.sx[k * S + s] = a.x[k * S + o];
+        a.sx[k * S + s] = x[k * S + o];
         a.sv[k * S + s] = a.v[k * S + o];
         a.sF[k * S + s] = a.F[k * S + o];
     }
@@ -625,11 +651,14 @@ __device__ __forceinline__ float4 rel_pos3(const DevArgs &a, const RepDev &R, in
     return make_float4((float)(x0 - c0), (float)(x1 - c1), (float)(x2 - c2), __int_as_float(pc));
 }
 
-__device__ __forceinline__ float4 rel_pos(const DevArgs &a, const RepDev &R, int s)
+__device__ __forceinline__ float4 rel_pos(const DevArgs &a, const RepDev &R, const double *x, int s)
 {
     size_t S = a.S;
-    return rel_pos3(a, R, a.cellc[s], a.x[s], a.x[S + s], a.x[2 * S + s]);
+    return rel_pos3(a, R, a.cellc[s], x[s], x[S + s], x[2 * S + s]);
 }
+
+// position buffers: the state a step (or a list build) starts from, and the positions the
+// pair kernels use (the state outside a step)
 
 __global__ void k_copyback(DevArgs a)
 {
@@ -638,18 +667,20 @@ __global__ void k_copyback(DevArgs a)
     const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
     if (s - R.slot_off >= R.n_atoms) return;
     size_t S = a.S;
+    const int b = buf_cur(a);
+    double *x = a.xs[b];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         double xk = a.sx[k * S + s];
-        a.x[k * S + s] = xk;
+        x[k * S + s] = xk;
         a.xb[k * S + s] = xk;
         a.v[k * S + s] = a.sv[k * S + s];
         a.F[k * S + s] = a.sF[k * S + s];
     }
     a.orig[s] = a.sorig[s];
     a.fixed[s] = a.sfixed[s];
-    const float4 p = rel_pos(a, R, s);
-    a.pos4[s] = p;   // also used by the FP32 prefilter of k_nbr
+    const float4 p = rel_pos(a, R, x, s);
+    a.p4[b][s] = p;   // also used by the FP32 prefilter of k_nbr
     if (a.mixed) a.pb[s] = p;
     if (s == 0) a.st->pos4_ok = 1;
 }
@@ -674,7 +705,10 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
     if (s - R.slot_off >= R.n_atoms) return;
     if (*(volatile int32_t *)&a.st->err & MDE_LOST) { a.cnt[s] = 0; return; }
     size_t S = a.S;
-    const float4 pi = a.pos4[s];
+    const int bc = buf_cur(a);
+    const double *x = a.xs[bc];
+    const float4 *pos4 = a.p4[bc];
+    const float4 pi = pos4[s];
     int pc = __float_as_int(pi.w);
     int c0 = cell_x(pc), c1 = cell_y(pc), c2 = cell_z(pc);
     const float cut2 = (float)a.cut2;
@@ -709,7 +743,7 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
                   // four candidate positions are loaded before any test or list store
                   float4 pjv[4];
 #pragma unroll
-                  for (int u = 0; u < 4; ++u) pjv[u] = __ldg(&a.pos4[min(t0 + u, e - 1)]);
+                  for (int u = 0; u < 4; ++u) pjv[u] = __ldg(&pos4[min(t0 + u, e - 1)]);
 #pragma unroll
                   for (int u = 0; u < 4; ++u) {
                     const int t = t0 + u;
@@ -719,9 +753,9 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
                     const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
                     bool in = r2f < lo2;
                     if (valid && !in && !(r2f > hi2)) {
-                        double ddx = mi_exact(__dsub_rn(a.x[t], a.x[s]), R.per[0], R.L[0]);
-                        double ddy = mi_exact(__dsub_rn(a.x[S + t], a.x[S + s]), R.per[1], R.L[1]);
-                        double ddz = mi_exact(__dsub_rn(a.x[2 * S + t], a.x[2 * S + s]), R.per[2], R.L[2]);
+                        double ddx = mi_exact(__dsub_rn(x[t], x[s]), R.per[0], R.L[0]);
+                        double ddy = mi_exact(__dsub_rn(x[S + t], x[S + s]), R.per[1], R.L[1]);
+                        double ddz = mi_exact(__dsub_rn(x[2 * S + t], x[2 * S + s]), R.per[2], R.L[2]);
                         in = norm2_exact(ddx, ddy, ddz) < a.cut2;
                     }
                     if (in && valid) {
@@ -770,11 +804,11 @@ __global__ void __launch_bounds__(128) k_nbrc(DevArgs a)
     // cell-relative position with an error below 1e-4 A for coordinates below ~1e3 A;
     // the 0.01 A margin keeps every atom the exact test of k_nbrc_near could accept.
     // A non-finite position is queued (and then skipped: k_bin reports it).
-    const float4 p = a.pos4[s];
+    const float4 p = a.p4[buf_cur(a)][s];
     const int pc = __float_as_int(p.w);
     const float pr[3] = {p.x, p.y, p.z};
     const int cc[3] = {cell_x(pc), cell_y(pc), cell_z(pc)};
-    const float zi32 = (float)a.rs[r].z_ind;
+    const float zi32 = (float)a.rs[r].z_cur;
     const float lim = (float)a.cutc + 0.01f;
     bool far = false;
 #pragma unroll
@@ -798,8 +832,9 @@ __global__ void __launch_bounds__(256) k_nbrc_near(DevArgs a)
         const int s = a.cand[qi];
         const int r = a.tile_rep[s / MD_TILE];
         const RepDev &R = a.rep[r];
-        const double z_ind = a.rs[r].z_ind;
-        const double xi[3] = {a.x[s], a.x[S + s], a.x[2 * S + s]};
+        const double z_ind = a.rs[r].z_cur;
+        const double *x = a.xs[buf_cur(a)];
+        const double xi[3] = {x[s], x[S + s], x[2 * S + s]};
         if (!(isfinite(xi[0]) && isfinite(xi[1]) && isfinite(xi[2]))) continue;   // reported by k_bin
         unsigned long long mask[3];
         float q32[3];
@@ -869,132 +904,139 @@ __global__ void __launch_bounds__(256) k_nbrc_near(DevArgs a)
 
 __global__ void k_build_done(DevArgs a)
 {
-    for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) a.rs[r].z_build = a.rs[r].z_ind;
+    for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) a.rs[r].z_build = a.rs[r].z_cur;
     if (threadIdx.x == 0) {
         a.st->rebuilds += 1; a.st->since_build = 0;
         a.st->inner_ok = 0; a.st->inner_ok_next = 0;   // slots were permuted: the inner list is stale
+        a.st->drift_ok = 0;                             // and so is a drift made before the rebuild
     }
 }
 
 // ============================================================================ Tasks 2 + 3
 
-// Tasks 2 + 3 for step t, and the displacement test of step t+1's Task 1: the positions
-// x(t+1) written here are the ones the next step's decision examines (Sec. 2.6 rule on
-// max_i |x_i - x_build,i|, FP64, every operation separately rounded).  One CTA = one tile.
-__global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
+// Task 3 of one atom (Eqs. A11-A12: half kick, drift) from its state (x, v, F) at time t:
+// v(t + dt/2) to vh, x(t + dt) and its cell-relative copy to the buffers xd, pd, and the
+// displacement tests of x(t + dt): since the Verlet-list build (d2bits, for the rebuild
+// test; FP32 estimate from the cell-relative positions when it is below thr by more than
+// its error, else exact FP64) and, in mixed precision, since the inner-list build (ibits).
+// Fixed atoms keep x and v (they are copied).
+__device__ __forceinline__ void drift_atom(const DevArgs &a, const RepDev &R, int s, float thr,
+                                           double x0, double x1, double x2, double v0, double v1, double v2,
+                                           double F0, double F1, double F2, double *xd, float4 *pd,
+                                           unsigned long long &d2bits, unsigned &ibits)
 {
-    const int s = blockIdx.x * MD_TILE + threadIdx.x;
-    const int r = a.tile_rep[blockIdx.x];
-    const RepDev &R = a.rep[r];
-    if (s == R.slot_off) {   // Task 2: the rigid indenter moves by v_ind dt
-        RepState &st = a.rs[r];
-        st.z_ind = __dadd_rn(st.z_ind, __dmul_rn(R.v_ind, R.dt));
-        if (s == 0) {   // after this step's Task 1 decision
-            a.st->step += 1; a.st->since_build += 1;
-            if (!a.mixed) a.st->pos4_ok = 0;   // the FP64 path does not keep pos4 current
-        }
+    const size_t S = a.S;
+    if (!a.fixed[s]) {
+        const double hk = R.hk;
+        v0 = fma(hk, F0, v0); v1 = fma(hk, F1, v1); v2 = fma(hk, F2, v2);                 // Eq. A12
+        x0 = fma(R.dt, v0, x0); x1 = fma(R.dt, v1, x1); x2 = fma(R.dt, v2, x2);           // Eq. A11
     }
-    unsigned long long d2bits = 0ull;
-    unsigned ibits = 0u;
-    if (s - R.slot_off < R.n_atoms) {
-        const size_t S = a.S;
-        double x0 = a.x[s], x1 = a.x[S + s], x2 = a.x[2 * S + s];
-        if (!a.fixed[s]) {
-            const double hk = R.hk;
-            double v0 = fma(hk, a.F[s], a.v[s]);                    // Eq. A12
-            double v1 = fma(hk, a.F[S + s], a.v[S + s]);
-            double v2 = fma(hk, a.F[2 * S + s], a.v[2 * S + s]);
-            a.v[s] = v0; a.v[S + s] = v1; a.v[2 * S + s] = v2;
-            x0 = fma(R.dt, v0, x0); x1 = fma(R.dt, v1, x1); x2 = fma(R.dt, v2, x2);   // Eq. A11
-            a.x[s] = x0; a.x[S + s] = x1; a.x[2 * S + s] = x2;
-        }
-        bool exact = true;
-        if (a.mixed) {
-            const float4 p = rel_pos3(a, R, a.cellc[s], x0, x1, x2);
-            a.pos4[s] = p;
-            // displacement since the Verlet-list build from the cell-relative positions
-            // (same cell frame): when clearly below the threshold k_decide set, it cannot
-            // change the next decision and the exact FP64 value is not needed
-            const float4 b = a.pb[s];
-            const float bx = p.x - b.x, by = p.y - b.y, bz = p.z - b.z;
-            const float d2f = fmaf(bx, bx, fmaf(by, by, bz * bz));
-            const float thr = a.rs[r].dthr;
-            exact = !(thr > 0.0f && d2f < thr * thr);
-            // displacement since the inner list was rebuilt (same cell frame: a rebuild of the
-            // Verlet list in between invalidates the inner list anyway)
-            const float4 q = a.pin[s];
-            const float ex = p.x - q.x, ey = p.y - q.y, ez = p.z - q.z;
-            float dm2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-            if (!(dm2 <= 1e30f)) dm2 = 1e30f;   // not finite: force the rebuild
-            ibits = __float_as_uint(dm2);       // dm2 >= 0: bit order = value order
-        }
-        if (exact) {
-            double d2 = norm2_exact(__dsub_rn(x0, a.xb[s]), __dsub_rn(x1, a.xb[S + s]), __dsub_rn(x2, a.xb[2 * S + s]));
-            if (d2 != d2) d2 = 1e300;   // NaN position: force a rebuild, which reports it
-            d2bits = (unsigned long long)__double_as_longlong(d2);   // d2 >= 0: bit order = value order
-        }
+    a.vh[s] = v0; a.vh[S + s] = v1; a.vh[2 * S + s] = v2;
+    xd[s] = x0; xd[S + s] = x1; xd[2 * S + s] = x2;
+    bool exact = true;
+    if (a.mixed) {
+        const float4 p = rel_pos3(a, R, a.cellc[s], x0, x1, x2);
+        pd[s] = p;
+        // same cell frame as the build's copy pb: a displacement clearly below thr cannot
+        // change the rebuild test and its exact FP64 value is not needed
+        const float4 b = a.pb[s];
+        const float bx = p.x - b.x, by = p.y - b.y, bz = p.z - b.z;
+        const float d2f = fmaf(bx, bx, fmaf(by, by, bz * bz));
+        exact = !(thr > 0.0f && d2f < thr * thr);
+        // displacement since the inner list was rebuilt (same cell frame: a rebuild of the
+        // Verlet list in between invalidates the inner list anyway)
+        const float4 q = a.pin[s];
+        const float ex = p.x - q.x, ey = p.y - q.y, ez = p.z - q.z;
+        float dm2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+        if (!(dm2 <= 1e30f)) dm2 = 1e30f;   // not finite: force the rebuild
+        ibits = __float_as_uint(dm2);       // dm2 >= 0: bit order = value order
     }
+    if (exact) {
+        double d2 = norm2_exact(__dsub_rn(x0, a.xb[s]), __dsub_rn(x1, a.xb[S + s]), __dsub_rn(x2, a.xb[2 * S + s]));
+        if (d2 != d2) d2 = 1e300;   // NaN position: force a rebuild, which reports it
+        d2bits = (unsigned long long)__double_as_longlong(d2);   // d2 >= 0: bit order = value order
+    }
+}
+
+// maxima of a CTA's d2bits and ibits into *d2max and *imax (every thread of the CTA calls it)
+__device__ __forceinline__ void cta_max_disp(unsigned long long d2bits, unsigned ibits,
+                                             unsigned long long *d2max, unsigned *imax)
+{
     for (int o = 16; o > 0; o >>= 1) {
         unsigned long long t = __shfl_xor_sync(0xffffffffu, d2bits, o);
         d2bits = t > d2bits ? t : d2bits;
         ibits = max(ibits, __shfl_xor_sync(0xffffffffu, ibits, o));
     }
-    __shared__ unsigned long long sm[MD_TILE / 32];
-    __shared__ unsigned smi[MD_TILE / 32];
+    __shared__ unsigned long long sm[32];
+    __shared__ unsigned smi[32];
+    const int nw = (blockDim.x + 31) >> 5;
     if ((threadIdx.x & 31) == 0) { sm[threadIdx.x >> 5] = d2bits; smi[threadIdx.x >> 5] = ibits; }
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long m = 0ull;
         unsigned mi = 0u;
-        for (int w = 0; w < MD_TILE / 32; ++w) { m = sm[w] > m ? sm[w] : m; mi = max(mi, smi[w]); }
-        if (m) atomicMax(&a.rs[r].d2max_bits, m);
-        if (mi) atomicMax(&a.st->imax_bits, mi);
+        for (int w = 0; w < nw; ++w) { m = sm[w] > m ? sm[w] : m; mi = max(mi, smi[w]); }
+        if (m) atomicMax(d2max, m);
+        if (mi) atomicMax(imax, mi);
     }
 }
 
+// Task 3 when the last step's force epilogue did not make it (first step after a state was
+// set, or a rebuild this step): from the state in buffer ph_cur & 1 to buffer ph & 1 (one
+// buffer in FP64 mode: in place).  One CTA = one tile (one replica).
+__global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
+{
+    const int s = blockIdx.x * MD_TILE + threadIdx.x;
+    const int r = a.tile_rep[blockIdx.x];
+    const RepDev &R = a.rep[r];
+    if (s == 0 && !a.mixed) a.st->pos4_ok = 0;   // the FP64 path does not keep pos4 current
+    const int bs = buf_cur(a), bd = buf_step(a);
+    unsigned long long d2bits = 0ull;
+    unsigned ibits = 0u;
+    if (s - R.slot_off < R.n_atoms) {
+        const size_t S = a.S;
+        const double *x = a.xs[bs];
+        drift_atom(a, R, s, a.rs[r].dthr, x[s], x[S + s], x[2 * S + s], a.v[s], a.v[S + s], a.v[2 * S + s],
+                   a.F[s], a.F[S + s], a.F[2 * S + s], a.xs[bd], a.p4[bd], d2bits, ibits);
+    }
+    cta_max_disp(d2bits, ibits, &a.rs[r].d2b[bd], &a.st->imax_bits);
+}
+
 // List test after positions were replaced (md_set_state): exact FP64 max |x - x_build|^2
-// per replica, as k_verlet1 reduces it for k_decide, then k_state_need applies the
-// displacement rule of k_decide (whatever the rebuild mode: the caller's positions are
-// not integrator steps) and raises any_rebuild.
+// per replica of the state positions (buffer ph & 1), where k_decide looks for it, then
+// k_state_need applies the displacement rule of k_decide (whatever the rebuild mode: the
+// caller's positions are not integrator steps) and raises any_rebuild.
 __global__ void __launch_bounds__(MD_TILE) k_state_disp(DevArgs a)
 {
     const int s = blockIdx.x * MD_TILE + threadIdx.x;
     const int r = a.tile_rep[blockIdx.x];
     const RepDev &R = a.rep[r];
+    const int b = buf_step(a);
     unsigned long long d2bits = 0ull;
     if (s - R.slot_off < R.n_atoms) {
         const size_t S = a.S;
-        double d2 = norm2_exact(__dsub_rn(a.x[s], a.xb[s]), __dsub_rn(a.x[S + s], a.xb[S + s]),
-                                __dsub_rn(a.x[2 * S + s], a.xb[2 * S + s]));
+        const double *x = a.xs[b];
+        double d2 = norm2_exact(__dsub_rn(x[s], a.xb[s]), __dsub_rn(x[S + s], a.xb[S + s]),
+                                __dsub_rn(x[2 * S + s], a.xb[2 * S + s]));
         if (d2 != d2) d2 = 1e300;
         d2bits = (unsigned long long)__double_as_longlong(d2);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long t = __shfl_xor_sync(0xffffffffu, d2bits, o);
-        d2bits = t > d2bits ? t : d2bits;
-    }
-    __shared__ unsigned long long sm[MD_TILE / 32];
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = d2bits;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long m = 0ull;
-        for (int w = 0; w < MD_TILE / 32; ++w) m = sm[w] > m ? sm[w] : m;
-        if (m) atomicMax(&a.rs[r].d2max_bits, m);
-    }
+    cta_max_disp(d2bits, 0u, &a.rs[r].d2b[b], &a.st->imax_bits);
 }
 
 __global__ void k_state_zero(DevArgs a)
 {
-    for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) a.rs[r].d2max_bits = 0ull;
-    if (threadIdx.x == 0) a.st->imax_bits = 0u;
+    for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) { a.rs[r].d2b[0] = 0ull; a.rs[r].d2b[1] = 0ull; }
+    if (threadIdx.x == 0) { a.st->imax_bits = 0u; a.st->imax_next = 0u; a.st->drift_ok = 0; }
 }
 
 __global__ void k_state_need(DevArgs a)
 {
+    const int b = buf_step(a);
     int any = 0;
     for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) {
         const RepState &S = a.rs[r];
-        const double dmax = sqrt(__longlong_as_double((long long)S.d2max_bits));
+        const double dmax = sqrt(__longlong_as_double((long long)S.d2b[b]));
         any |= (2.0 * dmax > a.skin) ||
                (a.rep[r].n_c > 0 && __dadd_rn(dmax, fabs(__dsub_rn(S.z_ind, S.z_build))) > a.skin);
     }
@@ -1002,19 +1044,20 @@ __global__ void k_state_need(DevArgs a)
     if (threadIdx.x == 0) a.st->any_rebuild = any;
 }
 
-// pos4 of every atom about its cell's centre at the current positions (cells of the last
-// build), and, in mixed precision, the displacement since the inner list was built (as
-// k_verlet1 reduces it): the next k_density keeps that list if it is still valid.
-// imax_bits must be zero on entry (k_state_zero).
+// pos4 of every atom about its cell's centre at the state positions (buffer ph & 1, cells
+// of the last build), and, in mixed precision, the displacement since the inner list was
+// built (as k_verlet1 reduces it): the next k_density keeps that list if it is still valid.
+// imax_bits must be zero on entry (k_state_zero).  A drift made from the earlier state is void.
 __global__ void __launch_bounds__(MD_TILE) k_refresh_pos4(DevArgs a)
 {
     const int s = blockIdx.x * MD_TILE + threadIdx.x;
-    if (s == 0) { a.st->pos4_ok = 1; a.st->inner_ok = a.st->inner_ok_next; }
+    if (s == 0) { a.st->pos4_ok = 1; a.st->inner_ok = a.st->inner_ok_next; a.st->drift_ok = 0; }
     const RepDev &R = a.rep[a.tile_rep[blockIdx.x]];
+    const int b = buf_step(a);
     unsigned ibits = 0u;
     if (s - R.slot_off < R.n_atoms) {
-        const float4 p = rel_pos(a, R, s);
-        a.pos4[s] = p;
+        const float4 p = rel_pos(a, R, a.xs[b], s);
+        a.p4[b][s] = p;
         if (a.mixed) {
             const float4 q = a.pin[s];
             const float ex = p.x - q.x, ey = p.y - q.y, ez = p.z - q.z;
@@ -1126,7 +1169,8 @@ __device__ __forceinline__ float fa_val(const Pot32 &Q, float r2)
 
 // Phi beyond its double root (t > 0) is zero with its slope; t is clamped to 0 there,
 // where the Taylor form gives exactly 0 for both
-template <int IPOW>
+// f, f' and Phi' of a pair; Phi itself only when EN (the energies are wanted)
+template <int IPOW, bool EN>
 __device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, float &f, float &df, float &ph, float &dph)
 {
     const float r = r2 * rinv;
@@ -1134,7 +1178,7 @@ __device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, flo
     f = fr - Q.f_rc - (r - Q.rc) * Q.df_rc;
     df = -Q.beta * fr * rinv - Q.df_rc;
     const float t = fminf(fmaf(r, Q.inv_re, -Q.d) + fmaf(r, Q.inv_re_lo, -Q.d_lo), 0.0f);
-    ph = t * t * fmaf(fmaf(fmaf(Q.b3, t, Q.b2), t, Q.b1), t, Q.b0);
+    ph = EN ? t * t * fmaf(fmaf(fmaf(Q.b3, t, Q.b2), t, Q.b1), t, Q.b0) : 0.0f;
     dph = t * fmaf(fmaf(fmaf(Q.c3, t, Q.c2), t, Q.c1), t, Q.c0);
 }
 
@@ -1167,7 +1211,8 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
     const bool rebuild = !a.st->inner_ok || !(__uint_as_float(a.st->imax_bits) <= a.ithr2);
     float rho = 0.f, Ps = 0.f;
     int m = 0;   // inner-list entries of this lane
-    const float4 pi = a.pos4[s];
+    const float4 *pp = a.p4[buf_step(a)];   // positions x(t + dt)
+    const float4 pi = pp[s];
     const PairGeom G = pair_geom(R, __float_as_int(pi.w));
     const bool per = __any_sync(0xffffffffu, real && G.xmask != 0u);
     auto work = [&](auto PERC) {
@@ -1184,7 +1229,7 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
                 }
                 float4 pj[MD_UNROLL];
 #pragma unroll
-                for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&a.pos4[e[u] & MD_J_MASK]);
+                for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&pp[e[u] & MD_J_MASK]);
 #pragma unroll
                 for (int u = 0; u < MD_UNROLL; ++u) {
                     float dx, dy, dz;
@@ -1214,7 +1259,7 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
                 }
                 float4 pj[MD_UNROLL];
 #pragma unroll
-                for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&a.pos4[e[u] & MD_J_MASK]);
+                for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&pp[e[u] & MD_J_MASK]);
 #pragma unroll
                 for (int u = 0; u < MD_UNROLL; ++u) {
                     float dx, dy, dz;
@@ -1256,11 +1301,12 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
 }
 
 // Task 4b,c (Eq. (1) with the M term, Eqs. A6-A10; Morse Eqs. A5, A9) and Task 5 (the
-// closing half kick, FP64).  The force on i from j is coef * (x_j - x_i), coef = [(F'_i +
+// closing half kick, FP64).  EN: the pair and Morse energies, the indenter load and the
+// kinetic energy into the CTA partials (only the last step of an md_step call needs them).  The force on i from j is coef * (x_j - x_i), coef = [(F'_i +
 // F'_j) f' + (M'_i + M'_j) 2 f f' + Phi'] / r, over the inner list; its entries beyond rc
 // (~3 %) get weight 0 by a select (a branch on the distance measured 10 % slower).
-template <int TPA, int IPOW>
-__global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int integrate)
+template <int TPA, int IPOW, bool EN>
+__global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int integrate)
 {
     __shared__ float4 sm_off[64];
     const int A = blockDim.x / TPA;
@@ -1275,7 +1321,9 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
     const size_t S = a.S;
     float gx = 0.f, gy = 0.f, gz = 0.f, ep = 0.f;
     float mx = 0.f, my = 0.f, mz = 0.f, em = 0.f;
-    const float4 pi = a.pos4[s];
+    const int bn = buf_step(a), bo = buf_cur(a);   // x(t + dt) in bn; x(t + 2 dt) goes to bo
+    const float4 *pp = a.p4[bn];
+    const float4 pi = pp[s];
     const PairGeom G = pair_geom(R, __float_as_int(pi.w));
     const bool per = __any_sync(0xffffffffu, real && G.xmask != 0u);
     auto work = [&](auto PERC) {
@@ -1295,7 +1343,7 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
 #pragma unroll
             for (int u = 0; u < MD_UNROLL; ++u) {
                 const unsigned j = e[u] & MD_J_MASK;
-                pj[u] = __ldg(&a.pos4[j]);
+                pj[u] = __ldg(&pp[j]);
                 fmj[u] = __ldg(&a.fm32[j]);
             }
 #pragma unroll
@@ -1309,13 +1357,13 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
                     const float w = r2 < Q.rc2 ? 0.5f : 0.0f;
                     const float rinv = rsqrt_nr(r2);
                     float f, df, ph, dph;
-                    fa_phi<IPOW>(Q, r2, rinv, f, df, ph, dph);
+                    fa_phi<IPOW, EN>(Q, r2, rinv, f, df, ph, dph);
                     const float coef = fmaf(fmi.x + fmj[u].x, df, fmaf((fmi.y + fmj[u].y) * 2.0f * f, df, dph)) * rinv;
                     const float cw = coef * (w + w);
                     gx = fmaf(cw, dx, gx);
                     gy = fmaf(cw, dy, gy);
                     gz = fmaf(cw, dz, gz);
-                    ep = fmaf(w, ph, ep);
+                    if (EN) ep = fmaf(w, ph, ep);
                 }
             }
         }
@@ -1324,34 +1372,56 @@ __global__ void __launch_bounds__(256) k_force_mixed(DevArgs a, PotDev P, int in
     // Cr-C (Morse): summed by k_morse_mixed for the atoms with Cr-C neighbours
     if (real && lane == 0 && a.cntc[s] > 0) {
         const float4 fmo = a.fmorse[s];
-        mx = fmo.x; my = fmo.y; mz = fmo.z; em = fmo.w;
+        mx = fmo.x; my = fmo.y; mz = fmo.z; em = EN ? fmo.w : 0.0f;
     }
 #pragma unroll
     for (int o = TPA / 2; o > 0; o >>= 1) {
         gx += __shfl_xor_sync(0xffffffffu, gx, o);
         gy += __shfl_xor_sync(0xffffffffu, gy, o);
         gz += __shfl_xor_sync(0xffffffffu, gz, o);
-        ep += __shfl_xor_sync(0xffffffffu, ep, o);
         mx += __shfl_xor_sync(0xffffffffu, mx, o);
         my += __shfl_xor_sync(0xffffffffu, my, o);
         mz += __shfl_xor_sync(0xffffffffu, mz, o);
-        em += __shfl_xor_sync(0xffffffffu, em, o);
+        if (EN) {
+            ep += __shfl_xor_sync(0xffffffffu, ep, o);
+            em += __shfl_xor_sync(0xffffffffu, em, o);
+        }
     }
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    unsigned long long d2bits = 0ull;
+    unsigned ibits = 0u;
     if (real && lane == 0) {
         const double Fx = gx + mx, Fy = gy + my, Fz = gz + mz;
         a.F[s] = Fx; a.F[S + s] = Fy; a.F[2 * S + s] = Fz;
-        double vx = a.v[s], vy = a.v[S + s], vz = a.v[2 * S + s];
-        if (integrate && !a.fixed[s]) {   // Task 5: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2 (FP64)
-            const double hk = R.hk;
-            vx = fma(hk, Fx, vx); vy = fma(hk, Fy, vy); vz = fma(hk, Fz, vz);
-            a.v[s] = vx; a.v[S + s] = vy; a.v[2 * S + s] = vz;
+        double vx, vy, vz;
+        if (integrate) {   // Task 5: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2 (FP64)
+            vx = a.vh[s]; vy = a.vh[S + s]; vz = a.vh[2 * S + s];
+            if (!a.fixed[s]) {
+                const double hk = R.hk;
+                vx = fma(hk, Fx, vx); vy = fma(hk, Fy, vy); vz = fma(hk, Fz, vz);
+                a.v[s] = vx; a.v[S + s] = vy; a.v[2 * S + s] = vz;
+            }
+            // Task 3 of the next step, from the state just completed: x(t + 2 dt) to buffer
+            // bo, its rebuild test for the next k_decide but one, its inner-list test for
+            // the next k_density.  The next k_decide keeps it unless it rebuilds the lists.
+            const double *x = a.xs[bn];
+            drift_atom(a, R, s, a.rs[r].dthr2, x[s], x[S + s], x[2 * S + s], vx, vy, vz, Fx, Fy, Fz,
+                       a.xs[bo], a.p4[bo], d2bits, ibits);
+        } else {
+            vx = a.v[s]; vy = a.v[S + s]; vz = a.v[2 * S + s];
         }
-        const float ux = (float)vx, uy = (float)vy, uz = (float)vz;
-        acc[0] = ep; acc[1] = em; acc[2] = -mz;
-        acc[3] = (float)(0.5 / MD_ACC) * (float)R.mass * (ux * ux + uy * uy + uz * uz);
+        if (EN) {
+            const float ux = (float)vx, uy = (float)vy, uz = (float)vz;
+            acc[0] = ep; acc[1] = em; acc[2] = -mz;
+            acc[3] = (float)(0.5 / MD_ACC) * (float)R.mass * (ux * ux + uy * uy + uz * uz);
+        }
     }
-    cta_partials<4>(acc, a.part + 2 * (size_t)a.max_blocks, a.max_blocks, blockIdx.x);
+    if (integrate) cta_max_disp(d2bits, ibits, &a.rs[r].d2b[bo], &a.st->imax_next);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.st->drift_ok = integrate;
+        if (integrate) a.st->since_build += 1;
+    }
+    if (EN) cta_partials<4>(acc, a.part + 2 * (size_t)a.max_blocks, a.max_blocks, blockIdx.x);
 }
 
 // Task 4c for the mixed path (Eqs. A5, A9): one warp per atom with Cr-C neighbours (the
@@ -1370,7 +1440,8 @@ __global__ void __launch_bounds__(256) k_morse_mixed(DevArgs a, PotDev P)
         const int r = a.tile_rep[s / MD_TILE];
         const RepDev &R = a.rep[r];
         const int nc = a.cntc[s];
-        const double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
+        const double *x = a.xs[buf_step(a)];   // x(t + dt), with the indenter at z_ind(t + dt)
+        const double xi = x[s], yi = x[S + s], zi = x[2 * S + s];
         const double z_ind = a.rs[r].z_ind;
         float mx = 0.f, my = 0.f, mz = 0.f, em = 0.f;
         for (int k = lane; k < nc; k += 32) {
@@ -1407,14 +1478,15 @@ __global__ void __launch_bounds__(256) k_density_fp64(DevArgs a, PotDev P)
     const bool real = (s - R.slot_off) < R.n_atoms;
     const size_t S = a.S;
     double rho = 0.0, Ps = 0.0;
+    const double *x = a.xs[buf_step(a)];
     if (real) {
-        const double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
+        const double xi = x[s], yi = x[S + s], zi = x[2 * S + s];
         const int n = a.cnt[s];
         for (int k = lane; k < n; k += TPA) {
             const int j = (int)((unsigned)__ldg(&a.nbr[(size_t)k * S + s]) & MD_J_MASK);
-            const double dx = mi64(a.x[j] - xi, R.per[0], R.L[0]);
-            const double dy = mi64(a.x[S + j] - yi, R.per[1], R.L[1]);
-            const double dz = mi64(a.x[2 * S + j] - zi, R.per[2], R.L[2]);
+            const double dx = mi64(x[j] - xi, R.per[0], R.L[0]);
+            const double dy = mi64(x[S + j] - yi, R.per[1], R.L[1]);
+            const double dz = mi64(x[2 * S + j] - zi, R.per[2], R.L[2]);
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < P.rc2) {
                 double f, df;
@@ -1452,15 +1524,16 @@ __global__ void __launch_bounds__(256) k_force_fp64(DevArgs a, PotDev P, int int
     const size_t S = a.S, C = a.C;
     double gx = 0.0, gy = 0.0, gz = 0.0, ep = 0.0;
     double mx = 0.0, my = 0.0, mz = 0.0, em = 0.0;
+    const double *x = a.xs[buf_step(a)];
     if (real) {
-        const double xi = a.x[s], yi = a.x[S + s], zi = a.x[2 * S + s];
+        const double xi = x[s], yi = x[S + s], zi = x[2 * S + s];
         const double2 fmi = a.fm64[s];
         const int n = a.cnt[s];
         for (int k = lane; k < n; k += TPA) {
             const int j = (int)((unsigned)__ldg(&a.nbr[(size_t)k * S + s]) & MD_J_MASK);
-            const double dx = mi64(a.x[j] - xi, R.per[0], R.L[0]);
-            const double dy = mi64(a.x[S + j] - yi, R.per[1], R.L[1]);
-            const double dz = mi64(a.x[2 * S + j] - zi, R.per[2], R.L[2]);
+            const double dx = mi64(x[j] - xi, R.per[0], R.L[0]);
+            const double dy = mi64(x[S + j] - yi, R.per[1], R.L[1]);
+            const double dz = mi64(x[2 * S + j] - zi, R.per[2], R.L[2]);
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < P.rc2) {
                 const double2 fmj = a.fm64[j];
@@ -1507,7 +1580,8 @@ __global__ void __launch_bounds__(256) k_force_fp64(DevArgs a, PotDev P, int int
     if (real && lane == 0) {
         const double Fx = gx + mx, Fy = gy + my, Fz = gz + mz;
         a.F[s] = Fx; a.F[S + s] = Fy; a.F[2 * S + s] = Fz;
-        double vx = a.v[s], vy = a.v[S + s], vz = a.v[2 * S + s];
+        const double *vs = integrate ? a.vh : a.v;   // v(t + dt/2) from k_verlet1, or the state
+        double vx = vs[s], vy = vs[S + s], vz = vs[2 * S + s];
         if (integrate && !a.fixed[s]) {   // Task 5: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2
             const double hk = 0.5 * R.dt * R.acc_per_f;
             vx += hk * Fx; vy += hk * Fy; vz += hk * Fz;
@@ -1515,6 +1589,10 @@ __global__ void __launch_bounds__(256) k_force_fp64(DevArgs a, PotDev P, int int
         }
         acc[0] = ep; acc[1] = em; acc[2] = -mz;
         acc[3] = 0.5 * R.mass * (vx * vx + vy * vy + vz * vz) / MD_ACC;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.st->drift_ok = 0;   // no drift ahead on the FP64 path: k_verlet1 runs every step
+        if (integrate) a.st->since_build += 1;
     }
     cta_partials<4>(acc, a.part + 2 * (size_t)a.max_blocks, a.max_blocks, blockIdx.x);
 }
@@ -1553,9 +1631,9 @@ inline unsigned nblk(long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // ============================================================================ launchers
 
-cudaError_t launch_decide(const DevArgs &a, int force, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s)
+cudaError_t launch_decide(const DevArgs &a, int mode, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s)
 {
-    k_decide<<<1, 256, 0, s>>>(a, force, use_cond, h);
+    k_decide<<<1, 256, 0, s>>>(a, mode, use_cond, h);
     return cudaGetLastError();
 }
 
@@ -1615,12 +1693,17 @@ static void dens_t(const DevArgs &a, const PotDev &p, int block, cudaStream_t s)
 }
 
 template <int TPA>
-static void force_t(const DevArgs &a, const PotDev &p, int block, int integ, cudaStream_t s)
+static void force_t(const DevArgs &a, const PotDev &p, int block, int integ, int en, cudaStream_t s)
 {
     int A = block / TPA;
     if (a.mixed) {
-        if (p.q.ipow == 3) k_force_mixed<TPA, 3><<<a.S / A, block, 0, s>>>(a, p, integ);
-        else k_force_mixed<TPA, 0><<<a.S / A, block, 0, s>>>(a, p, integ);
+        if (p.q.ipow == 3) {
+            if (en) k_force_mixed<TPA, 3, true><<<a.S / A, block, 0, s>>>(a, p, integ);
+            else k_force_mixed<TPA, 3, false><<<a.S / A, block, 0, s>>>(a, p, integ);
+        } else {
+            if (en) k_force_mixed<TPA, 0, true><<<a.S / A, block, 0, s>>>(a, p, integ);
+            else k_force_mixed<TPA, 0, false><<<a.S / A, block, 0, s>>>(a, p, integ);
+        }
     }
     else {
         k_force_fp64<TPA><<<a.S / A, block, 0, s>>>(a, p, integ);
@@ -1644,20 +1727,21 @@ cudaError_t launch_morse(const DevArgs &a, const PotDev &p, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, cudaStream_t s)
+cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int energies,
+                         cudaStream_t s)
 {
-    return launch_force_split(a, p, c, integrate, 1, s);
+    return launch_force_split(a, p, c, integrate, energies, 1, s);
 }
 
-cudaError_t launch_force_split(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int with_morse,
-                               cudaStream_t s)
+cudaError_t launch_force_split(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int energies,
+                               int with_morse, cudaStream_t s)
 {
     if (with_morse && a.mixed) k_morse_mixed<<<MD_NEAR_BLOCKS, 256, 0, s>>>(a, p);
     switch (c.tpa) {
-    case 1: force_t<1>(a, p, c.block, integrate, s); break;
-    case 2: force_t<2>(a, p, c.block, integrate, s); break;
-    case 4: force_t<4>(a, p, c.block, integrate, s); break;
-    default: force_t<8>(a, p, c.block, integrate, s); break;
+    case 1: force_t<1>(a, p, c.block, integrate, energies, s); break;
+    case 2: force_t<2>(a, p, c.block, integrate, energies, s); break;
+    case 4: force_t<4>(a, p, c.block, integrate, energies, s); break;
+    default: force_t<8>(a, p, c.block, integrate, energies, s); break;
     }
     return cudaGetLastError();
 }

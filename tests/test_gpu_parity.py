@@ -265,6 +265,49 @@ def test_graph_and_direct_launch_bitwise_equal(md, params):
     assert t["steps"] == 5 and t["force"] > 0 and t["density"] > 0
 
 
+def test_interleaved_calls_keep_the_trajectory(md, params):
+    """The mixed-precision force kernel makes the next step's drift; a state set from the
+    host (even unchanged, even with another step count), forces recomputed, or lists
+    rebuilt between steps void it and the next step drifts afresh.  A run interrupted by
+    such calls that do not change the state follows the uninterrupted run bit for bit, with
+    graphs (unrolled and single steps) and with direct launches alike."""
+    rep = tiny(amp=0.05, gap=2.0, T=600.0)
+    ref = md.MD([rep], params, precision="mixed")
+    ref.step(3 + 1 + 2 + 9 + 4)
+    runs = [md.MD([rep], params, precision="mixed", use_graph=g) for g in (True, False)]
+    for sim in runs:
+        sim.step(3)
+        x, v, z, st = sim.state(0)
+        sim.set_state(0, x, v, z, st)          # same state: lists kept
+        sim.step(1)
+        sim.compute_forces()
+        sim.step(2)
+        sim.step(9)                            # one unrolled graph and one single step
+        x, v, z, st = sim.state(0)
+        sim.set_state(0, x, v, z, st + 1)      # another step count (the buffers keep their parity)
+        sim.step(4)
+        assert sim.energy(0)["step"] == 3 + 1 + 2 + 9 + 4 + 1
+    xr, vr, zr, _ = ref.state(0)
+    for sim in runs:
+        x, v, z, _ = sim.state(0)
+        assert np.array_equal(x, xr) and np.array_equal(v, vr) and z == zr
+        assert np.array_equal(sim.forces(0), ref.forces(0))
+    # an explicit list build reorders the pair sums: graph and direct runs still agree
+    for sim in runs:
+        sim.build_neighbors()
+        sim.step(6)
+    ref.step(6)
+    xa, va, _, _ = runs[0].state(0)
+    xb, vb, _, _ = runs[1].state(0)
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    d = xa - ref.state(0)[0]   # the explicit build wrapped positions into the periodic box
+    L = rep.box_hi - rep.box_lo
+    d -= np.round(d / L) * L * (rep.periodic == 1)
+    assert np.abs(d).max() < 1e-3
+    for sim in runs + [ref]:
+        sim.close()
+
+
 def _uneven_replicas(n=5):
     reps = []
     for r, (nxy, nz, R, T) in enumerate([(6, 6, 5.0, 100.0), (9, 7, 6.0, 450.0), (7, 11, 5.5, 250.0),
