@@ -149,7 +149,7 @@ int clear_err(md_t *h)
 int forces_now(md_t *h, cudaStream_t s)
 {
     h->drift = false;   // the force kernel without Task 5 makes no drift
-    CU(launch_density(h->a, h->pot, h->cfg, s));
+    CU(launch_density(h->a, h->pot, h->cfg, 1, s));
     CU(launch_force(h->a, h->pot, h->cfg, 0, 1, s));
     CU(launch_reduce(h->a, h->cfg, s));
     return MD_OK;
@@ -252,11 +252,11 @@ int capture(md_t *h, int nsteps, bool first_full, bool last_energy, cudaGraphExe
             CU(cudaStreamWaitEvent(h->cap2, h->fork, 0));
             CU(launch_morse(h->a, h->pot, h->cap2));
             CU(cudaEventRecord(h->join, h->cap2));
-            CU(launch_density(h->a, h->pot, h->cfg, h->cap));
+            CU(launch_density(h->a, h->pot, h->cfg, en, h->cap));
             CU(cudaStreamWaitEvent(h->cap, h->join, 0));
             CU(launch_force_split(h->a, h->pot, h->cfg, 1, en, 0, h->cap));
         } else {
-            CU(launch_density(h->a, h->pot, h->cfg, h->cap));
+            CU(launch_density(h->a, h->pot, h->cfg, en, h->cap));
             CU(launch_force(h->a, h->pot, h->cfg, 1, en, h->cap));
         }
         CU(cudaStreamGetCaptureInfo(h->cap, &cs, nullptr, nullptr, &d, nullptr, &nd));
@@ -301,7 +301,7 @@ int step_direct(md_t *h, cudaEvent_t *ev, bool *rebuilt, bool energies)
     if (ev) CU(cudaEventRecord(ev[3], s));
     if (verlet) CU(launch_verlet1(h->a, s));
     if (ev) CU(cudaEventRecord(ev[4], s));
-    CU(launch_density(h->a, h->pot, h->cfg, s));
+    CU(launch_density(h->a, h->pot, h->cfg, energies ? 1 : 0, s));
     if (ev) CU(cudaEventRecord(ev[5], s));
     CU(launch_force(h->a, h->pot, h->cfg, 1, energies ? 1 : 0, s));
     if (ev) CU(cudaEventRecord(ev[6], s));
@@ -631,7 +631,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     CUI(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
     h->ev.resize(8);
     for (auto &e : h->ev) CUI(cudaEventCreate(&e));
-    h->unroll = real < 200000 ? 8 : 1;
+    h->unroll = 8;
 
     // ---- first list build and forces at t = 0
     INIT_FAIL(rebuild_growing(h));

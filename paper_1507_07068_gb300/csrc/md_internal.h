@@ -220,7 +220,8 @@ int md_build_pot(const md_params *p, PotDev *out, Cf64 **d_tabs64, float4 **d_ta
 cudaError_t launch_decide(const DevArgs &a, int mode, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s);
 cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s);
-cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c, cudaStream_t s);
+// energies = 0: the mixed-precision kernel leaves the embedding-energy partials alone
+cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int energies, cudaStream_t s);
 // energies = 0: the mixed-precision force kernel leaves the energy partials alone (k_reduce
 // must follow a launch with energies = 1); the FP64 one always writes them
 cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int energies,

@@ -396,18 +396,25 @@ __device__ __forceinline__ int buf_step(const DevArgs &a) { return (int)(*(volat
 __global__ void k_decide(DevArgs a, int mode, int use_cond, cudaGraphConditionalHandle h)
 {
     const int force = mode == DEC_BUILD;
-    const long long T = a.st->ph;   // buffer counter of the state this step starts from
+    // the status words first, all at once (this kernel is a chain of dependent memory
+    // accesses on the critical path of every step)
+    const DevStatus *stc = a.st;
+    const long long T = stc->ph;   // buffer counter of the state this step starts from
+    const long long since = stc->since_build;
+    const int drift_ok = stc->drift_ok, inner_next = stc->inner_ok_next;
+    const unsigned imax_next = stc->imax_next;
     const int bs = (int)(T & 1);
     int any = 0;
     for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) {
         RepState &S = a.rs[r];
-        double dmax = sqrt(__longlong_as_double((long long)S.d2b[bs]));
+        const unsigned long long d0 = S.d2b[0], d1 = S.d2b[1];
+        double dmax = sqrt(__longlong_as_double((long long)(bs ? d1 : d0)));
         S.d2b[bs] = 0ull;   // refilled by the force epilogue's drift to t + 2 dt
         int need;
         if (force) {
             need = 1;   // explicit build: no displacement test against a previous list
         } else if (a.rebuild_every > 0) {
-            need = a.st->since_build >= a.rebuild_every;
+            need = since >= a.rebuild_every;
             if (!need && 2.0 * dmax > a.skin) atomicOr(&a.st->err, MDE_SKIN);
         } else {
             need = (2.0 * dmax > a.skin) ||
@@ -439,11 +446,11 @@ __global__ void k_decide(DevArgs a, int mode, int use_cond, cudaGraphConditional
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
         const int run_verlet = mode == DEC_FULL || (mode == DEC_DRIFT && any);
-        if (mode == DEC_DRIFT && !any && !a.st->drift_ok) atomicOr(&a.st->err, MDE_SCHED);
+        if (mode == DEC_DRIFT && !any && !drift_ok) atomicOr(&a.st->err, MDE_SCHED);
         a.st->ph_cur = T;
         if (!force) { a.st->ph = T + 1; a.st->step += 1; }
-        a.st->inner_ok = a.st->inner_ok_next;   // a rebuild of the Verlet list below clears both
-        a.st->imax_bits = run_verlet ? 0u : a.st->imax_next;
+        a.st->inner_ok = inner_next;   // a rebuild of the Verlet list below clears both
+        a.st->imax_bits = run_verlet ? 0u : imax_next;
         a.st->imax_next = 0u;
         if (run_verlet)   // k_verlet1 fills the accumulator of the positions it makes
             for (int r = 0; r < a.n_rep; ++r) a.rs[r].d2b[bs ^ 1] = 0ull;
@@ -471,7 +478,12 @@ __global__ void k_zero_i32(int32_t *p, int n)
 __global__ void k_bin(DevArgs a)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s == 0) { a.st->max_cnt = 0; a.st->max_cntc = 0; a.st->n_cand = 0; a.st->n_near = 0; }
+    if (s == 0) {
+        // the list maxima describe the last build, unless an overflow is pending: then they
+        // keep the largest count since, which the error message reports
+        if (!(a.st->err & (MDE_OVERFLOW | MDE_COVERFLOW))) { a.st->max_cnt = 0; a.st->max_cntc = 0; }
+        a.st->n_cand = 0; a.st->n_near = 0;
+    }
     if (s >= a.S) return;
     int r = a.tile_rep[s / MD_TILE];
     const RepDev &R = a.rep[r];
@@ -1183,8 +1195,8 @@ __device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, flo
 }
 
 // Task 4a (Eqs. A2-A3): rho_i, P_i over the pairs within rc; F'(rho_i), M'(P_i) stored,
-// F(rho_i), M(P_i) into the CTA's energy partials.  MD_UNROLL entries per lane are loaded
-// (list entry, then position) before any is used.
+// and with EN F(rho_i), M(P_i) into the CTA's energy partials.  MD_UNROLL entries per lane
+// are loaded (list entry, then position) before any is used.
 //
 // The inner list (Sec. 2.6) holds the Verlet-list entries within rc + inner skin at its
 // last rebuild, in Verlet-list order.  Every pair within rc is in it while no atom has
@@ -1194,7 +1206,7 @@ __device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, flo
 // order, so the sums do not depend on which list a step uses.
 // The launch bound caps the kernel at 51 registers: with both loops in one kernel the
 // compiler otherwise takes 60-64 and the loss of occupancy costs ~10 %.
-template <int TPA, int IPOW>
+template <int TPA, int IPOW, bool EN>
 __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
 {
     __shared__ float4 sm_off[64];
@@ -1297,7 +1309,7 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
         a.fm32[s] = make_float2(Fp, Mp);
         acc[0] = F; acc[1] = M;
     }
-    cta_partials<2>(acc, a.part, a.max_blocks, blockIdx.x);
+    if (EN) cta_partials<2>(acc, a.part, a.max_blocks, blockIdx.x);
 }
 
 // Task 4b,c (Eq. (1) with the M term, Eqs. A6-A10; Morse Eqs. A5, A9) and Task 5 (the
@@ -1680,12 +1692,17 @@ cudaError_t launch_refresh_pos4(const DevArgs &a, cudaStream_t s)
 }
 
 template <int TPA>
-static void dens_t(const DevArgs &a, const PotDev &p, int block, cudaStream_t s)
+static void dens_t(const DevArgs &a, const PotDev &p, int block, int en, cudaStream_t s)
 {
     int A = block / TPA;
     if (a.mixed) {
-        if (p.q.ipow == 3) k_density_mixed<TPA, 3><<<a.S / A, block, 0, s>>>(a, p);   // beta = 6
-        else k_density_mixed<TPA, 0><<<a.S / A, block, 0, s>>>(a, p);
+        if (p.q.ipow == 3) {   // beta = 6
+            if (en) k_density_mixed<TPA, 3, true><<<a.S / A, block, 0, s>>>(a, p);
+            else k_density_mixed<TPA, 3, false><<<a.S / A, block, 0, s>>>(a, p);
+        } else {
+            if (en) k_density_mixed<TPA, 0, true><<<a.S / A, block, 0, s>>>(a, p);
+            else k_density_mixed<TPA, 0, false><<<a.S / A, block, 0, s>>>(a, p);
+        }
     }
     else {
         k_density_fp64<TPA><<<a.S / A, block, 0, s>>>(a, p);
@@ -1710,13 +1727,13 @@ static void force_t(const DevArgs &a, const PotDev &p, int block, int integ, int
     }
 }
 
-cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c, cudaStream_t s)
+cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int energies, cudaStream_t s)
 {
     switch (c.tpa) {
-    case 1: dens_t<1>(a, p, c.block, s); break;
-    case 2: dens_t<2>(a, p, c.block, s); break;
-    case 4: dens_t<4>(a, p, c.block, s); break;
-    default: dens_t<8>(a, p, c.block, s); break;
+    case 1: dens_t<1>(a, p, c.block, energies, s); break;
+    case 2: dens_t<2>(a, p, c.block, energies, s); break;
+    case 4: dens_t<4>(a, p, c.block, energies, s); break;
+    default: dens_t<8>(a, p, c.block, energies, s); break;
     }
     return cudaGetLastError();
 }
