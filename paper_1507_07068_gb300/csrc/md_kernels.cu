@@ -1179,9 +1179,9 @@ __device__ __forceinline__ float fa_val(const Pot32 &Q, float r2)
     return f_direct<IPOW>(Q, r2, r) - Q.f_rc - (r - Q.rc) * Q.df_rc;
 }
 
-// Phi beyond its double root (t > 0) is zero with its slope; t is clamped to 0 there,
-// where the Taylor form gives exactly 0 for both
-// f, f' and Phi' of a pair; Phi itself only when EN (the energies are wanted)
+// f, f' and Phi' of a pair, and Phi itself when EN (the energies are wanted).  Phi beyond
+// its double root (t > 0) is zero with its slope; t is clamped to 0 there, where the
+// Taylor form gives exactly 0 for both.
 template <int IPOW, bool EN>
 __device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, float &f, float &df, float &ph, float &dph)
 {
@@ -1306,17 +1306,18 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
         float F, Fp, M, Mp;
         Q.embed(rho, F, Fp);
         Q.mterm(Ps, M, Mp);
-        a.fm32[s] = make_float2(Fp, Mp);
+        a.fm32[s] = make_float2(Fp, 2.0f * Mp);   // (F', 2 M'): the force loop's factors
         acc[0] = F; acc[1] = M;
     }
     if (EN) cta_partials<2>(acc, a.part, a.max_blocks, blockIdx.x);
 }
 
 // Task 4b,c (Eq. (1) with the M term, Eqs. A6-A10; Morse Eqs. A5, A9) and Task 5 (the
-// closing half kick, FP64).  EN: the pair and Morse energies, the indenter load and the
-// kinetic energy into the CTA partials (only the last step of an md_step call needs them).  The force on i from j is coef * (x_j - x_i), coef = [(F'_i +
+// closing half kick, FP64).  The force on i from j is coef * (x_j - x_i), coef = [(F'_i +
 // F'_j) f' + (M'_i + M'_j) 2 f f' + Phi'] / r, over the inner list; its entries beyond rc
-// (~3 %) get weight 0 by a select (a branch on the distance measured 10 % slower).
+// (~3 %) drop out by a select (a branch on the distance measured 10 % slower).  EN: the
+// pair and Morse energies, the indenter load and the kinetic energy into the CTA partials
+// (only the last step of an md_step call needs them).
 template <int TPA, int IPOW, bool EN>
 __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int integrate)
 {
@@ -1364,18 +1365,19 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
                 disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 if ((e[u] & MD_J_MASK) != (unsigned)s) {   // padding is the atom itself
-                    // inner-list entries beyond rc (at most rc + inner skin) get weight 0:
-                    // their terms are finite and drop out exactly
-                    const float w = r2 < Q.rc2 ? 0.5f : 0.0f;
+                    // inner-list entries beyond rc (at most rc + inner skin) drop out by a
+                    // select: their terms are finite
+                    const bool in = r2 < Q.rc2;
                     const float rinv = rsqrt_nr(r2);
                     float f, df, ph, dph;
                     fa_phi<IPOW, EN>(Q, r2, rinv, f, df, ph, dph);
-                    const float coef = fmaf(fmi.x + fmj[u].x, df, fmaf((fmi.y + fmj[u].y) * 2.0f * f, df, dph)) * rinv;
-                    const float cw = coef * (w + w);
+                    // [(F'_i + F'_j) + 2 (M'_i + M'_j) f] f' + Phi', over r
+                    const float coef = fmaf(fmaf(fmi.y + fmj[u].y, f, fmi.x + fmj[u].x), df, dph) * rinv;
+                    const float cw = in ? coef : 0.0f;
                     gx = fmaf(cw, dx, gx);
                     gy = fmaf(cw, dy, gy);
                     gz = fmaf(cw, dz, gz);
-                    if (EN) ep = fmaf(w, ph, ep);
+                    if (EN) ep += in ? 0.5f * ph : 0.0f;
                 }
             }
         }
