@@ -58,6 +58,8 @@ struct md_handle {
     cudaStream_t cap = nullptr;          // private stream used only for graph capture
     cudaStream_t cap2 = nullptr;         // second capture stream: k_morse_mixed beside k_density
     cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t xfer = nullptr;         // md_set_state: the velocities' upload beside the list test
+    cudaEvent_t xev0 = nullptr, xev1 = nullptr;
     md_options opt{};
     md_params pot_h{};
     PotDev pot{};
@@ -146,10 +148,13 @@ int clear_err(md_t *h)
     return MD_OK;
 }
 
-int forces_now(md_t *h, cudaStream_t s)
+// density and forces at the current positions (no integration); before_force: an event the
+// force kernel waits for (it reads the velocities, for the kinetic energy)
+int forces_now(md_t *h, cudaStream_t s, cudaEvent_t before_force = nullptr)
 {
     h->drift = false;   // the force kernel without Task 5 makes no drift
     CU(launch_density(h->a, h->pot, h->cfg, 1, s));
+    if (before_force) CU(cudaStreamWaitEvent(s, before_force, 0));
     CU(launch_force(h->a, h->pot, h->cfg, 0, 1, s));
     CU(launch_reduce(h->a, h->cfg, s));
     return MD_OK;
@@ -342,6 +347,9 @@ void md_free(md_t *h)
     if (h->cap2) cudaStreamDestroy(h->cap2);
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->join) cudaEventDestroy(h->join);
+    if (h->xfer) { cudaStreamSynchronize(h->xfer); cudaStreamDestroy(h->xfer); }
+    if (h->xev0) cudaEventDestroy(h->xev0);
+    if (h->xev1) cudaEventDestroy(h->xev1);
     delete h;
 }
 
@@ -627,6 +635,9 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     }
     CUI(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     CUI(cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking));
+    CUI(cudaStreamCreateWithFlags(&h->xfer, cudaStreamNonBlocking));
+    CUI(cudaEventCreateWithFlags(&h->xev0, cudaEventDisableTiming));
+    CUI(cudaEventCreateWithFlags(&h->xev1, cudaEventDisableTiming));
     CUI(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
     CUI(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
     h->ev.resize(8);
@@ -774,13 +785,23 @@ int md_get_energy(md_t *h, int32_t r, md_energy *out)
     return MD_OK;
 }
 
-static int fetch(md_t *h, int32_t r, const double *s0, const double *s1, double *out3n)
+// queue the gather of one per-atom array of replica r into caller order (stage half `half`
+// of the staging buffer) and its copy to out3n; the caller synchronises
+static int fetch_async(md_t *h, int32_t r, const double *s0, const double *s1, double *out3n, int half)
 {
     const RepDev &R = h->rep[r];
     int n = R.n_atoms;
-    k_state_out<<<(n + 255) / 256, 256, 0, h->stream>>>(s0, s1, h->a.st, h->stage, h->a.orig, R.slot_off, n, h->a.S);
+    double *stage = h->stage + 3 * (size_t)n * half;
+    k_state_out<<<(n + 255) / 256, 256, 0, h->stream>>>(s0, s1, h->a.st, stage, h->a.orig, R.slot_off, n, h->a.S);
     CU(cudaGetLastError());
-    CU(cudaMemcpyAsync(out3n, h->stage, 3 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(out3n, stage, 3 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return MD_OK;
+}
+
+static int fetch(md_t *h, int32_t r, const double *s0, const double *s1, double *out3n)
+{
+    int rc = fetch_async(h, r, s0, s1, out3n, 0);
+    if (rc) return rc;
     CU(cudaStreamSynchronize(h->stream));
     return MD_OK;
 }
@@ -807,16 +828,18 @@ int md_get_state(md_t *h, int32_t r, double *x3n, double *v3n, double *z_ind, in
 {
     int rc = check_replica(h, r);
     if (rc) return rc;
-    if (x3n && (rc = fetch(h, r, h->a.xs[0], h->a.xs[1], x3n))) return rc;
-    if (v3n && (rc = fetch(h, r, h->a.v, h->a.v, v3n))) return rc;
+    // both gathers and copies queued, one synchronisation: the gather of v runs while x is
+    // on its way
+    if (x3n && (rc = fetch_async(h, r, h->a.xs[0], h->a.xs[1], x3n, 0))) return rc;
+    if (v3n && (rc = fetch_async(h, r, h->a.v, h->a.v, v3n, 1))) return rc;
+    RepState rs; DevStatus st;
     if (z_ind || step) {
-        RepState rs; DevStatus st;
         CU(cudaMemcpyAsync(&rs, h->a.rs + r, sizeof rs, cudaMemcpyDeviceToHost, h->stream));
         CU(cudaMemcpyAsync(&st, h->a.st, sizeof st, cudaMemcpyDeviceToHost, h->stream));
-        CU(cudaStreamSynchronize(h->stream));
-        if (z_ind) *z_ind = rs.z_ind;
-        if (step) *step = st.step;
     }
+    CU(cudaStreamSynchronize(h->stream));
+    if (z_ind) *z_ind = rs.z_ind;
+    if (step) *step = st.step;
     return MD_OK;
 }
 
@@ -827,19 +850,26 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     const RepDev &R = h->rep[r];
     int n = R.n_atoms;
     h->drift = false;   // k_state_zero voids the drift made from the old state
+    if (x3n) CU(cudaMemcpyAsync(h->stage, x3n, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    // The velocities go up on the transfer stream once the positions are up (one copy at a
+    // time fills the link) and the work queued before this call is done; the list test,
+    // the pair positions and the density, which do not read v, run meanwhile.  Every
+    // reader of v below waits for xev1.
+    CU(cudaEventRecord(h->xev0, h->stream));
+    if (v3n) {
+        double *st2 = h->stage + 3 * (size_t)n;
+        CU(cudaStreamWaitEvent(h->xfer, h->xev0, 0));
+        CU(cudaMemcpyAsync(st2, v3n, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->xfer));
+        k_state_in<<<(n + 255) / 256, 256, 0, h->xfer>>>(st2, h->a.v, h->a.v, h->a.st, h->a.orig, R.slot_off, n,
+                                                         h->a.S);
+        CU(cudaGetLastError());
+        CU(cudaEventRecord(h->xev1, h->xfer));
+    }
     if (x3n) {
-        CU(cudaMemcpyAsync(h->stage, x3n, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         k_state_in<<<(n + 255) / 256, 256, 0, h->stream>>>(h->stage, h->a.xs[0], h->a.xs[1], h->a.st, h->a.orig,
                                                            R.slot_off, n, h->a.S);
         CU(cudaGetLastError());
         CU(cudaMemsetAsync(&h->a.st->pos4_ok, 0, sizeof(int32_t), h->stream));   // pos4 is stale now
-    }
-    if (v3n) {
-        double *st2 = h->stage + 3 * (size_t)n;
-        CU(cudaMemcpyAsync(st2, v3n, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        k_state_in<<<(n + 255) / 256, 256, 0, h->stream>>>(st2, h->a.v, h->a.v, h->a.st, h->a.orig, R.slot_off, n,
-                                                           h->a.S);
-        CU(cudaGetLastError());
     }
     k_set_scalars<<<1, 1, 0, h->stream>>>(h->a.rs, r, z_ind, h->a.st, (long long)step, 1);
     CU(cudaGetLastError());
@@ -855,9 +885,12 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     int32_t need = 1;
     CU(cudaMemcpyAsync(&need, &h->a.st->any_rebuild, sizeof need, cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
-    if (need) return ensure_forces(h);
+    if (need) {   // the list build moves the velocities with the atoms
+        if (v3n) CU(cudaStreamWaitEvent(h->stream, h->xev1, 0));
+        return ensure_forces(h);
+    }
     CU(launch_refresh_pos4(h->a, h->stream));   // also the inner list's displacement test
-    if ((rc2 = forces_now(h, h->stream))) return rc2;
+    if ((rc2 = forces_now(h, h->stream, v3n ? h->xev1 : nullptr))) return rc2;
     DevStatus st;
     if ((rc2 = read_status(h, &st))) return rc2;
     if ((rc2 = status_to_code(h, st))) return rc2;
