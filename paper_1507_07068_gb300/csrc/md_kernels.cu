@@ -931,8 +931,8 @@ __global__ void k_build_done(DevArgs a)
 // displacement tests of x(t + dt): since the Verlet-list build (d2bits, for the rebuild
 // test; FP32 estimate from the cell-relative positions when it is below thr by more than
 // its error, else exact FP64) and, in mixed precision, since the inner-list build (ibits).
-// Fixed atoms keep x and v (they are copied).
-__device__ __forceinline__ void drift_atom(const DevArgs &a, const RepDev &R, int s, float thr,
+// Fixed atoms keep x and v (they are copied).  pc: the atom's cell at the last list build.
+__device__ __forceinline__ void drift_atom(const DevArgs &a, const RepDev &R, int s, int pc, float thr,
                                            double x0, double x1, double x2, double v0, double v1, double v2,
                                            double F0, double F1, double F2, double *xd, float4 *pd,
                                            unsigned long long &d2bits, unsigned &ibits)
@@ -947,7 +947,7 @@ __device__ __forceinline__ void drift_atom(const DevArgs &a, const RepDev &R, in
     xd[s] = x0; xd[S + s] = x1; xd[2 * S + s] = x2;
     bool exact = true;
     if (a.mixed) {
-        const float4 p = rel_pos3(a, R, a.cellc[s], x0, x1, x2);
+        const float4 p = rel_pos3(a, R, pc, x0, x1, x2);
         pd[s] = p;
         // same cell frame as the build's copy pb: a displacement clearly below thr cannot
         // change the rebuild test and its exact FP64 value is not needed
@@ -1008,7 +1008,7 @@ __global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
     if (s - R.slot_off < R.n_atoms) {
         const size_t S = a.S;
         const double *x = a.xs[bs];
-        drift_atom(a, R, s, a.rs[r].dthr, x[s], x[S + s], x[2 * S + s], a.v[s], a.v[S + s], a.v[2 * S + s],
+        drift_atom(a, R, s, a.cellc[s], a.rs[r].dthr, x[s], x[S + s], x[2 * S + s], a.v[s], a.v[S + s], a.v[2 * S + s],
                    a.F[s], a.F[S + s], a.F[2 * S + s], a.xs[bd], a.p4[bd], d2bits, ibits);
     }
     cta_max_disp(d2bits, ibits, &a.rs[r].d2b[bd], &a.st->imax_bits);
@@ -1138,6 +1138,12 @@ __device__ __forceinline__ void disp(const float4 &pi, const float4 &pj, unsigne
 }
 
 template <bool B> struct BoolC { static constexpr bool value = B; };
+
+// bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16); no registers, no wait
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 // The pair loops of the mixed path evaluate the forms of Eqs. A2 and A4 directly in FP32
 // (no table gather: at FP32 resolution a Hermite table adds nothing but 32 bytes of memory
@@ -1335,10 +1341,27 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
     float gx = 0.f, gy = 0.f, gz = 0.f, ep = 0.f;
     float mx = 0.f, my = 0.f, mz = 0.f, em = 0.f;
     const int bn = buf_step(a), bo = buf_cur(a);   // x(t + dt) in bn; x(t + 2 dt) goes to bo
+    if (integrate && threadIdx.x == 0 && (A & 1) == 0) {
+        // the epilogue's per-atom inputs of this CTA's atoms, on their way to L2 while the
+        // pair loop runs (A even: every range starts and ends on a 16-byte boundary)
+        const int s0 = blockIdx.x * A;
+        const size_t S = a.S;
+        for (int k = 0; k < 3; ++k) {
+            prefetch_l2(a.xs[bn] + k * S + s0, A * 8u);
+            prefetch_l2(a.vh + k * S + s0, A * 8u);
+        }
+        prefetch_l2(a.pb + s0, A * 16u);
+        prefetch_l2(a.pin + s0, A * 16u);
+    }
     const float4 *pp = a.p4[bn];
     const float4 pi = pp[s];
     const PairGeom G = pair_geom(R, __float_as_int(pi.w));
     const bool per = __any_sync(0xffffffffu, real && G.xmask != 0u);
+    if (TPA == 1) {   // this warp's inner-list rows (32 atoms: 128 B per row) on their way to L2
+        const int nmax = __reduce_max_sync(0xffffffffu, real ? a.icnt[s] : 0);
+        const int sw = s & ~31;
+        for (int k = threadIdx.x & 31; k < nmax; k += 32) prefetch_l2(a.inner + (size_t)k * S + sw, 128u);
+    }
     auto work = [&](auto PERC) {
         constexpr bool PER = decltype(PERC)::value;
         if (!real) return;
@@ -1419,7 +1442,7 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
             // bo, its rebuild test for the next k_decide but one, its inner-list test for
             // the next k_density.  The next k_decide keeps it unless it rebuilds the lists.
             const double *x = a.xs[bn];
-            drift_atom(a, R, s, a.rs[r].dthr2, x[s], x[S + s], x[2 * S + s], vx, vy, vz, Fx, Fy, Fz,
+            drift_atom(a, R, s, __float_as_int(pi.w), a.rs[r].dthr2, x[s], x[S + s], x[2 * S + s], vx, vy, vz, Fx, Fy, Fz,
                        a.xs[bo], a.p4[bo], d2bits, ibits);
         } else {
             vx = a.v[s]; vy = a.v[S + s]; vz = a.v[2 * S + s];
