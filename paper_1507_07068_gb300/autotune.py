@@ -46,7 +46,7 @@ def _time_steps(sim: "md.MD", warmup: int, steps: int) -> float:
 
 def autotune(replicas: Sequence, params: Optional[dict] = None, precision: str = "mixed",
              shapes: Iterable[Tuple[int, int]] = ((1, 64), (1, 128), (2, 128), (4, 128)),
-             skins: Iterable[float] = (0.3, 0.6, 1.0), steps: int = 60, warmup: int = 5,
+             skins: Iterable[float] = (0.3, 0.6, 1.0, 1.1), steps: int = 60, warmup: int = 5,
              base_skin: float = 0.3,
              interval_safety: float = 0.7, log=None) -> Tuned:
     """Time each (tpa, block) at base_skin, then each skin with the best shape, then

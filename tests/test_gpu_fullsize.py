@@ -12,7 +12,7 @@ from gpu_helpers import rel_force_err
 
 pytestmark = pytest.mark.gpu
 
-SKIN = 1.0   # the Verlet skin of the benchmark's configuration
+SKIN = 1.1   # the Verlet skin of the benchmark's configuration
 
 
 @pytest.fixture(scope="module")
