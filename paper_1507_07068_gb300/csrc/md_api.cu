@@ -545,6 +545,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     INIT_FAIL(dalloc(h, &a.sorig, S));
     INIT_FAIL(dalloc(h, &a.sfixed, S));
     INIT_FAIL(dalloc(h, &a.part, 6 * (size_t)a.max_blocks));
+    INIT_FAIL(dalloc(h, &a.rsum, 6 * (size_t)MD_RED_CHUNKS * n_replicas));
     double *d_xc0; int32_t *d_ccs, *d_ccc;
     float4 *d_xc32;
     INIT_FAIL(dalloc(h, &d_xc0, 3 * (size_t)(cslots > 0 ? cslots : 1)));

@@ -24,6 +24,7 @@
 #include "../../include/md.h"
 
 #define MD_TILE 128          // slots per tile; a CTA of the per-atom kernels covers <= one tile
+#define MD_RED_CHUNKS 128    // k_reduce: CTAs per replica, each summing a contiguous run of CTA partials
 #define MD_ACC 9.6485332e-3  // 1 eV/(A u) in A/fs^2
 #define MD_KB 8.617333262e-5 // Boltzmann constant, eV/K
 #define MD_CELL_BITS 10      // bits per packed cell coordinate (grids up to 1024 cells per axis)
@@ -127,7 +128,7 @@ struct RepState {
     int32_t need;                        // rebuild decided for this step
     float dthr, dthr2;                   // mixed: displacements below these (A) cannot decide the rebuild
                                          // test of the positions k_verlet1 / the force epilogue produce
-    int32_t pad;
+    int32_t rctr;                        // k_reduce: chunks of this replica summed so far (0 between calls)
 };
 
 // energies of one replica (device copy of md_energy's sums)
@@ -205,6 +206,7 @@ struct DevArgs {
     int32_t C;
     // block partial sums: [6][max_blocks]
     double *part;
+    double *rsum;                        // k_reduce scratch: [n_rep][MD_RED_CHUNKS][6] chunk sums
     int32_t max_blocks;
 };
 

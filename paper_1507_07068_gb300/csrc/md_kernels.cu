@@ -1634,31 +1634,69 @@ __global__ void __launch_bounds__(256) k_force_fp64(DevArgs a, PotDev P, int int
     cta_partials<4>(acc, a.part + 2 * (size_t)a.max_blocks, a.max_blocks, blockIdx.x);
 }
 
-// per-replica sums of the CTA partials, fixed order: thread t adds blocks t, t+B, ...;
-// then a fixed tree over threads (one CTA per replica, one term at a time)
-__global__ void __launch_bounds__(1024) k_reduce(DevArgs a, int atoms_per_block)
+// per-replica sums of the CTA partials in a fixed order.  MD_RED_CHUNKS CTAs per replica
+// each sum a contiguous run of the partials (thread t adds blocks t, t + B, ... of all six
+// terms together; the lanes of a warp by a fixed shuffle tree; thread 0 the warp sums in
+// warp order) into rsum; the CTA that finishes last (a counter per replica, after a fence)
+// adds the chunk sums in chunk order and resets the counter.  Which CTA finishes last does
+// not change a bit of the result.
+__global__ void __launch_bounds__(64) k_reduce(DevArgs a, int atoms_per_block)
 {
-    int r = blockIdx.x;
+    const int r = blockIdx.y, ch = blockIdx.x, nch = gridDim.x;
     const RepDev &R = a.rep[r];
-    int b0 = R.slot_off / atoms_per_block, b1 = (R.slot_off + R.n_slots) / atoms_per_block;
-    __shared__ double sm[1024];
-    double out[6];
-    for (int t = 0; t < 6; ++t) {
-        double acc = 0.0;
-        for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) acc += a.part[(size_t)t * a.max_blocks + b];
-        sm[threadIdx.x] = acc;
-        __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
-            __syncthreads();
-        }
-        out[t] = sm[0];
-        __syncthreads();
+    const int b0 = R.slot_off / atoms_per_block, b1 = (R.slot_off + R.n_slots) / atoms_per_block;
+    const int per = (b1 - b0 + nch - 1) / nch;
+    const int c0 = min(b1, b0 + ch * per), c1 = min(b1, c0 + per);
+    const size_t stride = (size_t)a.max_blocks;
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = c0 + threadIdx.x; b < c1; b += blockDim.x) {
+#pragma unroll
+        for (int t = 0; t < 6; ++t) acc[t] += a.part[t * stride + b];
     }
+#pragma unroll
+    for (int t = 0; t < 6; ++t)
+        for (int o = 16; o > 0; o >>= 1) acc[t] += __shfl_down_sync(0xffffffffu, acc[t], o);
+    __shared__ double sm[32][6];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int t = 0; t < 6; ++t) sm[wid][t] = acc[t];
+    }
+    __syncthreads();
+    double *mine = a.rsum + ((size_t)r * nch + ch) * 6;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += sm[w][t];
+            mine[t] = s;
+        }
+        __threadfence();   // the chunk sums are visible before the count says so
+        last = atomicAdd(&a.rs[r].rctr, 1) == nch - 1;
+    }
+    __syncthreads();
+    if (!last) return;   // CTA-uniform
+    __threadfence();
+    // the chunk sums (read past L1, where another CTA's writes are not) into shared memory
+    // by many threads at once, then added in chunk order
+    __shared__ double cs[MD_RED_CHUNKS * 6];
+    const double *all = a.rsum + (size_t)r * nch * 6;
+    for (int i = threadIdx.x; i < nch * 6; i += blockDim.x) cs[i] = __ldcg(&all[i]);
+    __syncthreads();
+    __shared__ double out[6];
+    if (threadIdx.x < 6) {   // one thread per term (FP64 adds are slow on this part: in parallel)
+        const int t = threadIdx.x;
+        double s = 0.0;
+        for (int k = 0; k < nch; ++k) s += cs[k * 6 + t];
+        out[t] = s;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         RepEnergy &E = a.en[r];
         E.embed = out[0]; E.mterm = out[1]; E.pair = out[2]; E.morse = out[3];
         E.load = out[4]; E.kinetic = out[5];
+        a.rs[r].rctr = 0;
     }
 }
 
@@ -1790,7 +1828,7 @@ cudaError_t launch_force_split(const DevArgs &a, const PotDev &p, const LaunchCf
 
 cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
-    k_reduce<<<a.n_rep, 1024, 0, s>>>(a, c.block / c.tpa);
+    k_reduce<<<dim3(MD_RED_CHUNKS, a.n_rep), 64, 0, s>>>(a, c.block / c.tpa);
     return cudaGetLastError();
 }
 
