@@ -53,6 +53,15 @@ __global__ void k_set_scalars(RepState *rs, int r, double z_ind, DevStatus *st, 
 
 }  // namespace
 
+// small device-to-host readbacks land in pinned memory (a copy into pageable memory goes
+// through a driver bounce buffer and costs more than the copy itself)
+struct HostPin {
+    DevStatus st;
+    RepEnergy E;
+    RepState rs;
+    int32_t flag, verlet;
+};
+
 struct md_handle {
     cudaStream_t stream = nullptr;       // caller's stream
     cudaStream_t cap = nullptr;          // private stream used only for graph capture
@@ -79,6 +88,7 @@ struct md_handle {
     cudaGraphExec_t exec1 = nullptr, execU = nullptr, execE = nullptr;
     cudaGraphExec_t execF = nullptr, execFE = nullptr;
     bool drift = false;   // mixed: the last force kernel made the next step's Task 3 (mirrors drift_ok)
+    HostPin *hp = nullptr;
     int unroll = 1;
     bool forces_valid = false;
     std::vector<cudaEvent_t> ev;
@@ -127,8 +137,9 @@ int cu_check(md_t *h, cudaError_t e, const char *what)
 
 int read_status(md_t *h, DevStatus *st)
 {
-    CU(cudaMemcpyAsync(st, h->a.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&h->hp->st, h->a.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
+    *st = h->hp->st;
     return MD_OK;
 }
 
@@ -297,10 +308,10 @@ int step_direct(md_t *h, cudaEvent_t *ev, bool *rebuilt, bool energies)
     if (ev) CU(cudaEventRecord(ev[0], s));
     CU(launch_decide(h->a, h->drift ? DEC_DRIFT : DEC_FULL, 0, 0, s));
     if (ev) CU(cudaEventRecord(ev[1], s));
-    int32_t flag = 0, verlet = 1;
-    CU(cudaMemcpyAsync(&flag, &h->a.st->any_rebuild, sizeof flag, cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(&verlet, &h->a.st->run_verlet, sizeof verlet, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(&h->hp->flag, &h->a.st->any_rebuild, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(&h->hp->verlet, &h->a.st->run_verlet, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    const int32_t flag = h->hp->flag, verlet = h->hp->verlet;
     if (ev) CU(cudaEventRecord(ev[2], s));
     if (flag) CU(launch_rebuild(h->a, s));
     if (ev) CU(cudaEventRecord(ev[3], s));
@@ -350,6 +361,7 @@ void md_free(md_t *h)
     if (h->xfer) { cudaStreamSynchronize(h->xfer); cudaStreamDestroy(h->xfer); }
     if (h->xev0) cudaEventDestroy(h->xev0);
     if (h->xev1) cudaEventDestroy(h->xev1);
+    if (h->hp) cudaFreeHost(h->hp);
     delete h;
 }
 
@@ -641,6 +653,8 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     CUI(cudaEventCreateWithFlags(&h->xev1, cudaEventDisableTiming));
     CUI(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
     CUI(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
+    CUI(cudaHostAlloc((void **)&h->hp, sizeof(HostPin), cudaHostAllocDefault));
+    memset(h->hp, 0, sizeof(HostPin));
     h->ev.resize(8);
     for (auto &e : h->ev) CUI(cudaEventCreate(&e));
     h->unroll = 8;
@@ -767,11 +781,13 @@ int md_get_energy(md_t *h, int32_t r, md_energy *out)
     int rc = check_replica(h, r);
     if (rc) return rc;
     if (!out) return fail(h, MD_ERR_ARG, "md_get_energy: null output");
-    RepEnergy E; DevStatus st; RepState rs;
-    CU(cudaMemcpyAsync(&E, h->a.en + r, sizeof E, cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaMemcpyAsync(&rs, h->a.rs + r, sizeof rs, cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaMemcpyAsync(&st, h->a.st, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&h->hp->E, h->a.en + r, sizeof(RepEnergy), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&h->hp->rs, h->a.rs + r, sizeof(RepState), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&h->hp->st, h->a.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
+    const RepEnergy E = h->hp->E;
+    const RepState rs = h->hp->rs;
+    const DevStatus st = h->hp->st;
     const RepDev &R = h->rep[r];
     out->embed = E.embed; out->pair = E.pair; out->mterm = E.mterm; out->morse = E.morse;
     out->kinetic = E.kinetic;
@@ -833,14 +849,13 @@ int md_get_state(md_t *h, int32_t r, double *x3n, double *v3n, double *z_ind, in
     // on its way
     if (x3n && (rc = fetch_async(h, r, h->a.xs[0], h->a.xs[1], x3n, 0))) return rc;
     if (v3n && (rc = fetch_async(h, r, h->a.v, h->a.v, v3n, 1))) return rc;
-    RepState rs; DevStatus st;
     if (z_ind || step) {
-        CU(cudaMemcpyAsync(&rs, h->a.rs + r, sizeof rs, cudaMemcpyDeviceToHost, h->stream));
-        CU(cudaMemcpyAsync(&st, h->a.st, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaMemcpyAsync(&h->hp->rs, h->a.rs + r, sizeof(RepState), cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaMemcpyAsync(&h->hp->st, h->a.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
     }
     CU(cudaStreamSynchronize(h->stream));
-    if (z_ind) *z_ind = rs.z_ind;
-    if (step) *step = st.step;
+    if (z_ind) *z_ind = h->hp->rs.z_ind;
+    if (step) *step = h->hp->st.step;
     return MD_OK;
 }
 
@@ -883,9 +898,9 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     int rc2 = clear_err(h);
     if (rc2) return rc2;
     CU(launch_state_check(h->a, h->stream));
-    int32_t need = 1;
-    CU(cudaMemcpyAsync(&need, &h->a.st->any_rebuild, sizeof need, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&h->hp->flag, &h->a.st->any_rebuild, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
+    const int32_t need = h->hp->flag;
     if (need) {   // the list build moves the velocities with the atoms
         if (v3n) CU(cudaStreamWaitEvent(h->stream, h->xev1, 0));
         return ensure_forces(h);
