@@ -44,13 +44,6 @@ __global__ void k_state_out(const double *s0, const double *s1, const DevStatus 
     for (int k = 0; k < 3; ++k) stage[3 * (size_t)o + k] = src[k * S + s];
 }
 
-// z_build is kept: the list test of md_set_state compares z_ind with it
-__global__ void k_set_scalars(RepState *rs, int r, double z_ind, DevStatus *st, long long step, int set_step)
-{
-    rs[r].z_ind = z_ind;
-    if (set_step) st->step = step;
-}
-
 }  // namespace
 
 // small device-to-host readbacks land in pinned memory (a copy into pageable memory goes
@@ -865,7 +858,7 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     if (rc) return rc;
     const RepDev &R = h->rep[r];
     int n = R.n_atoms;
-    h->drift = false;   // k_state_zero voids the drift made from the old state
+    h->drift = false;   // k_state_prep voids the drift made from the old state
     if (x3n) CU(cudaMemcpyAsync(h->stage, x3n, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     // The velocities go up on the transfer stream once the positions are up (one copy at a
     // time fills the link) and the work queued before this call is done; the list test,
@@ -881,23 +874,13 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
         CU(cudaGetLastError());
         CU(cudaEventRecord(h->xev1, h->xfer));
     }
-    if (x3n) {
-        k_state_in<<<(n + 255) / 256, 256, 0, h->stream>>>(h->stage, h->a.xs[0], h->a.xs[1], h->a.st, h->a.orig,
-                                                           R.slot_off, n, h->a.S);
-        CU(cudaGetLastError());
-        CU(cudaMemsetAsync(&h->a.st->pos4_ok, 0, sizeof(int32_t), h->stream));   // pos4 is stale now
-    }
-    k_set_scalars<<<1, 1, 0, h->stream>>>(h->a.rs, r, z_ind, h->a.st, (long long)step, 1);
-    CU(cudaGetLastError());
     h->forces_valid = false;
     // The lists stay valid when the new state passes the rebuild test md_step applies
-    // (max |x - x_build| and the indenter's travel against the skin): then only the
-    // cell-relative positions are refreshed (and the inner list rebuilt if its own test
-    // fails).  Otherwise (or when positions leave their periodic image, become NaN, ...)
-    // a full rebuild.
-    int rc2 = clear_err(h);
-    if (rc2) return rc2;
-    CU(launch_state_check(h->a, h->stream));
+    // (max |x - x_build| and the indenter's travel against the skin): the positions, their
+    // pos4 and both displacement tests come out of one pass, and the inner list is rebuilt
+    // by the density pass if its own test fails.  Otherwise (or when positions leave their
+    // periodic image, become NaN, ...) a full rebuild.
+    CU(launch_state_set(h->a, r, R.slot_off, n, z_ind, (long long)step, x3n ? h->stage : nullptr, h->stream));
     CU(cudaMemcpyAsync(&h->hp->flag, &h->a.st->any_rebuild, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     const int32_t need = h->hp->flag;
@@ -905,7 +888,7 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
         if (v3n) CU(cudaStreamWaitEvent(h->stream, h->xev1, 0));
         return ensure_forces(h);
     }
-    CU(launch_refresh_pos4(h->a, h->stream));   // also the inner list's displacement test
+    int rc2;
     if ((rc2 = forces_now(h, h->stream, v3n ? h->xev1 : nullptr))) return rc2;
     DevStatus st;
     if ((rc2 = read_status(h, &st))) return rc2;

@@ -151,6 +151,8 @@ struct DevStatus {
     int32_t inner_ok_next;  // set by the k_density that rebuilt it; k_decide moves it over
     int32_t drift_ok;       // mixed: the force epilogue already made the next step's Tasks 2-3
     int32_t run_verlet;     // k_verlet1 runs this step (a rebuild, or a step launched as DEC_FULL)
+    int32_t imax_fresh;     // the last k_density rebuilt the inner list: every atom's displacement
+                            // since is 0 at the positions it used (imax_bits is then stale)
     int64_t step, rebuilds, since_build;
     // position buffers xs[], p4[] in use: the state is in buffer ph & 1 (during a step, from
     // k_decide on, the positions the pair kernels evaluate); the state a step started from
@@ -233,9 +235,13 @@ cudaError_t launch_morse(const DevArgs &a, const PotDev &p, cudaStream_t s);
 cudaError_t launch_force_split(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int energies,
                                int with_morse, cudaStream_t s);
 cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s);
-cudaError_t launch_refresh_pos4(const DevArgs &a, cudaStream_t s);
-// d2max of every replica at the current positions and any_rebuild by the displacement rule
-cudaError_t launch_state_check(const DevArgs &a, cudaStream_t s);
+// md_set_state for replica r (n atoms from slot slot_off): clear the error word, set z_ind
+// and the step count, then (stage = new positions in caller order, or NULL to keep them)
+// store the positions, their pos4, the exact displacement test against the last build
+// (d2b of replica r) and the inner list's displacement test, then any_rebuild by the
+// displacement rule over every replica
+cudaError_t launch_state_set(const DevArgs &a, int r, int slot_off, int n, double z_ind, long long step,
+                             const double *stage, cudaStream_t s);
 
 // ---- allocation-free small-system evaluation (md_forces_small): all pairs, FP64 forms
 enum { MD_SMALL_BLOCK = 128, MD_SMALL_MAX_BLOCKS = MD_SMALL_MAX_ATOMS / MD_SMALL_BLOCK };

@@ -1014,34 +1014,67 @@ __global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
     cta_max_disp(d2bits, ibits, &a.rs[r].d2b[bd], &a.st->imax_bits);
 }
 
-// List test after positions were replaced (md_set_state): exact FP64 max |x - x_build|^2
-// per replica of the state positions (buffer ph & 1), where k_decide looks for it, then
-// k_state_need applies the displacement rule of k_decide (whatever the rebuild mode: the
-// caller's positions are not integrator steps) and raises any_rebuild.
-__global__ void __launch_bounds__(MD_TILE) k_state_disp(DevArgs a)
+// md_set_state, before the new positions: the error word cleared, replica r's indenter
+// displacement and the step count set, its accumulator for the rebuild test of the state
+// positions zeroed, the drift made from the old state voided.  The inner list's
+// displacement max keeps the other replicas' current values (their positions do not
+// change) unless the last k_density rebuilt that list, which makes them all 0.
+__global__ void k_state_prep(DevArgs a, int r, double z_ind, long long step)
 {
-    const int s = blockIdx.x * MD_TILE + threadIdx.x;
-    const int r = a.tile_rep[blockIdx.x];
+    if (threadIdx.x != 0) return;
+    DevStatus *st = a.st;
+    st->err = 0;
+    st->step = step;
+    st->drift_ok = 0;
+    st->inner_ok = st->inner_ok_next;
+    if (st->imax_fresh) st->imax_bits = 0u;
+    st->pos4_ok = a.mixed;   // FP64: the other replicas' pos4 are not kept current
+    RepState &S = a.rs[r];
+    S.z_ind = z_ind;
+    S.d2b[st->ph & 1] = 0ull;
+}
+
+// md_set_state for the n atoms of replica r (slots slot_off ...): the new positions (from
+// stage in caller order, or the current ones when stage is NULL) into the state buffer,
+// their pos4, the exact FP64 max |x - x_build|^2 (as the drift reduces it for k_decide)
+// and, in mixed precision, the displacement since the inner list was built.
+__global__ void __launch_bounds__(256) k_state_scan(DevArgs a, int r, int slot_off, int n, const double *stage)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const RepDev &R = a.rep[r];
     const int b = buf_step(a);
     unsigned long long d2bits = 0ull;
-    if (s - R.slot_off < R.n_atoms) {
+    unsigned ibits = 0u;
+    if (i < n) {
         const size_t S = a.S;
-        const double *x = a.xs[b];
-        double d2 = norm2_exact(__dsub_rn(x[s], a.xb[s]), __dsub_rn(x[S + s], a.xb[S + s]),
-                                __dsub_rn(x[2 * S + s], a.xb[2 * S + s]));
-        if (d2 != d2) d2 = 1e300;
+        const int s = slot_off + i;
+        double *x = a.xs[b];
+        double x0, x1, x2;
+        if (stage) {
+            const int o = a.orig[s];
+            x0 = stage[3 * (size_t)o]; x1 = stage[3 * (size_t)o + 1]; x2 = stage[3 * (size_t)o + 2];
+            x[s] = x0; x[S + s] = x1; x[2 * S + s] = x2;
+        } else {
+            x0 = x[s]; x1 = x[S + s]; x2 = x[2 * S + s];
+        }
+        const float4 p = rel_pos3(a, R, a.cellc[s], x0, x1, x2);
+        a.p4[b][s] = p;
+        double d2 = norm2_exact(__dsub_rn(x0, a.xb[s]), __dsub_rn(x1, a.xb[S + s]), __dsub_rn(x2, a.xb[2 * S + s]));
+        if (d2 != d2) d2 = 1e300;   // NaN position: force a rebuild, which reports it
         d2bits = (unsigned long long)__double_as_longlong(d2);
+        if (a.mixed) {
+            const float4 q = a.pin[s];
+            const float ex = p.x - q.x, ey = p.y - q.y, ez = p.z - q.z;
+            float dm2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            if (!(dm2 <= 1e30f)) dm2 = 1e30f;
+            ibits = __float_as_uint(dm2);
+        }
     }
-    cta_max_disp(d2bits, 0u, &a.rs[r].d2b[b], &a.st->imax_bits);
+    cta_max_disp(d2bits, ibits, &a.rs[r].d2b[b], &a.st->imax_bits);
 }
 
-__global__ void k_state_zero(DevArgs a)
-{
-    for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) { a.rs[r].d2b[0] = 0ull; a.rs[r].d2b[1] = 0ull; }
-    if (threadIdx.x == 0) { a.st->imax_bits = 0u; a.st->imax_next = 0u; a.st->drift_ok = 0; }
-}
-
+// the displacement rule of k_decide on every replica's state positions (whatever the
+// rebuild mode: the caller's positions are not integrator steps), into any_rebuild
 __global__ void k_state_need(DevArgs a)
 {
     const int b = buf_step(a);
@@ -1054,32 +1087,6 @@ __global__ void k_state_need(DevArgs a)
     }
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) a.st->any_rebuild = any;
-}
-
-// pos4 of every atom about its cell's centre at the state positions (buffer ph & 1, cells
-// of the last build), and, in mixed precision, the displacement since the inner list was
-// built (as k_verlet1 reduces it): the next k_density keeps that list if it is still valid.
-// imax_bits must be zero on entry (k_state_zero).  A drift made from the earlier state is void.
-__global__ void __launch_bounds__(MD_TILE) k_refresh_pos4(DevArgs a)
-{
-    const int s = blockIdx.x * MD_TILE + threadIdx.x;
-    if (s == 0) { a.st->pos4_ok = 1; a.st->inner_ok = a.st->inner_ok_next; a.st->drift_ok = 0; }
-    const RepDev &R = a.rep[a.tile_rep[blockIdx.x]];
-    const int b = buf_step(a);
-    unsigned ibits = 0u;
-    if (s - R.slot_off < R.n_atoms) {
-        const float4 p = rel_pos(a, R, a.xs[b], s);
-        a.p4[b][s] = p;
-        if (a.mixed) {
-            const float4 q = a.pin[s];
-            const float ex = p.x - q.x, ey = p.y - q.y, ez = p.z - q.z;
-            float dm2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-            if (!(dm2 <= 1e30f)) dm2 = 1e30f;
-            ibits = __float_as_uint(dm2);
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) ibits = max(ibits, __shfl_xor_sync(0xffffffffu, ibits, o));
-    if ((threadIdx.x & 31) == 0 && ibits) atomicMax(&a.st->imax_bits, ibits);
 }
 
 // ============================================================================ Task 4, mixed precision
@@ -1306,7 +1313,10 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
         for (int k = m; k < mmax; ++k) a.inner[(size_t)(k * TPA + lane) * S + s] = s;
         if (lane == 0) a.icnt[s] = mmax * TPA;
     }
-    if (rebuild && blockIdx.x == 0 && threadIdx.x == 0) a.st->inner_ok_next = 1;   // read by the next k_decide
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (rebuild) a.st->inner_ok_next = 1;   // read by the next k_decide
+        a.st->imax_fresh = rebuild;
+    }
     float acc[2] = {0.f, 0.f};
     if (real && lane == 0) {
         float F, Fp, M, Mp;
@@ -1740,17 +1750,12 @@ cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_state_check(const DevArgs &a, cudaStream_t s)
+cudaError_t launch_state_set(const DevArgs &a, int r, int slot_off, int n, double z_ind, long long step,
+                             const double *stage, cudaStream_t s)
 {
-    k_state_zero<<<1, 256, 0, s>>>(a);
-    k_state_disp<<<a.S / MD_TILE, MD_TILE, 0, s>>>(a);
+    k_state_prep<<<1, 32, 0, s>>>(a, r, z_ind, step);
+    if (n > 0) k_state_scan<<<nblk(n, 256), 256, 0, s>>>(a, r, slot_off, n, stage);
     k_state_need<<<1, 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_refresh_pos4(const DevArgs &a, cudaStream_t s)
-{
-    k_refresh_pos4<<<a.S / MD_TILE, MD_TILE, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -406,6 +406,33 @@ def test_state_roundtrip(md, params):
     assert np.abs(d).max() < 1e-10
 
 
+def test_set_state_of_one_replica_in_a_batch(md, params):
+    """md_set_state on one replica of a batch: its new positions get the oracle's forces,
+    and the other replicas, whose state is unchanged, step on exactly as in a batch that
+    was never interrupted (no list rebuild: the change is within the skin)."""
+    import dataclasses
+    reps = _uneven_replicas(3)
+    a = md.MD(reps, params, precision="mixed", skin=1.1)   # no rebuild in either run
+    b = md.MD(reps, params, precision="mixed", skin=1.1)
+    a.step(12); b.step(12)
+    x, v, z, st = a.state(1)
+    nreb = a.energy(1)["rebuilds"]
+    rng = np.random.default_rng(11)
+    x1 = x + rng.uniform(-0.02, 0.02, x.shape)
+    a.set_state(1, x1, v, z, st)
+    assert a.energy(1)["rebuilds"] == nreb
+    o = oracle_eval(params, dataclasses.replace(reps[1], x_cr=x1), z_ind=z)
+    assert rel_force_err(a.forces(1), o["F"]).max() <= MIXED_TOL
+    a.step(9); b.step(9)
+    for r in (0, 2):
+        xa, va, za, sa = a.state(r)
+        xb, vb, zb, sb = b.state(r)
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb) and za == zb and sa == sb
+        assert np.array_equal(a.forces(r), b.forces(r))
+    assert np.isfinite(a.state(1)[0]).all()
+    a.close(); b.close()
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("mixed", MIXED_TOL)])
 def test_set_state_keeps_or_rebuilds_lists(md, params, precision, tol):
     """Positions replaced within the skin rule keep the lists (no rebuild counted) and give
