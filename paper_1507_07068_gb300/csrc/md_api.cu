@@ -152,14 +152,17 @@ int clear_err(md_t *h)
     return MD_OK;
 }
 
-// density and forces at the current positions (no integration); before_force: an event the
-// force kernel waits for (it reads the velocities, for the kinetic energy)
+// density and forces at the current positions (no integration); in mixed precision the force
+// kernel also makes the next step's drift from this state, so that the next step needs no
+// k_verlet1.  before_force: an event the force kernel waits for (it reads the velocities)
 int forces_now(md_t *h, cudaStream_t s, cudaEvent_t before_force = nullptr)
 {
-    h->drift = false;   // the force kernel without Task 5 makes no drift
+    const bool mixed = h->a.mixed != 0;
+    if (mixed) CU(launch_drift_prep(h->a, s));
     CU(launch_density(h->a, h->pot, h->cfg, 1, s));
     if (before_force) CU(cudaStreamWaitEvent(s, before_force, 0));
-    CU(launch_force(h->a, h->pot, h->cfg, 0, 1, s));
+    CU(launch_force(h->a, h->pot, h->cfg, mixed ? 2 : 0, 1, s));
+    h->drift = mixed;
     CU(launch_reduce(h->a, h->cfg, s));
     return MD_OK;
 }

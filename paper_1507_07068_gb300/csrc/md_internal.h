@@ -235,6 +235,9 @@ cudaError_t launch_morse(const DevArgs &a, const PotDev &p, cudaStream_t s);
 cudaError_t launch_force_split(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int energies,
                                int with_morse, cudaStream_t s);
 cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s);
+// before a force pass with integrate = 2 (mixed precision): thresholds and accumulators of
+// the drift it makes
+cudaError_t launch_drift_prep(const DevArgs &a, cudaStream_t s);
 // md_set_state for replica r (n atoms from slot slot_off): clear the error word, set z_ind
 // and the step count, then (stage = new positions in caller order, or NULL to keep them)
 // store the positions, their pos4, the exact displacement test against the last build

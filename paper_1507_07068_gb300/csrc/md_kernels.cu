@@ -1014,6 +1014,28 @@ __global__ void __launch_bounds__(MD_TILE) k_verlet1(DevArgs a)
     cta_max_disp(d2bits, ibits, &a.rs[r].d2b[bd], &a.st->imax_bits);
 }
 
+// Before a force pass that drifts a state set from outside (integrate = 2): per replica
+// the threshold below which the displacement of the drifted positions cannot decide the
+// rebuild test that examines them (as k_decide sets it when it advances a step, with the
+// lists of the last build), and the accumulators of that test and of the inner list's
+// test cleared.
+__global__ void k_drift_prep(DevArgs a)
+{
+    const int b = (int)((a.st->ph + 1) & 1);
+    for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) {
+        RepState &S = a.rs[r];
+        const RepDev &Rr = a.rep[r];
+        double T1 = 0.5 * a.skin;
+        if (a.rebuild_every == 0 && Rr.n_c > 0) {
+            const double z1 = __dadd_rn(S.z_ind, __dmul_rn(Rr.v_ind, Rr.dt));
+            T1 = fmin(T1, a.skin - fabs(z1 - S.z_build));
+        }
+        S.dthr = (float)(T1 - 1e-5);
+        S.d2b[b] = 0ull;
+    }
+    if (threadIdx.x == 0) a.st->imax_next = 0u;
+}
+
 // md_set_state, before the new positions: the error word cleared, replica r's indenter
 // displacement and the step count set, its accumulator for the rebuild test of the state
 // positions zeroed, the drift made from the old state voided.  The inner list's
@@ -1333,7 +1355,9 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
 // F'_j) f' + (M'_i + M'_j) 2 f f' + Phi'] / r, over the inner list; its entries beyond rc
 // (~3 %) drop out by a select (a branch on the distance measured 10 % slower).  EN: the
 // pair and Morse energies, the indenter load and the kinetic energy into the CTA partials
-// (only the last step of an md_step call needs them).
+// (only the last step of an md_step call needs them).  integrate: 0 forces only; 1 a time
+// step's Task 5, then the next step's Task 3 (drift) from the state just completed; 2 no
+// kick (the forces of a state set from outside), then the next step's Task 3 from it.
 template <int TPA, int IPOW, bool EN>
 __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int integrate)
 {
@@ -1350,7 +1374,7 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
     const size_t S = a.S;
     float gx = 0.f, gy = 0.f, gz = 0.f, ep = 0.f;
     float mx = 0.f, my = 0.f, mz = 0.f, em = 0.f;
-    const int bn = buf_step(a), bo = buf_cur(a);   // x(t + dt) in bn; x(t + 2 dt) goes to bo
+    const int bn = buf_step(a), bo = bn ^ 1;   // the positions evaluated in bn; the drift goes to bo
     if (integrate && threadIdx.x == 0 && (A & 1) == 0) {
         // the epilogue's per-atom inputs of this CTA's atoms, on their way to L2 while the
         // pair loop runs (A even: every range starts and ends on a 16-byte boundary)
@@ -1358,7 +1382,7 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
         const size_t S = a.S;
         for (int k = 0; k < 3; ++k) {
             prefetch_l2(a.xs[bn] + k * S + s0, A * 8u);
-            prefetch_l2(a.vh + k * S + s0, A * 8u);
+            prefetch_l2((integrate == 1 ? a.vh : a.v) + k * S + s0, A * 8u);
         }
         prefetch_l2(a.pb + s0, A * 16u);
         prefetch_l2(a.pin + s0, A * 16u);
@@ -1441,19 +1465,24 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
         const double Fx = gx + mx, Fy = gy + my, Fz = gz + mz;
         a.F[s] = Fx; a.F[S + s] = Fy; a.F[2 * S + s] = Fz;
         double vx, vy, vz;
-        if (integrate) {   // Task 5: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2 (FP64)
-            vx = a.vh[s]; vy = a.vh[S + s]; vz = a.vh[2 * S + s];
-            if (!a.fixed[s]) {
-                const double hk = R.hk;
-                vx = fma(hk, Fx, vx); vy = fma(hk, Fy, vy); vz = fma(hk, Fz, vz);
-                a.v[s] = vx; a.v[S + s] = vy; a.v[2 * S + s] = vz;
+        if (integrate) {
+            if (integrate == 1) {   // Task 5: v(t+dt) = v(t+dt/2) + a(t+dt) dt/2 (FP64)
+                vx = a.vh[s]; vy = a.vh[S + s]; vz = a.vh[2 * S + s];
+                if (!a.fixed[s]) {
+                    const double hk = R.hk;
+                    vx = fma(hk, Fx, vx); vy = fma(hk, Fy, vy); vz = fma(hk, Fz, vz);
+                    a.v[s] = vx; a.v[S + s] = vy; a.v[2 * S + s] = vz;
+                }
+            } else {
+                vx = a.v[s]; vy = a.v[S + s]; vz = a.v[2 * S + s];
             }
-            // Task 3 of the next step, from the state just completed: x(t + 2 dt) to buffer
-            // bo, its rebuild test for the next k_decide but one, its inner-list test for
-            // the next k_density.  The next k_decide keeps it unless it rebuilds the lists.
+            // Task 3 of the next step, from the state just completed (x(t + 2 dt) in a
+            // time step, x(t + dt) from a set state) to buffer bo, its rebuild test for the
+            // k_decide that examines those positions, its inner-list test for the k_density
+            // that evaluates them.  The next k_decide keeps it unless it rebuilds the lists.
             const double *x = a.xs[bn];
-            drift_atom(a, R, s, __float_as_int(pi.w), a.rs[r].dthr2, x[s], x[S + s], x[2 * S + s], vx, vy, vz, Fx, Fy, Fz,
-                       a.xs[bo], a.p4[bo], d2bits, ibits);
+            drift_atom(a, R, s, __float_as_int(pi.w), integrate == 1 ? a.rs[r].dthr2 : a.rs[r].dthr, x[s], x[S + s],
+                       x[2 * S + s], vx, vy, vz, Fx, Fy, Fz, a.xs[bo], a.p4[bo], d2bits, ibits);
         } else {
             vx = a.v[s]; vy = a.v[S + s]; vz = a.v[2 * S + s];
         }
@@ -1465,8 +1494,8 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
     }
     if (integrate) cta_max_disp(d2bits, ibits, &a.rs[r].d2b[bo], &a.st->imax_next);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.st->drift_ok = integrate;
-        if (integrate) a.st->since_build += 1;
+        a.st->drift_ok = integrate != 0;
+        if (integrate == 1) a.st->since_build += 1;
     }
     if (EN) cta_partials<4>(acc, a.part + 2 * (size_t)a.max_blocks, a.max_blocks, blockIdx.x);
 }
@@ -1747,6 +1776,12 @@ cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s)
 cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s)
 {
     k_verlet1<<<a.S / MD_TILE, MD_TILE, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_drift_prep(const DevArgs &a, cudaStream_t s)
+{
+    k_drift_prep<<<1, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
