@@ -219,6 +219,12 @@ int md_get_state(md_t *h, int32_t replica, double *x3n, double *v3n, double *z_i
  * MD_ERR_NBR_OVERFLOW, MD_ERR_CUDA. */
 int md_set_state(md_t *h, int32_t replica, const double *x3n, const double *v3n, double z_ind, int64_t step);
 
+/* The indenter's velocity v_ind (A/fs along z; negative = downwards) of one replica from
+ * the next step on (Task 2, Sec. 2.1; the loading and unloading legs of an indentation run,
+ * Sec. 2.5).  Positions, forces and lists are unchanged; the next step re-derives its
+ * displacement test for the new indenter path.  Errors: MD_ERR_ARG, MD_ERR_CUDA. */
+int md_set_indenter_velocity(md_t *h, int32_t replica, double v_ind);
+
 /* Test hook.  which = 0: Cr-Cr list, which = 1: Cr-C list, as built at the last rebuild.
  * cell_xyz (3*n_cr, may be NULL): cell coordinates of each atom in the Cr cell grid;
  * cnt (n_cr): list lengths (capped at the capacity); nbr (n_cr*kmax, may be NULL): entries

@@ -92,6 +92,7 @@ def lib():
         L.or_sim_new.argtypes = [C.c_void_p, C.c_int32, dp, dp, up, C.c_int32, dp, dp, dp, ip,
                                  C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, C.c_int32]
         L.or_sim_free.argtypes = [C.c_void_p]
+        L.or_sim_set_v_ind.argtypes = [C.c_void_p, C.c_double]
         L.or_sim_step.restype = C.c_int
         L.or_sim_step.argtypes = [C.c_void_p, C.c_int64]
         L.or_sim_get.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -251,6 +252,9 @@ class Sim:
     def step(self, n: int = 1):
         if lib().or_sim_step(self.h, int(n)):
             raise RuntimeError("or_sim_step failed")
+
+    def set_indenter_velocity(self, v_ind: float):
+        lib().or_sim_set_v_ind(self.h, float(v_ind))
 
     def state(self):
         x = np.zeros((self.n, 3)); v = np.zeros((self.n, 3)); F = np.zeros((self.n, 3))

@@ -816,6 +816,10 @@ int or_sim_step(or_sim *S, int64_t nsteps)
     return 0;
 }
 
+/* the indenter's velocity from the next step on (Task 2; the loading and unloading legs
+ * of an indentation run, Sec. 2.5) */
+void or_sim_set_v_ind(or_sim *S, double v_ind) { S->v_ind = v_ind; }
+
 /* out[8] = {embed, pair, M, morse, kinetic, potential, total, load}; counters[2] = {step, rebuilds} */
 void or_sim_get(const or_sim *S, double *x, double *v, double *F, double *out, double *z_ind, int64_t *counters)
 {

@@ -12,7 +12,7 @@
 
 #include "md_internal.h"
 
-#define MD_ABI_VERSION 2
+#define MD_ABI_VERSION 3
 
 namespace {
 
@@ -897,6 +897,20 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     if ((rc2 = read_status(h, &st))) return rc2;
     if ((rc2 = status_to_code(h, st))) return rc2;
     h->forces_valid = true;
+    return MD_OK;
+}
+
+int md_set_indenter_velocity(md_t *h, int32_t r, double v_ind)
+{
+    int rc = check_replica(h, r);
+    if (rc) return rc;
+    if (!(v_ind == v_ind)) return fail(h, MD_ERR_ARG, "md_set_indenter_velocity: v_ind is NaN");
+    h->rep[r].v_ind = v_ind;
+    RepDev *d = const_cast<RepDev *>(h->a.rep) + r;
+    CU(cudaMemcpyAsync(&d->v_ind, &h->rep[r].v_ind, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    // the drift made for the next step took its displacement threshold from the old path
+    h->drift = false;
     return MD_OK;
 }
 
