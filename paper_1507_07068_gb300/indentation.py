@@ -139,13 +139,15 @@ def main(argv=None) -> int:
     ap.add_argument("--speed-ms", type=float, default=10.0, help="indenter speed (m/s)")
     ap.add_argument("--sample-every", type=int, default=100)
     ap.add_argument("--skin", type=float, default=1.1)
+    ap.add_argument("--kcmax", type=int, default=512,
+                    help="Cr-C list capacity (a deep indent puts many C atoms in reach of one Cr atom)")
     ap.add_argument("--curve", default="", help="write the samples to this .npz file")
     args = ap.parse_args(argv)
     if args.workload not in mi.PRESETS:
         raise SystemExit(f"--workload: one of {sorted(mi.PRESETS)}")
     rep = mi.make_workload(args.workload).replicas[0]
     R = float(mi.PRESETS[args.workload][3])   # the hemisphere's radius (A)
-    sim = md.MD([rep], md.load_params(), precision=args.precision, skin=args.skin)
+    sim = md.MD([rep], md.load_params(), precision=args.precision, skin=args.skin, kcmax=args.kcmax)
     out = run(sim, 0, relax_steps=args.relax, depth_max=args.depth, speed=args.speed_ms * 1e-5,
               sample_every=args.sample_every)
     sim.close()
@@ -155,7 +157,10 @@ def main(argv=None) -> int:
     res = {"workload": args.workload, "n_cr": int(rep.n_cr), "n_c": int(rep.n_c), "precision": args.precision,
            "steps": int(out["step"][-1]), "max_load": float(out["load"].max()), "min_load": float(out["load"].min()),
            "depth_at_max_load": float(out["depth"][int(np.argmax(out["load"]))])}
-    if R > 0:
+    if R > 0 and out["load"][:iu].max() <= 0:
+        # the Hertz law and the Oliver-Pharr analysis describe a repulsive contact
+        res["analysis_error"] = "no repulsive load while loading (the Cr-C attraction dominates)"
+    elif R > 0:
         res["R"] = R
         try:
             res["hertz_E"] = hertz_modulus(out["depth"][:iu], out["load"][:iu], R)
