@@ -234,6 +234,13 @@ def make_workload(name: str, T: float = 300.0, n_replicas: int = 256,
     return Workload(name, [rep], steps=steps, precision=prec)
 
 
+def paper_cube(n: int, T: float = 300.0, seed: int = 1507) -> Replica:
+    """The paper's timing workload (Table 2, Sec. 4): a cube of n^3 BCC unit cells with free
+    lateral faces, (n+1)^3 + n^3 atoms (2331 / 17261 / 132921 for n = 10 / 20 / 40), two
+    fixed bottom planes, the indenter disabled."""
+    return make_replica(f"cube{n}", n, n, n, 0.0, T, seed=seed + n, n_fixed_planes=2, free_lateral=True)
+
+
 def small_cluster(n_side: int = 3, a: float = A_CR, jitter: float = 0.05, seed: int = 7,
                   vacuum: float = 10.0) -> Replica:
     """A small free BCC cluster with random displacements (no periodicity, no indenter)."""

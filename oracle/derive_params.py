@@ -23,6 +23,9 @@ and r_e = 2.754 A (Sec. 2.6) are given.  This script fixes a self-consistent set
   * Morse placeholders D_o = 0.2 eV, alpha_x = 6, y_eq = 2.2 A, rc_m = 6 A.
 
 Run:  python oracle/derive_params.py   (writes paper_1507_07068_gb300/cr_c_params.json)
+      python oracle/derive_params.py --rc 8.262 --out paper_1507_07068_gb300/cr_c_params_rstar.json
+      (the same fit with the paper's long cut-off r* = 3 r_e = 8.262 A for f and f^2,
+      Sec. 2.6; Phi still ends at its double root d r_e)
 Only oracle/ is called.
 """
 from __future__ import annotations
@@ -61,9 +64,9 @@ def base_params(**kw) -> dict:
     return p
 
 
-def main(out_path: str | None = None) -> dict:
+def main(out_path: str | None = None, rc: float | None = None) -> dict:
     a = TARGET["a_lat"]
-    p0 = base_params(tabulated=0)
+    p0 = base_params(tabulated=0) if rc is None else base_params(tabulated=0, rc=rc)
     rc = p0["rc"]
     V = bcc_vectors(a, rc)
     omega = a ** 3 / 2.0
@@ -79,9 +82,9 @@ def main(out_path: str | None = None) -> dict:
     def unit_pots():
         pots = []
         for k in range(4):
-            pots.append(oracle.Potential(base_params(tabulated=0, rho_e=rho_e, P_e=P_e, **{f"a{k}": 1.0})))
-        pots.append(oracle.Potential(base_params(tabulated=0, rho_e=rho_e, P_e=P_e, F_o=1.0)))
-        pots.append(oracle.Potential(base_params(tabulated=0, rho_e=rho_e, P_e=P_e, F_o=0.0, alpha=1.0)))
+            pots.append(oracle.Potential(base_params(tabulated=0, rc=rc, rho_e=rho_e, P_e=P_e, **{f"a{k}": 1.0})))
+        pots.append(oracle.Potential(base_params(tabulated=0, rc=rc, rho_e=rho_e, P_e=P_e, F_o=1.0)))
+        pots.append(oracle.Potential(base_params(tabulated=0, rc=rc, rho_e=rho_e, P_e=P_e, F_o=0.0, alpha=1.0)))
         return pots
 
     pots = unit_pots()
@@ -124,7 +127,7 @@ def main(out_path: str | None = None) -> dict:
     rhs = rhs - A[:, 4] * F_o
     M = A[:, [0, 1, 2, 3, 5]]
     sol = np.linalg.solve(M, rhs)
-    params = base_params(rho_e=float(rho_e), P_e=float(P_e), a0=float(sol[0]), a1=float(sol[1]),
+    params = base_params(rc=rc, rho_e=float(rho_e), P_e=float(P_e), a0=float(sol[0]), a1=float(sol[1]),
                          a2=float(sol[2]), a3=float(sol[3]), alpha=float(sol[4]), F_o=F_o)
     params["_note"] = ("derived for this implementation, not the paper's values: the paper's refs. [42] "
                        "and [34] are not printed; see oracle/derive_params.py")
@@ -139,4 +142,9 @@ def main(out_path: str | None = None) -> dict:
 
 
 if __name__ == "__main__":
-    print(json.dumps(main(), indent=1, sort_keys=True))
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--rc", type=float, default=None, help="cut-off of f and f^2 (A); default d r_e")
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    print(json.dumps(main(a.out, a.rc), indent=1, sort_keys=True))

@@ -17,3 +17,10 @@ def pytest_configure(config):
 def params():
     import oracle
     return oracle.load_params()
+
+
+@pytest.fixture(scope="session")
+def params_rstar():
+    """The same derived set fitted with the paper's long cut-off r* = 8.262 A (Sec. 2.6)."""
+    import oracle
+    return oracle.load_params(os.path.join(ROOT, "paper_1507_07068_gb300", "cr_c_params_rstar.json"))

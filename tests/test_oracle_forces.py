@@ -81,6 +81,44 @@ def test_bcc_closed_form(params, tab):
     assert abs((ep - em) / (2 * d) / N) < 1e-7
 
 
+@pytest.mark.parametrize("tab", [0, 1])
+def test_bcc_closed_form_long_cutoff(params_rstar, tab):
+    """The set fitted with r* = 8.262 A (Sec. 2.6): the same lattice targets hold with the
+    fifth and sixth neighbour shells inside the cut-off of f."""
+    params = params_rstar
+    assert params["rc"] == 8.262
+    pot = oracle.Potential(params, tabulated=tab)
+    n = 9   # three cells of r* per periodic axis
+
+    def energy(a):
+        x = mi.bcc_film(n, n, n, a)
+        lo = np.zeros(3); hi = np.full(3, n * a)
+        r = oracle.forces(pot, x, lo, hi, np.ones(3, np.int32))
+        return r, len(x)
+
+    r, N = energy(mi.A_CR)
+    tol = 1e-12 if tab == 0 else 1e-9
+    assert r["potential"] / N == pytest.approx(-params["_targets"]["E_c"], abs=tol)
+    assert np.abs(r["F"]).max() < 1e-12
+    assert abs(r["mterm"]) < 1e-12 * N
+    d = 1e-5
+    ep = energy(mi.A_CR + d)[0]["potential"]; em = energy(mi.A_CR - d)[0]["potential"]
+    assert abs((ep - em) / (2 * d) / N) < 1e-7
+    # rho_e is the density of a lattice atom: the shifted-force f summed over the BCC
+    # lattice points within r* (enumerated here directly: 8, 6, 12, 24, 8, 6, 24, 24, 24 ...)
+    m = 4
+    g = np.arange(-m, m + 1)
+    c = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).astype(float)
+    pts = np.concatenate([c, c + 0.5]) * mi.A_CR
+    rr = np.sqrt((pts ** 2).sum(1))
+    rc = params["rc"]
+    rr = rr[(rr > 0) & (rr < rc)]
+    f = lambda q: params["f_e"] * (params["r_e"] / q) ** params["beta"]
+    fs = f(rr) - f(rc) - (rr - rc) * (-params["beta"] * f(rc) / rc)   # shifted-force form
+    assert len(rr) == 8 + 6 + 12 + 24 + 8 + 6 + 24 + 24 + 24 + 32 + 12
+    assert params["rho_e"] == pytest.approx(float(fs.sum()), rel=1e-12)
+
+
 def _isolate(params, term):
     p = dict(params)
     zero_pair = dict(a0=0.0, a1=0.0, a2=0.0, a3=0.0)
