@@ -116,7 +116,8 @@ typedef struct md_system {
  *                   skin); k > 0 = rebuild every k steps (a larger displacement is then
  *                   reported as MD_ERR_SKIN_VIOLATION)
  *   kmax, kcmax   : neighbour capacity per atom for Cr-Cr and Cr-C (0 = defaults 80, 160)
- *   tpa           : threads per atom in the force kernels, 1, 2, 4 or 8 (0 = default)
+ *   tpa           : threads per atom in the force kernels, 1, 2, 4 or 8 (0 = the smallest
+ *                   that puts at least 65 536 threads on all replicas' atoms)
  *   block         : threads per block in the force kernels (0 = default)
  *   use_graph     : nonzero = md_step replays a captured CUDA graph
  *   inner_skin    : MD_MIXED only.  The inner list (Sec. 2.6: the Verlet-list entries the

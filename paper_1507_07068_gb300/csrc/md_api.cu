@@ -371,7 +371,13 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
         return fail(nullptr, MD_ERR_ARG, "md_init: precision must be MD_FP64 or MD_MIXED");
     if (!(opt->skin >= 0.0) || opt->rebuild_every < 0 || !isfinite(opt->inner_skin))
         return fail(nullptr, MD_ERR_ARG, "md_init: skin must be >= 0, rebuild_every >= 0 and inner_skin finite");
-    int tpa = opt->tpa ? opt->tpa : 1;
+    // threads per atom by default: the smallest of 1, 2, 4, 8 that puts at least 64Ki threads
+    // on the atoms of all replicas (a small system's atoms then share their lists among
+    // more lanes: 1 024 atoms run 1.4x, a 2 331-atom cube at the long cut-off 2.5x faster)
+    int64_t n_all = 0;
+    for (int32_t r = 0; r < n_replicas; ++r) n_all += sys[r].n_cr > 0 ? sys[r].n_cr : 0;
+    int tpa = opt->tpa;
+    if (!tpa) for (tpa = 1; tpa < 8 && n_all * tpa < 65536; tpa *= 2) {}
     int block = opt->block ? opt->block : 128;
     if (!(tpa == 1 || tpa == 2 || tpa == 4 || tpa == 8) || block < 32 || block > 256 || block % 32 ||
         MD_TILE % (block / tpa) != 0)
