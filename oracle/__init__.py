@@ -93,6 +93,10 @@ def lib():
                                  C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, C.c_int32]
         L.or_sim_free.argtypes = [C.c_void_p]
         L.or_sim_set_v_ind.argtypes = [C.c_void_p, C.c_double]
+        L.or_sim_virial.restype = C.c_int
+        L.or_sim_virial.argtypes = [C.c_void_p, dp]
+        L.or_virial.restype = C.c_int
+        L.or_virial.argtypes = [C.c_void_p, C.c_int32, dp, dp, dp, ip, C.c_int32, dp, C.c_int32, dp, dp, dp]
         L.or_sim_step.restype = C.c_int
         L.or_sim_step.argtypes = [C.c_void_p, C.c_int64]
         L.or_sim_get.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -222,6 +226,22 @@ def forces(pot: Potential, x, lo, hi, periodic, xc=None, method: int = 1, want_a
     return out
 
 
+def virial(pot: Potential, x, lo, hi, periodic, xc=None, method: int = 1):
+    """Per-atom virial (n, 6: xx, yy, zz, xy, xz, yz) at the given positions: each pair term
+    c (x_j - x_i) (x) (x_j - x_i) with c = (dE/dr) / r, half to each atom of the pair (a Cr-C
+    pair's half to the Cr atom).  Also returns the forces and energies of `forces`."""
+    x = _arr(x).reshape(-1, 3)
+    xc = np.zeros((0, 3)) if xc is None else _arr(xc).reshape(-1, 3)
+    n = len(x)
+    F = np.zeros((n, 3)); ep = np.zeros(5); W = np.zeros((n, 6))
+    err = lib().or_virial(pot.h, n, x, _arr(lo), _arr(hi), _arr(periodic, np.int32), len(xc),
+                          xc if len(xc) else np.zeros(3), int(method), F, ep, W)
+    if err:
+        raise RuntimeError(f"or_virial: {err}")
+    return dict(W=W, F=F, embed=ep[0], pair=ep[1], mterm=ep[2], morse=ep[3], load=ep[4],
+                potential=ep[0] + ep[1] + ep[2] + ep[3])
+
+
 class Sim:
     """Oracle time loop (Fig. 5): Verlet lists with skin, Tasks 1-5 per step."""
 
@@ -255,6 +275,13 @@ class Sim:
 
     def set_indenter_velocity(self, v_ind: float):
         lib().or_sim_set_v_ind(self.h, float(v_ind))
+
+    def virial(self):
+        """Per-atom virial (n, 6: xx, yy, zz, xy, xz, yz) of the current state."""
+        W = np.zeros((self.n, 6))
+        if lib().or_sim_virial(self.h, W):
+            raise RuntimeError("or_sim_virial failed")
+        return W
 
     def state(self):
         x = np.zeros((self.n, 3)); v = np.zeros((self.n, 3)); F = np.zeros((self.n, 3))

@@ -560,6 +560,19 @@ int64_t or_cneighbors(int32_t n, const double *x, int32_t nc, const double *xc, 
 /* Energy components and load of one force evaluation (Eq. A1 + Morse). */
 typedef struct { double embed, pair, mterm, morse, load; } or_epot;
 
+/* Per-atom virial (the potential part of the per-atom stress times volume; stresses are
+ * among the quantities Task 4 can give, Sec. 2.1, and their histories are derived along
+ * the run, Sec. 3.1).  Every pair term of the energy depends on one distance r; with
+ * c = (dE/dr) / r the force on i from j is c (x_j - x_i), and each of the two atoms of a
+ * pair takes half of c (x_j - x_i) (x) (x_j - x_i); a Cr-C pair gives its half to the Cr
+ * atom.  Summed over the atoms this is dE/d(strain) under a homogeneous deformation.
+ * Components xx, yy, zz, xy, xz, yz. */
+static void add_virial(double *w, double c, const double *d)
+{
+    w[0] += c * d[0] * d[0]; w[1] += c * d[1] * d[1]; w[2] += c * d[2] * d[2];
+    w[3] += c * d[0] * d[1]; w[4] += c * d[0] * d[2]; w[5] += c * d[1] * d[2];
+}
+
 /*
  * Task 4 (Sec. 2.1; Sec. 3.3.1.2 and 3.3.1.3): two passes over neighbour lists whose
  * entries are filtered by r < rc (the inner list of Sec. 2.6).
@@ -570,7 +583,8 @@ typedef struct { double embed, pair, mterm, morse, load; } or_epot;
  */
 static int eval_forces(const or_pot *P, int32_t n, const double *x, const or_box *b,
                        const or_list *nl, int32_t nc, const double *xc, const or_list *cl,
-                       double *F, double *rho_out, double *P_out, double *eatom_out, or_epot *E)
+                       double *F, double *rho_out, double *P_out, double *eatom_out, or_epot *E,
+                       double *W)
 {
     const or_params *p = &P->p;
     double rc2 = p->rc * p->rc, rcm2 = p->rc_m * p->rc_m;
@@ -606,6 +620,7 @@ static int eval_forces(const or_pot *P, int32_t n, const double *x, const or_box
     #pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < n; ++i) {
         double fx = 0.0, fy = 0.0, fz = 0.0, ep = 0.0, em = 0.0, lz = 0.0, d[3];
+        double w[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         for (int64_t s = nl->off[i]; s < nl->off[i + 1]; ++s) {
             int32_t j = nl->idx[s];
             double r2 = disp2(b, &x[3 * i], &x[3 * j], d);   /* d = x_j - x_i */
@@ -618,6 +633,7 @@ static int eval_forces(const or_pot *P, int32_t n, const double *x, const or_box
             /* F_i = -coef * (x_i - x_j)/r = +coef * d / r */
             fx += coef * d[0] / r; fy += coef * d[1] / r; fz += coef * d[2] / r;
             ep += 0.5 * pv;
+            if (W) add_virial(w, 0.5 * coef / r, d);
         }
         if (cl) {
             for (int64_t s = cl->off[i]; s < cl->off[i + 1]; ++s) {
@@ -631,9 +647,11 @@ static int eval_forces(const or_pot *P, int32_t n, const double *x, const or_box
                 fx += gx; fy += gy; fz += gz;
                 em += mv;
                 lz -= gz;          /* load = -sum_i F^Morse_{i,z} */
+                if (W) add_virial(w, 0.5 * md / y, d);
             }
         }
         F[3 * i] = fx; F[3 * i + 1] = fy; F[3 * i + 2] = fz;
+        if (W) for (int k = 0; k < 6; ++k) W[6 * i + k] = w[k];
         e_pair[i] = ep; e_mor[i] = em; ld[i] = lz;
     }
     E->embed = or_neumaier(e_emb, n);
@@ -658,7 +676,24 @@ int or_forces(const or_pot *P, int32_t n, const double *x, const double *lo, con
     int err = build_list(n, x, &b, P->p.rc, method, &nl);
     if (!err && nc > 0) err = build_clist(n, x, nc, xc, &b, P->p.rc_m, &cl);
     or_epot E = {0, 0, 0, 0, 0};
-    if (!err) err = eval_forces(P, n, x, &b, &nl, nc, xc, nc > 0 ? &cl : NULL, F, rho, Pden, eatom, &E);
+    if (!err) err = eval_forces(P, n, x, &b, &nl, nc, xc, nc > 0 ? &cl : NULL, F, rho, Pden, eatom, &E, NULL);
+    list_free(&nl); list_free(&cl);
+    if (err) return err;
+    epot[0] = E.embed; epot[1] = E.pair; epot[2] = E.mterm; epot[3] = E.morse; epot[4] = E.load;
+    return 0;
+}
+
+/* as or_forces, with the per-atom virial W (6 per atom, see add_virial) */
+int or_virial(const or_pot *P, int32_t n, const double *x, const double *lo, const double *hi,
+              const int32_t *per, int32_t nc, const double *xc, int32_t method, double *F, double *epot,
+              double *W)
+{
+    or_box b; or_list nl = {0}, cl = {0};
+    box_set(&b, lo, hi, per);
+    int err = build_list(n, x, &b, P->p.rc, method, &nl);
+    if (!err && nc > 0) err = build_clist(n, x, nc, xc, &b, P->p.rc_m, &cl);
+    or_epot E = {0, 0, 0, 0, 0};
+    if (!err) err = eval_forces(P, n, x, &b, &nl, nc, xc, nc > 0 ? &cl : NULL, F, NULL, NULL, NULL, &E, W);
     list_free(&nl); list_free(&cl);
     if (err) return err;
     epot[0] = E.embed; epot[1] = E.pair; epot[2] = E.mterm; epot[3] = E.morse; epot[4] = E.load;
@@ -713,7 +748,7 @@ static int sim_forces(or_sim *S)
 {
     sim_place_indenter(S);
     return eval_forces(S->P, S->n, S->x, &S->b, &S->nl, S->nc, S->xc, S->nc > 0 ? &S->cl : NULL,
-                       S->F, NULL, NULL, NULL, &S->E);
+                       S->F, NULL, NULL, NULL, &S->E, NULL);
 }
 
 static void sim_kinetic(or_sim *S)
@@ -814,6 +849,14 @@ int or_sim_step(or_sim *S, int64_t nsteps)
         S->since_build++;
     }
     return 0;
+}
+
+/* the per-atom virial (see add_virial) of the current state, from the current lists */
+int or_sim_virial(or_sim *S, double *W)
+{
+    sim_place_indenter(S);
+    return eval_forces(S->P, S->n, S->x, &S->b, &S->nl, S->nc, S->xc, S->nc > 0 ? &S->cl : NULL,
+                       S->F, NULL, NULL, NULL, &S->E, W);
 }
 
 /* the indenter's velocity from the next step on (Task 2; the loading and unloading legs
