@@ -220,6 +220,17 @@ int md_get_state(md_t *h, int32_t replica, double *x3n, double *v3n, double *z_i
  * MD_ERR_NBR_OVERFLOW, MD_ERR_CUDA. */
 int md_set_state(md_t *h, int32_t replica, const double *x3n, const double *v3n, double z_ind, int64_t step);
 
+/* Per-atom virial of one replica at the current state, 6 doubles per atom in caller order
+ * (xx, yy, zz, xy, xz, yz; eV): the potential part of the per-atom stress times volume
+ * (Task 4 can give stresses, Sec. 2.1; their histories are derived along a run, Sec. 3.1).
+ * Every pair term of the energy depends on one distance r; with c = (dE/dr)/r the force on
+ * i from j is c (x_j - x_i), and each atom of the pair holds half of
+ * c (x_j - x_i) (x) (x_j - x_i); a Cr-C pair gives its half to the Cr atom.  The sum over
+ * the atoms is the derivative of the energy under a homogeneous deformation.  The kinetic
+ * part, -m v (x) v, follows from md_get_state.  The call evaluates the forces again (same
+ * values) and then the virial.  Errors: MD_ERR_ARG, MD_ERR_CUDA. */
+int md_get_virial(md_t *h, int32_t replica, double *out6n);
+
 /* The indenter's velocity v_ind (A/fs along z; negative = downwards) of one replica from
  * the next step on (Task 2, Sec. 2.1; the loading and unloading legs of an indentation run,
  * Sec. 2.5).  Positions, forces and lists are unchanged; the next step re-derives its

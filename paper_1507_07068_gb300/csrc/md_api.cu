@@ -12,7 +12,7 @@
 
 #include "md_internal.h"
 
-#define MD_ABI_VERSION 3
+#define MD_ABI_VERSION 4
 
 namespace {
 
@@ -30,6 +30,17 @@ __global__ void k_state_in(const double *stage, double *d0, double *d1, const De
     int o = orig[s];
 #pragma unroll
     for (int k = 0; k < 3; ++k) dst[k * S + s] = stage[3 * (size_t)o + k];
+}
+
+// the per-atom virial of replica r into caller order, 6 per atom
+__global__ void k_vir_out(const double *vir, double *stage, const int32_t *orig, int slot_off, int n, size_t S)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = slot_off + i;
+    int o = orig[s];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) stage[6 * (size_t)o + k] = vir[k * S + s];
 }
 
 __global__ void k_state_out(const double *s0, const double *s1, const DevStatus *st, double *stage,
@@ -904,6 +915,27 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     if ((rc2 = status_to_code(h, st))) return rc2;
     h->forces_valid = true;
     return MD_OK;
+}
+
+int md_get_virial(md_t *h, int32_t r, double *out6n)
+{
+    int rc = check_replica(h, r);
+    if (rc) return rc;
+    if (!out6n) return fail(h, MD_ERR_ARG, "md_get_virial: null output");
+    if ((rc = ensure_forces(h))) return rc;
+    if (!h->a.vir && (rc = dalloc(h, &h->a.vir, 6 * (size_t)h->a.S))) return rc;
+    // a force evaluation first: F'(rho), M'(P) and the inner list then belong to the current
+    // slot order and positions whatever call came before (a list build permutes the slots)
+    if ((rc = forces_now(h, h->stream))) return rc;
+    CU(launch_virial(h->a, h->pot, h->cfg, h->stream));
+    const RepDev &R = h->rep[r];
+    const int n = R.n_atoms;
+    k_vir_out<<<(n + 255) / 256, 256, 0, h->stream>>>(h->a.vir, h->stage, h->a.orig, R.slot_off, n, h->a.S);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(out6n, h->stage, 6 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    DevStatus st;
+    if ((rc = read_status(h, &st))) return rc;
+    return status_to_code(h, st);
 }
 
 int md_set_indenter_velocity(md_t *h, int32_t r, double v_ind)

@@ -195,6 +195,7 @@ struct DevArgs {
     uint8_t *fixed;
     int32_t *nbr, *cnt, *nbrc, *cntc;
     int32_t *cand, *near;        // Cr-C: atoms within reach of an indenter grid / with neighbours
+    double *vir;                 // per-atom virial [6][S] (xx yy zz xy xz yz), allocated on first request
     float4 *fmorse;              // mixed precision: Morse force and energy of each atom in near
     // rebuild scratch
     int32_t *key, *perm, *cell_count, *cell_start, *cell_fill, *scan_blk;
@@ -235,6 +236,9 @@ cudaError_t launch_morse(const DevArgs &a, const PotDev &p, cudaStream_t s);
 cudaError_t launch_force_split(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int energies,
                                int with_morse, cudaStream_t s);
 cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s);
+// per-atom virial of every atom at the state positions into a.vir (uses the lists and the
+// F', M' of the last force evaluation, which are those of the state)
+cudaError_t launch_virial(const DevArgs &a, const PotDev &p, const LaunchCfg &c, cudaStream_t s);
 // before a force pass with integrate = 2 (mixed precision): thresholds and accumulators of
 // the drift it makes
 cudaError_t launch_drift_prep(const DevArgs &a, cudaStream_t s);

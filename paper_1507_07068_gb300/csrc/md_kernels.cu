@@ -1673,6 +1673,154 @@ __global__ void __launch_bounds__(256) k_force_fp64(DevArgs a, PotDev P, int int
     cta_partials<4>(acc, a.part + 2 * (size_t)a.max_blocks, a.max_blocks, blockIdx.x);
 }
 
+// ============================================================================ per-atom virial
+
+// c d (x) d / 2 into w (xx yy zz xy xz yz): the pair term whose energy derivative is c r
+template <class T>
+__device__ __forceinline__ void add_vir(T (&w)[6], T c, T dx, T dy, T dz)
+{
+    const T h = c * (T)0.5;
+    w[0] += h * dx * dx; w[1] += h * dy * dy; w[2] += h * dz * dz;
+    w[3] += h * dx * dy; w[4] += h * dx * dz; w[5] += h * dy * dz;
+}
+
+// Per-atom virial (the potential part of per-atom stress times volume; Sec. 2.1 lists
+// stresses among Task 4's outputs): every pair term of the energy depends on one distance r,
+// the force on i from j is c (x_j - x_i) with c = (dE/dr) / r -- the coef of k_force_mixed --
+// and each atom of the pair takes half of c (x_j - x_i) (x) (x_j - x_i); a Cr-C pair gives
+// its half to the Cr atom.  Mixed precision: the inner list and pos4 of the state, FP32 pair
+// terms as in k_force_mixed, the Cr-C pairs with FP64 geometry as in k_morse_mixed.
+template <int TPA, int IPOW>
+__global__ void __launch_bounds__(256) k_virial_mixed(DevArgs a, PotDev P)
+{
+    __shared__ float4 sm_off[64];
+    const int A = blockDim.x / TPA;
+    const int g = threadIdx.x / TPA, lane = threadIdx.x % TPA;
+    const int s = blockIdx.x * A + g;
+    const int r = a.tile_rep[(blockIdx.x * A) / MD_TILE];
+    const RepDev &R = a.rep[r];
+    fill_offsets(sm_off, R);
+    __syncthreads();
+    const Pot32 &Q = static_cast<const Pot32 &>(P.q);
+    const bool real = (s - R.slot_off) < R.n_atoms;
+    const size_t S = a.S;
+    const int b = buf_step(a);
+    const float4 *pp = a.p4[b];
+    const float4 pi = pp[s];
+    const PairGeom G = pair_geom(R, __float_as_int(pi.w));
+    const bool per = __any_sync(0xffffffffu, real && G.xmask != 0u);
+    float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    auto work = [&](auto PERC) {
+        constexpr bool PER = decltype(PERC)::value;
+        if (!real) return;
+        const float2 fmi = a.fm32[s];
+        const int n = a.icnt[s];
+        for (int k = lane; k < n; k += TPA) {
+            const unsigned e = (unsigned)__ldg(&a.inner[(size_t)k * S + s]);
+            const unsigned j = e & MD_J_MASK;
+            if (j == (unsigned)s) continue;   // padding
+            float dx, dy, dz;
+            disp<PER>(pi, __ldg(&pp[j]), e >> MD_J_BITS, sm_off, G, dx, dy, dz);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (!(r2 < Q.rc2)) continue;
+            const float2 fmj = __ldg(&a.fm32[j]);
+            const float rinv = rsqrt_nr(r2);
+            float f, df, ph, dph;
+            fa_phi<IPOW, false>(Q, r2, rinv, f, df, ph, dph);
+            const float coef = fmaf(fmaf(fmi.y + fmj.y, f, fmi.x + fmj.x), df, dph) * rinv;
+            add_vir(w, coef, dx, dy, dz);
+        }
+    };
+    if (per) work(BoolC<true>{}); else work(BoolC<false>{});
+#pragma unroll
+    for (int o = TPA / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k] += __shfl_xor_sync(0xffffffffu, w[k], o);
+    if (!real || lane != 0) return;
+    double W[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) W[k] = w[k];
+    const int nc = a.cntc[s];
+    if (nc > 0) {
+        const double *x = a.xs[b];
+        const double xi = x[s], yi = x[S + s], zi = x[2 * S + s];
+        const double z_ind = a.rs[r].z_ind;
+        const size_t C = a.C;
+        for (int k = 0; k < nc; ++k) {
+            const int c = __ldg(&a.nbrc[(size_t)k * S + s]);
+            const double ddx = mi64(a.xc0[c] - xi, R.per[0], R.L[0]);
+            const double ddy = mi64(a.xc0[C + c] - yi, R.per[1], R.L[1]);
+            const double ddz = mi64(a.xc0[2 * C + c] + z_ind - zi, R.per[2], R.L[2]);
+            const double y2 = ddx * ddx + ddy * ddy + ddz * ddz;
+            if (y2 < P.rcm2) {
+                const float yinv = rsqrtf((float)y2);
+                float v, dv;
+                Q.morse((float)y2 * yinv, v, dv);
+                add_vir(W, (double)(dv * yinv), ddx, ddy, ddz);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a.vir[k * S + s] = W[k];
+}
+
+// the same in FP64 over the Verlet list (pairs within rc), FP64 potential forms
+template <int TPA>
+__global__ void __launch_bounds__(256) k_virial_fp64(DevArgs a, PotDev P)
+{
+    const int A = blockDim.x / TPA;
+    const int g = threadIdx.x / TPA, lane = threadIdx.x % TPA;
+    const int s = blockIdx.x * A + g;
+    const int r = a.tile_rep[(blockIdx.x * A) / MD_TILE];
+    const RepDev &R = a.rep[r];
+    const bool real = (s - R.slot_off) < R.n_atoms;
+    const size_t S = a.S, C = a.C;
+    const double *x = a.xs[buf_step(a)];
+    double w[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (real) {
+        const double xi = x[s], yi = x[S + s], zi = x[2 * S + s];
+        const double2 fmi = a.fm64[s];
+        const int n = a.cnt[s];
+        for (int k = lane; k < n; k += TPA) {
+            const int j = (int)((unsigned)__ldg(&a.nbr[(size_t)k * S + s]) & MD_J_MASK);
+            const double dx = mi64(x[j] - xi, R.per[0], R.L[0]);
+            const double dy = mi64(x[S + j] - yi, R.per[1], R.L[1]);
+            const double dz = mi64(x[2 * S + j] - zi, R.per[2], R.L[2]);
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < P.rc2) {
+                const double2 fmj = a.fm64[j];
+                const double rr = sqrt(r2);
+                double f, df, ph, dph;
+                f_64(P, rr, f, df);
+                phi_64(P, rr, ph, dph);
+                add_vir(w, ((fmi.x + fmj.x) * df + (fmi.y + fmj.y) * 2.0 * f * df + dph) / rr, dx, dy, dz);
+            }
+        }
+        const int nc = a.cntc[s];
+        const double z_ind = a.rs[r].z_ind;
+        for (int k = lane; k < nc; k += TPA) {
+            const int c = __ldg(&a.nbrc[(size_t)k * S + s]);
+            const double ddx = mi64(a.xc0[c] - xi, R.per[0], R.L[0]);
+            const double ddy = mi64(a.xc0[C + c] - yi, R.per[1], R.L[1]);
+            const double ddz = mi64(a.xc0[2 * C + c] + z_ind - zi, R.per[2], R.L[2]);
+            const double y2 = ddx * ddx + ddy * ddy + ddz * ddz;
+            if (y2 < P.rcm2) {
+                const double y = sqrt(y2);
+                double v, dv;
+                morse_64(P, y, v, dv);
+                add_vir(w, dv / y, ddx, ddy, ddz);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = TPA / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k] += __shfl_xor_sync(0xffffffffu, w[k], o);
+    if (real && lane == 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a.vir[k * S + s] = w[k];
+}
+
 // per-replica sums of the CTA partials in a fixed order.  MD_RED_CHUNKS CTAs per replica
 // each sum a contiguous run of the partials (thread t adds blocks t, t + B, ... of all six
 // terms together; the lanes of a warp by a fixed shuffle tree; thread 0 the warp sums in
@@ -1862,6 +2010,29 @@ cudaError_t launch_force_split(const DevArgs &a, const PotDev &p, const LaunchCf
     case 2: force_t<2>(a, p, c.block, integrate, energies, s); break;
     case 4: force_t<4>(a, p, c.block, integrate, energies, s); break;
     default: force_t<8>(a, p, c.block, integrate, energies, s); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int TPA>
+static void vir_t(const DevArgs &a, const PotDev &p, int block, cudaStream_t s)
+{
+    const int A = block / TPA;
+    if (a.mixed) {
+        if (p.q.ipow == 3) k_virial_mixed<TPA, 3><<<a.S / A, block, 0, s>>>(a, p);
+        else k_virial_mixed<TPA, 0><<<a.S / A, block, 0, s>>>(a, p);
+    } else {
+        k_virial_fp64<TPA><<<a.S / A, block, 0, s>>>(a, p);
+    }
+}
+
+cudaError_t launch_virial(const DevArgs &a, const PotDev &p, const LaunchCfg &c, cudaStream_t s)
+{
+    switch (c.tpa) {
+    case 1: vir_t<1>(a, p, c.block, s); break;
+    case 2: vir_t<2>(a, p, c.block, s); break;
+    case 4: vir_t<4>(a, p, c.block, s); break;
+    default: vir_t<8>(a, p, c.block, s); break;
     }
     return cudaGetLastError();
 }

@@ -27,16 +27,18 @@ def run(sim, replica: int = 0, relax_steps: int = 0, depth_max: float = 3.08, sp
     relax (indenter at rest), load (downwards at `speed` A/fs until the depth reaches
     `depth_max`) and unload (upwards at `speed` until the depth is back to `unload_to`,
     default the depth at the start of loading).  Every `sample_every` steps the step,
-    indenter displacement, depth and load are recorded.  Returns the samples as arrays
+    indenter displacement, depth, load, temperature and potential energy are recorded
+    (the time histories of Sec. 3.1).  Returns the samples as arrays
     and the index of the first unloading sample."""
     if speed <= 0 or sample_every < 1:
         raise ValueError("speed > 0 and sample_every >= 1 are required")
-    rec = {"step": [], "z_ind": [], "depth": [], "load": [], "phase": []}
+    rec = {"step": [], "z_ind": [], "depth": [], "load": [], "temperature": [], "potential": [], "phase": []}
 
     def sample(phase):
         e = sim.energy(replica)
         rec["step"].append(e["step"]); rec["z_ind"].append(e["z_indenter"])
         rec["depth"].append(e["depth"]); rec["load"].append(e["load"]); rec["phase"].append(phase)
+        rec["temperature"].append(e["temperature"]); rec["potential"].append(e["potential"])
         return e
 
     sim.set_indenter_velocity(replica, 0.0)

@@ -80,7 +80,7 @@ _lib = None
 EXPORTS = ["md_init", "md_build_neighbors", "md_compute_forces", "md_step", "md_step_profiled",
            "md_get_energy", "md_get_forces", "md_get_indenter_load", "md_get_state", "md_set_state",
            "md_get_neighbors", "md_get_info", "md_last_error", "md_free", "md_version", "md_forces_small",
-           "md_set_indenter_velocity"]
+           "md_set_indenter_velocity", "md_get_virial"]
 
 
 def lib(build: bool = True):
@@ -105,6 +105,7 @@ def lib(build: bool = True):
     L.md_get_state.argtypes = [vp, C.c_int32, vp, vp, vp, vp]
     L.md_set_state.argtypes = [vp, C.c_int32, vp, vp, C.c_double, C.c_int64]
     L.md_set_indenter_velocity.argtypes = [vp, C.c_int32, C.c_double]
+    L.md_get_virial.argtypes = [vp, C.c_int32, vp]
     L.md_get_neighbors.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, C.c_int32]
     L.md_get_info.argtypes = [vp, vp]
     L.md_last_error.argtypes = [vp]
@@ -216,6 +217,12 @@ def md_get_state(h, replica: int, n_cr: int, x: Optional[np.ndarray] = None, v: 
 
 def md_set_state(h, replica: int, x: Optional[np.ndarray], v: Optional[np.ndarray], z_ind: float, step: int):
     _check(h, lib().md_set_state(h, int(replica), _ptr(x), _ptr(v), float(z_ind), int(step)))
+
+
+def md_get_virial(h, replica: int, n_cr: int, out: Optional[np.ndarray] = None):
+    out = np.empty((n_cr, 6)) if out is None else out
+    _check(h, lib().md_get_virial(h, int(replica), _ptr(out)))
+    return out
 
 
 def md_set_indenter_velocity(h, replica: int, v_ind: float):
@@ -356,6 +363,10 @@ class MD:
         x = None if x is None else np.ascontiguousarray(x, np.float64)
         v = None if v is None else np.ascontiguousarray(v, np.float64)
         md_set_state(self.h, r, x, v, z_ind, step)
+
+    def virial(self, r: int = 0):
+        """Per-atom virial (n, 6: xx, yy, zz, xy, xz, yz; eV) of replica r."""
+        return md_get_virial(self.h, r, self.n[r])
 
     def set_indenter_velocity(self, r: int, v_ind: float):
         md_set_indenter_velocity(self.h, r, v_ind)
