@@ -95,6 +95,7 @@ struct md_handle {
     HostPin *hp = nullptr;
     int unroll = 1;
     bool forces_valid = false;
+    bool energies_valid = false;   // the energy sums belong to the current state
     std::vector<cudaEvent_t> ev;
     std::string err;
 };
@@ -165,16 +166,19 @@ int clear_err(md_t *h)
 
 // density and forces at the current positions (no integration); in mixed precision the force
 // kernel also makes the next step's drift from this state, so that the next step needs no
-// k_verlet1.  before_force: an event the force kernel waits for (it reads the velocities)
-int forces_now(md_t *h, cudaStream_t s, cudaEvent_t before_force = nullptr)
+// k_verlet1.  before_force: an event the force kernel waits for (it reads the velocities).
+// energies = false leaves the energy sums stale (md_get_energy then evaluates them).
+int forces_now(md_t *h, cudaStream_t s, cudaEvent_t before_force = nullptr, bool energies = true)
 {
     const bool mixed = h->a.mixed != 0;
+    const int en = energies || !mixed;   // the FP64 kernels always sum the energies
     if (mixed) CU(launch_drift_prep(h->a, s));
-    CU(launch_density(h->a, h->pot, h->cfg, 1, s));
+    CU(launch_density(h->a, h->pot, h->cfg, en, s));
     if (before_force) CU(cudaStreamWaitEvent(s, before_force, 0));
-    CU(launch_force(h->a, h->pot, h->cfg, mixed ? 2 : 0, 1, s));
+    CU(launch_force(h->a, h->pot, h->cfg, mixed ? 2 : 0, en, s));
     h->drift = mixed;
-    CU(launch_reduce(h->a, h->cfg, s));
+    if (en) CU(launch_reduce(h->a, h->cfg, s));
+    h->energies_valid = en != 0;
     return MD_OK;
 }
 
@@ -748,7 +752,10 @@ int md_step(md_t *h, int64_t n)
         for (int64_t k = 0; k < n; ++k)
             if ((rc = step_direct(h, nullptr, nullptr, k == n - 1))) return rc;
     }
-    if (n > 0) CU(launch_reduce(h->a, h->cfg, h->stream));
+    if (n > 0) {
+        CU(launch_reduce(h->a, h->cfg, h->stream));
+        h->energies_valid = true;
+    }
     DevStatus st;
     if ((rc = read_status(h, &st))) return rc;
     return status_to_code(h, st);
@@ -783,6 +790,7 @@ int md_step_profiled(md_t *h, int64_t n, md_phase_times *out)
         float ms;
         CU(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
         out->reduce += ms;
+        h->energies_valid = true;
     }
     DevStatus st;
     if ((rc = read_status(h, &st))) return rc;
@@ -794,6 +802,10 @@ int md_get_energy(md_t *h, int32_t r, md_energy *out)
     int rc = check_replica(h, r);
     if (rc) return rc;
     if (!out) return fail(h, MD_ERR_ARG, "md_get_energy: null output");
+    if (!h->energies_valid) {   // a state set since the last sums: evaluate them now
+        if ((rc = ensure_forces(h))) return rc;
+        if (!h->energies_valid && (rc = forces_now(h, h->stream))) return rc;
+    }
     CU(cudaMemcpyAsync(&h->hp->E, h->a.en + r, sizeof(RepEnergy), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaMemcpyAsync(&h->hp->rs, h->a.rs + r, sizeof(RepState), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaMemcpyAsync(&h->hp->st, h->a.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
@@ -909,7 +921,9 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
         return ensure_forces(h);
     }
     int rc2;
-    if ((rc2 = forces_now(h, h->stream, v3n ? h->xev1 : nullptr))) return rc2;
+    // the energy sums are left to md_get_energy: a caller that sets a state and steps on
+    // reads those of the step
+    if ((rc2 = forces_now(h, h->stream, v3n ? h->xev1 : nullptr, false))) return rc2;
     DevStatus st;
     if ((rc2 = read_status(h, &st))) return rc2;
     if ((rc2 = status_to_code(h, st))) return rc2;
