@@ -1,18 +1,26 @@
 // md_kernels.cu -- the sm_103a kernels of libmd and their launchers.
 //
 // Per time step (Fig. 5 / Table 1 of Pal et al., arXiv:1507.07068):
-//   k_decide    Task 1 decision (Sec. 2.6 skin/2 rule on max_i |x_i - x_build,i|, which the
-//               previous step's k_verlet1 reduced) -> device flag + graph conditional
+//   k_decide    Task 1 decision (Sec. 2.6 skin/2 rule on max_i |x_i - x_build,i|, reduced by
+//               the drift that made the positions) -> device flag + graph conditional; Task 2
+//               (the indenter moves by v dt); advances the position-buffer counter
 //   [rebuild]   Task 1 rebuild: k_bin (wrap, FP64 cell keys, histogram), scan, k_scatter,
 //               k_cellsort (ascending caller id within a cell), k_gather/k_copyback
-//               (permute every per-atom array), k_nbr (full Cr-Cr Verlet list), k_nbrc
-//               (Cr-C list through the indenter's own cell grid), k_build_done
-//   k_verlet1   Tasks 2+3: indenter move, half kick + drift (Eqs. A11-A12), refresh of the
-//               FP32 cell-relative positions, displacement test for the next decision
-//   k_density   Task 4a: rho_i, P_i (Eq. A2) -> F'(rho_i), M'(P_i), F(rho_i), M(P_i) (Eq. A3)
+//               (permute every per-atom array), k_nbr (full Cr-Cr Verlet list), k_nbrc /
+//               k_nbrc_near (Cr-C list through the indenter's own cell grid), k_build_done
+//   k_verlet1   Task 3 (half kick + drift, Eqs. A11-A12, the FP32 cell-relative positions,
+//               the displacement tests) into the other position buffer: every step in FP64;
+//               in mixed precision only after a list build (the force epilogue drifts)
+//   k_density   Task 4a: rho_i, P_i (Eq. A2) -> F'(rho_i), M'(P_i), F(rho_i), M(P_i) (Eq. A3);
+//               rebuilds the inner list (Sec. 2.6) when its own displacement test asks
+//   k_morse_mixed  Task 4c for the atoms under the indenter (one warp per atom)
 //   k_force     Task 4b,c + 5: Eq. (1) with the M term (A6-A8, A10), Morse (A5, A9),
-//               indenter load; epilogue: closing half kick (Task 5), kinetic energy
+//               indenter load; epilogue: closing half kick (Task 5) and, in mixed
+//               precision, the next step's Task 3
 //   k_reduce    per-replica FP64 sums of the CTA partials in a fixed order (once per call)
+// Outside the step: k_state_prep / k_state_scan / k_state_need (md_set_state),
+// k_drift_prep (the drift made by a force evaluation outside a step), k_virial_* (per-atom
+// virial), the allocation-free small-system kernels (md_forces_small).
 // Every per-atom kernel writes only its own atom (full neighbour list: no atomics in
 // the force path); energy and load sums are warp-shuffle -> CTA partial -> fixed-order
 // final pass, so results do not depend on scheduling.
