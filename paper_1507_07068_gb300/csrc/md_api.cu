@@ -60,7 +60,7 @@ __global__ void k_state_out(const double *s0, const double *s1, const DevStatus 
 // small device-to-host readbacks land in pinned memory (a copy into pageable memory goes
 // through a driver bounce buffer and costs more than the copy itself)
 struct HostPin {
-    DevStatus st;
+    DevStatus st{};
     RepEnergy E;
     RepState rs;
     int32_t flag, verlet;
@@ -197,7 +197,7 @@ int rebuild_growing(md_t *h)
         int rc = clear_err(h);
         if (rc) return rc;
         if ((rc = rebuild_now(h))) return rc;
-        DevStatus st;
+        DevStatus st{};
         if ((rc = read_status(h, &st))) return rc;
         bool grow = false;
         if ((st.err & MDE_OVERFLOW) && st.max_cnt > h->a.kmax) {
@@ -671,7 +671,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     CUI(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
     CUI(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
     CUI(cudaHostAlloc((void **)&h->hp, sizeof(HostPin), cudaHostAllocDefault));
-    memset(h->hp, 0, sizeof(HostPin));
+    *h->hp = HostPin{};
     h->ev.resize(8);
     for (auto &e : h->ev) CUI(cudaEventCreate(&e));
     h->unroll = 8;
@@ -680,7 +680,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     INIT_FAIL(rebuild_growing(h));
     INIT_FAIL(forces_now(h, h->stream));
     {
-        DevStatus st;
+        DevStatus st{};
         INIT_FAIL(read_status(h, &st));
         INIT_FAIL(status_to_code(h, st));
         st.rebuilds = 0; st.step = 0; st.since_build = 0;
@@ -756,7 +756,7 @@ int md_step(md_t *h, int64_t n)
         CU(launch_reduce(h->a, h->cfg, h->stream));
         h->energies_valid = true;
     }
-    DevStatus st;
+    DevStatus st{};
     if ((rc = read_status(h, &st))) return rc;
     return status_to_code(h, st);
 }
@@ -792,7 +792,7 @@ int md_step_profiled(md_t *h, int64_t n, md_phase_times *out)
         out->reduce += ms;
         h->energies_valid = true;
     }
-    DevStatus st;
+    DevStatus st{};
     if ((rc = read_status(h, &st))) return rc;
     return status_to_code(h, st);
 }
@@ -924,7 +924,7 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     // the energy sums are left to md_get_energy: a caller that sets a state and steps on
     // reads those of the step
     if ((rc2 = forces_now(h, h->stream, v3n ? h->xev1 : nullptr, false))) return rc2;
-    DevStatus st;
+    DevStatus st{};
     if ((rc2 = read_status(h, &st))) return rc2;
     if ((rc2 = status_to_code(h, st))) return rc2;
     h->forces_valid = true;
@@ -947,7 +947,7 @@ int md_get_virial(md_t *h, int32_t r, double *out6n)
     k_vir_out<<<(n + 255) / 256, 256, 0, h->stream>>>(h->a.vir, h->stage, h->a.orig, R.slot_off, n, h->a.S);
     CU(cudaGetLastError());
     CU(cudaMemcpyAsync(out6n, h->stage, 6 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    DevStatus st;
+    DevStatus st{};
     if ((rc = read_status(h, &st))) return rc;
     return status_to_code(h, st);
 }
@@ -1007,7 +1007,7 @@ int md_get_neighbors(md_t *h, int32_t r, int32_t which, int32_t *cell_xyz, int32
 int md_get_info(md_t *h, int64_t *out9)
 {
     if (!h || !out9) return MD_ERR_ARG;
-    DevStatus st;
+    DevStatus st{};
     int rc = read_status(h, &st);
     if (rc) return rc;
     out9[0] = h->n_rep; out9[1] = h->n_cr; out9[2] = h->n_c; out9[3] = h->a.S; out9[4] = h->a.total_cells;

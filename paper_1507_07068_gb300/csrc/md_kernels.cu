@@ -309,21 +309,6 @@ __device__ __forceinline__ void cubic32(const float4 *T, int n, float s, float i
 }
 
 struct Pot32 : PotF32 {   // the FP32 constants (filled on the host) with the FP32 forms
-    __device__ __forceinline__ void f(float r, float &v, float &dv) const
-    {
-        if (tabulated) { cubic32(tf, nf, fmaf(r, inv_hf, -rmin_s_f), inv_hf, v, dv); return; }
-        float fr = exp2f(lf0 - beta * __log2f(r));
-        v = fr - f_rc - (r - rc) * df_rc;
-        dv = -beta * fr / r - df_rc;
-    }
-    __device__ __forceinline__ void phi(float r, float &v, float &dv) const
-    {
-        if (tabulated) { cubic32(tp, nf, fmaf(r, inv_hf, -rmin_s_f), inv_hf, v, dv); return; }
-        float t = fmaf(r, inv_re, -d);
-        if (t > 0.0f) { v = dv = 0.0f; return; }
-        v = t * t * fmaf(fmaf(fmaf(b3, t, b2), t, b1), t, b0);
-        dv = t * fmaf(fmaf(fmaf(5.0f * b3, t, 4.0f * b2), t, 3.0f * b1), t, 2.0f * b0) * inv_re;
-    }
     __device__ __forceinline__ void morse(float y, float &v, float &dv) const
     {
         if (tabulated) { cubic32(tm, nm, fmaf(y, inv_hm, -rmin_s_m), inv_hm, v, dv); return; }
