@@ -319,7 +319,10 @@ def run_gpu(args):
             k64 = max(5, min(args.steps, args.fp64_steps))
             a0.record(stream); s64.step(k64); a1.record(stream); torch.cuda.synchronize()
             variants["fp64"] = {"value": n_cr * k64 / (a0.elapsed_time(a1) * 1e-3), "steps": k64, "skin_A": 0.3,
-                                "ms_per_step": a0.elapsed_time(a1) / k64}
+                                "ms_per_step": a0.elapsed_time(a1) / k64,
+                                # the bound of this form: the CUDA cores' FP64 FMA rate, measured here
+                                # (the FP64 pipe share of its kernels is in profiles/fp64_kernels_1M.md)
+                                "fp64_fma_peak_tflops": md.md_probe_fp64_fma() * 1e-12}
             s64.close()
         if args.workload != "batched":
             bw = mi.make_workload("batched")

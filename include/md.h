@@ -311,6 +311,13 @@ int md_forces_small(const md_params *params, int32_t n_cr, const double *x_cr, i
                     const int32_t periodic[3], double *F, double *energy, void *stream,
                     char *errbuf, size_t errlen);
 
+/* Measurement helper (no counterpart in the paper): the FP64 FMA rate of the current
+ * device's CUDA cores, from eight independent FMA chains per thread over 8 CTAs of 256
+ * threads per SM, timed with CUDA events; *flops_per_s counts 2 flops per FMA, *ms (may be
+ * NULL) is one launch's time.  The FP64 form of the force kernels is bounded by this rate.
+ * Allocates and frees its own buffer; synchronises.  Errors: MD_ERR_ARG, MD_ERR_CUDA. */
+int md_probe_fp64_fma(double *flops_per_s, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,7 +12,7 @@
 
 #include "md_internal.h"
 
-#define MD_ABI_VERSION 4
+#define MD_ABI_VERSION 5
 
 namespace {
 
@@ -1016,6 +1016,59 @@ int md_get_info(md_t *h, int64_t *out9)
 }
 
 }  // extern "C"
+
+// ============================================================================ FP64 FMA probe
+
+namespace {
+// eight independent FMA chains per thread; the result is stored so that nothing is elided
+__global__ void __launch_bounds__(256) k_fp64_fma_probe(double *out, int iters, double b, double c)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double a0 = t * 1e-9, a1 = a0 + 1.0, a2 = a0 + 2.0, a3 = a0 + 3.0, a4 = a0 + 4.0, a5 = a0 + 5.0,
+           a6 = a0 + 6.0, a7 = a0 + 7.0;
+    for (int i = 0; i < iters; ++i) {
+        a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
+        a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
+    }
+    out[t] = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+}
+}  // namespace
+
+extern "C" int md_probe_fp64_fma(double *flops_per_s, double *ms)
+{
+    if (!flops_per_s) return MD_ERR_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return MD_ERR_CUDA;
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    double *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStream_t st = nullptr;
+    int rc = MD_OK;
+    float t = 0.f;
+    if (cudaMalloc((void **)&out, sizeof(double) * (size_t)blocks * threads) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = MD_ERR_CUDA;
+    } else {
+        k_fp64_fma_probe<<<blocks, threads, 0, st>>>(out, iters, 0.999999, 1e-7);   // warm-up
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < 5; ++k) k_fp64_fma_probe<<<blocks, threads, 0, st>>>(out, iters, 0.999999, 1e-7);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess ||
+            cudaGetLastError() != cudaSuccess)
+            rc = MD_ERR_CUDA;
+    }
+    if (rc == MD_OK) {
+        *flops_per_s = 5.0 * 2.0 * 8.0 * iters * (double)blocks * threads / (t * 1e-3);
+        if (ms) *ms = t / 5.0;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (out) cudaFree(out);
+    return rc;
+}
 
 // ============================================================================ md_forces_small
 

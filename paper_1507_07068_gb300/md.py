@@ -80,7 +80,7 @@ _lib = None
 EXPORTS = ["md_init", "md_build_neighbors", "md_compute_forces", "md_step", "md_step_profiled",
            "md_get_energy", "md_get_forces", "md_get_indenter_load", "md_get_state", "md_set_state",
            "md_get_neighbors", "md_get_info", "md_last_error", "md_free", "md_version", "md_forces_small",
-           "md_set_indenter_velocity", "md_get_virial"]
+           "md_set_indenter_velocity", "md_get_virial", "md_probe_fp64_fma"]
 
 
 def lib(build: bool = True):
@@ -106,6 +106,7 @@ def lib(build: bool = True):
     L.md_set_state.argtypes = [vp, C.c_int32, vp, vp, C.c_double, C.c_int64]
     L.md_set_indenter_velocity.argtypes = [vp, C.c_int32, C.c_double]
     L.md_get_virial.argtypes = [vp, C.c_int32, vp]
+    L.md_probe_fp64_fma.argtypes = [vp, vp]
     L.md_get_neighbors.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, C.c_int32]
     L.md_get_info.argtypes = [vp, vp]
     L.md_last_error.argtypes = [vp]
@@ -223,6 +224,15 @@ def md_get_virial(h, replica: int, n_cr: int, out: Optional[np.ndarray] = None):
     out = np.empty((n_cr, 6)) if out is None else out
     _check(h, lib().md_get_virial(h, int(replica), _ptr(out)))
     return out
+
+
+def md_probe_fp64_fma() -> float:
+    """FP64 FMA rate of the current device's CUDA cores (flop/s, 2 per FMA)."""
+    f = C.c_double(); ms = C.c_double()
+    code = lib().md_probe_fp64_fma(C.cast(C.pointer(f), C.c_void_p), C.cast(C.pointer(ms), C.c_void_p))
+    if code != MD_OK:
+        raise MDError(code, "md_probe_fp64_fma failed")
+    return f.value
 
 
 def md_set_indenter_velocity(h, replica: int, v_ind: float):
