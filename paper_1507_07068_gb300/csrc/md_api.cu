@@ -397,6 +397,11 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     if (!(tpa == 1 || tpa == 2 || tpa == 4 || tpa == 8) || block < 32 || block > 256 || block % 32 ||
         MD_TILE % (block / tpa) != 0)
         return fail(nullptr, MD_ERR_ARG, "md_init: tpa must be 1, 2, 4 or 8 and block a multiple of 32 in [32, 256] with %d %% (block/tpa) == 0", MD_TILE);
+    for (int32_t r = 0; r < n_replicas; ++r) {   // host-side checks before any device work
+        const md_system &y = sys[r];
+        if (y.n_cr < 1 || y.n_c < 0 || !y.x_cr || !y.v_cr || (y.n_c > 0 && !y.x_c) || !(y.dt > 0) || !(y.mass_cr > 0))
+            return fail(nullptr, MD_ERR_ARG, "md_init: replica %d: need n_cr >= 1, positions, velocities, dt > 0, mass > 0", r);
+    }
     h = new md_t();
     h->stream = (cudaStream_t)cuda_stream;
     h->opt = *opt;

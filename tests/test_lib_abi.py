@@ -71,6 +71,10 @@ def test_bad_arguments_rejected_before_any_device_work(libmd):
     opt.precision = md.MD_MIXED
     opt.tpa = 3
     assert L.md_init(sysarr, 1, C.byref(opt), None, C.byref(h)) == md.MD_ERR_ARG
+    opt.tpa = 0
+    # an empty replica (no film atoms) is rejected, not run
+    assert L.md_init(sysarr, 1, C.byref(opt), None, C.byref(h)) == md.MD_ERR_ARG
+    assert b"n_cr >= 1" in L.md_last_error(None) and not h.value
     md.md_free(None)
 
 
