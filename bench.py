@@ -261,7 +261,7 @@ def run_gpu(args):
     kmean = float(cnt.mean())
     inner_skin = args.inner_skin if args.inner_skin > 0 else (0.0 if args.inner_skin < 0 else 0.1)
     kin, kskin = inner_mean(sim, reps[0], (params["rc"], params["rc"] + inner_skin))
-    phases = {k: prof[k] / prof["steps"] for k in ("skin", "rebuild", "verlet1", "density", "force", "reduce")}
+    phases = {k: prof[k] / prof["steps"] for k in ("skin", "rebuild", "verlet1", "density", "morse", "force", "reduce")}
     dom = "force" if phases["force"] >= phases["density"] else "density"
     peak, peak_kind = load_peaks()
     bytes_per_launch = algorithmic_bytes(dom, kmean, kin, kskin, args.precision) * n_cr

@@ -158,13 +158,15 @@ typedef struct md_energy {
 /* Per-phase device time of md_step_profiled, milliseconds summed over its steps:
  * skin = the Task 1 decision (with Task 2), rebuild = binning + lists (when decided),
  * verlet1 = Task 3 with the displacement test the next decision uses, density / force =
- * Task 4 (force includes Task 5).  In mixed precision the force kernel also makes the next
- * step's Task 3 from the state it has just completed (as do the force evaluations of
- * md_init, md_set_state and md_compute_forces); verlet1 then runs only on steps that
- * rebuild the lists or follow md_build_neighbors.  reduce = the energy sums, which run once
- * at the end of the call. */
+ * Task 4 (force includes Task 5), morse = the Cr-C sums of the atoms under the indenter
+ * (mixed precision: their own kernel, run between density and force here and beside the
+ * density kernel in md_step; FP64: inside force, morse = 0).  In mixed precision the
+ * force kernel also makes the next step's Task 3 from the state it has just completed
+ * (as do the force evaluations of md_init, md_set_state and md_compute_forces); verlet1
+ * then runs only on steps that rebuild the lists or follow md_build_neighbors.  reduce =
+ * the energy sums, which run once at the end of the call. */
 typedef struct md_phase_times {
-    double skin, rebuild, verlet1, density, force, reduce;
+    double skin, rebuild, verlet1, density, morse, force, reduce;
     int64_t steps, rebuilds;
 } md_phase_times;
 

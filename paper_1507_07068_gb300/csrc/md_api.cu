@@ -12,7 +12,7 @@
 
 #include "md_internal.h"
 
-#define MD_ABI_VERSION 5
+#define MD_ABI_VERSION 6
 
 namespace {
 
@@ -330,8 +330,10 @@ int step_direct(md_t *h, cudaEvent_t *ev, bool *rebuilt, bool energies)
     if (ev) CU(cudaEventRecord(ev[4], s));
     CU(launch_density(h->a, h->pot, h->cfg, energies ? 1 : 0, s));
     if (ev) CU(cudaEventRecord(ev[5], s));
-    CU(launch_force(h->a, h->pot, h->cfg, 1, energies ? 1 : 0, s));
+    if (h->a.mixed) CU(launch_morse(h->a, h->pot, s));
     if (ev) CU(cudaEventRecord(ev[6], s));
+    CU(launch_force_split(h->a, h->pot, h->cfg, 1, energies ? 1 : 0, 0, s));
+    if (ev) CU(cudaEventRecord(ev[7], s));
     h->drift = h->a.mixed != 0;
     if (rebuilt) *rebuilt = flag != 0;
     return MD_OK;
@@ -776,14 +778,15 @@ int md_step_profiled(md_t *h, int64_t n, md_phase_times *out)
     for (int64_t k = 0; k < n; ++k) {
         bool rebuilt = false;
         if ((rc = step_direct(h, h->ev.data(), &rebuilt, k == n - 1))) return rc;
-        CU(cudaEventSynchronize(h->ev[6]));
-        float ms[6];
-        for (int p = 0; p < 6; ++p) CU(cudaEventElapsedTime(&ms[p], h->ev[p], h->ev[p + 1]));
+        CU(cudaEventSynchronize(h->ev[7]));
+        float ms[7];
+        for (int p = 0; p < 7; ++p) CU(cudaEventElapsedTime(&ms[p], h->ev[p], h->ev[p + 1]));
         out->skin += ms[0];
         out->rebuild += ms[2];
         out->verlet1 += ms[3];
         out->density += ms[4];
-        out->force += ms[5];
+        out->morse += ms[5];
+        out->force += ms[6];
         out->steps += 1;
         out->rebuilds += rebuilt ? 1 : 0;
     }

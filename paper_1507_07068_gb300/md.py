@@ -63,7 +63,7 @@ class md_energy(C.Structure):
 
 
 class md_phase_times(C.Structure):
-    _fields_ = [(n, C.c_double) for n in ("skin", "rebuild", "verlet1", "density", "force", "reduce")] + \
+    _fields_ = [(n, C.c_double) for n in ("skin", "rebuild", "verlet1", "density", "morse", "force", "reduce")] + \
                [("steps", C.c_int64), ("rebuilds", C.c_int64)]
 
     def as_dict(self) -> dict:
