@@ -1,6 +1,6 @@
 """Dynamics on the GPU: NVE energy conservation of the FP64 and mixed-precision forms
-(SURVEY-style pin (ix): static indenter, no fixed atoms, periodic x, y), the mixed form's
-trajectory against the FP64 form, and the autotuner."""
+(static indenter, no fixed atoms, periodic x, y: nothing does work on the film), the mixed
+form's trajectory against the FP64 form, and the autotuner."""
 import json
 import os
 
@@ -53,9 +53,11 @@ def test_nve_energy_drift(md, params):
         assert dev < 5e-5, (prec, dev)
         assert abs(slope) < 2e-5, (prec, slope)
     print("NVE", json.dumps(out))
-    os.makedirs("gpurun_out", exist_ok=True)
-    with open(os.path.join("gpurun_out", "nve_drift.json"), "w") as fh:
-        json.dump(out, fh, indent=1)
+    res = os.environ.get("MD_RESULTS_DIR")   # optional: keep the numbers as a file
+    if res:
+        os.makedirs(res, exist_ok=True)
+        with open(os.path.join(res, "nve_drift.json"), "w") as fh:
+            json.dump(out, fh, indent=1)
 
 
 def test_mixed_trajectory_tracks_fp64(md, params):
