@@ -1306,6 +1306,13 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
                     const int k = k0 + u * TPA;
                     e[u] = k < n ? ld_stream(&a.inner[(size_t)k * S + s]) : (unsigned)s;
                 }
+                // the rows two batches ahead on their way to L1 (-2.5 % here; the same in
+                // k_force, whose L1 holds the F', M' gathers too, measured +7 %)
+#pragma unroll
+                for (int u = 0; u < MD_UNROLL; ++u) {
+                    const int k = k0 + (u + 2 * MD_UNROLL) * TPA;
+                    if (k < n) asm volatile("prefetch.global.L1 [%0];" ::"l"(&a.inner[(size_t)k * S + s]));
+                }
                 float4 pj[MD_UNROLL];
 #pragma unroll
                 for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&pp[e[u] & MD_J_MASK]);
