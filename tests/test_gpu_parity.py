@@ -262,7 +262,13 @@ def test_graph_and_direct_launch_bitwise_equal(md, params):
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
     assert a.energy(0) == b.energy(0)
     t = b.step_profiled(5)
-    assert t["steps"] == 5 and t["force"] > 0 and t["density"] > 0
+    assert t["steps"] == 5 and t["force"] > 0 and t["density"] > 0 and t["morse"] > 0
+    # the profiled steps (direct launches, the Morse kernel in its own timed phase) take
+    # the same trajectory
+    a.step(5)
+    xa, va, _, _ = a.state(0)
+    xb, vb, _, _ = b.state(0)
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
 
 
 def test_interleaved_calls_keep_the_trajectory(md, params):
