@@ -1,6 +1,7 @@
-"""Parity at the full size of the 1,000,000-atom film in the launch configuration the
-benchmark times (mixed precision, default launch shape, cell order and lists as built by
-the library), against the FP64 oracle over every atom."""
+"""Parity at full size in the launch configuration the benchmark times (mixed precision,
+default launch shape, cell order and lists as built by the library): the 1,000,000- and
+8,000,000-atom films against the FP64 oracle over every atom, and the 256-replica batch
+against the FP64 form."""
 import dataclasses
 
 import numpy as np
@@ -125,3 +126,32 @@ def test_fullsize_batched_mixed_against_fp64(md, params):
         worst = max(worst, err / bar)
     b64.close(); bm.close()
     print("batched: worst per-atom mixed force error over 256 replicas: %.2f of the bar" % worst)
+
+
+def test_fullsize_8m_mixed_forces_and_lists(md, params):
+    """The 8,000,000-atom film (200 x 200 x 100 cells, the largest configuration) after
+    100 mixed-precision steps: cells and a sample of neighbour sets bit-exact, and every
+    atom's mixed-precision force within 1e-5 of the FP64 oracle."""
+    oracle.set_threads(0)
+    rep0 = mi.make_workload("8M").replicas[0]
+    sim = md.MD([rep0], params, precision="mixed", skin=SKIN)
+    sim.step(100)
+    x, v, z, st = sim.state(0)
+    sim.close()
+    rep = dataclasses.replace(rep0, x_cr=x, v_cr=v, z_indenter0=z)
+    sim = md.MD([rep], params, precision="mixed", skin=SKIN)   # lists built from x
+    Fm = sim.forces(0)
+    cut = params["rc"] + SKIN
+    cell, cnt, nbr = sim.neighbors(0, 0)
+    sim.close()
+    assert np.array_equal(cell, oracle.cell_coords(rep.x_cr, rep.box_lo, rep.box_hi, rep.periodic, cut))
+    off, idx = oracle.neighbors(rep.x_cr, rep.box_lo, rep.box_hi, rep.periodic, cut, method=1)
+    rng = np.random.default_rng(8)
+    for i in rng.choice(rep.n_cr, 3000, replace=False):
+        assert set(nbr[i, :cnt[i]].tolist()) == set(idx[off[i]:off[i + 1]].tolist())
+    del off, idx, nbr
+    ref = oracle.forces(oracle.Potential(params), rep.x_cr, rep.box_lo, rep.box_hi, rep.periodic,
+                        rep.x_c + np.array([0.0, 0.0, rep.z_indenter0]))
+    err = rel_force_err(Fm, ref["F"])
+    print("8M mixed: max %.2e p99 %.2e" % (err.max(), np.quantile(err, 0.99)))
+    assert err.max() <= 1e-5
