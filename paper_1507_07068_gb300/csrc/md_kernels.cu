@@ -1299,19 +1299,21 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
             if (lane == 0) a.pin[s] = pi;
         } else {
             const int n = a.icnt[s];
+            // the next batch's list entries are loaded while this batch is gathered and
+            // summed (as in k_force), so only the gather's latency stays on the path
+            unsigned en[MD_UNROLL];
+#pragma unroll
+            for (int u = 0; u < MD_UNROLL; ++u) {
+                const int k = lane + u * TPA;
+                en[u] = k < n ? ld_stream(&a.inner[(size_t)k * S + s]) : (unsigned)s;
+            }
             for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
                 unsigned e[MD_UNROLL];
 #pragma unroll
                 for (int u = 0; u < MD_UNROLL; ++u) {
-                    const int k = k0 + u * TPA;
-                    e[u] = k < n ? ld_stream(&a.inner[(size_t)k * S + s]) : (unsigned)s;
-                }
-                // the rows two batches ahead on their way to L1 (-2.5 % here; the same in
-                // k_force, whose L1 holds the F', M' gathers too, measured +7 %)
-#pragma unroll
-                for (int u = 0; u < MD_UNROLL; ++u) {
-                    const int k = k0 + (u + 2 * MD_UNROLL) * TPA;
-                    if (k < n) asm volatile("prefetch.global.L1 [%0];" ::"l"(&a.inner[(size_t)k * S + s]));
+                    e[u] = en[u];
+                    const int k = k0 + (u + MD_UNROLL) * TPA;
+                    en[u] = k < n ? ld_stream(&a.inner[(size_t)k * S + s]) : (unsigned)s;
                 }
                 float4 pj[MD_UNROLL];
 #pragma unroll
@@ -1410,23 +1412,35 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
         if (!real) return;
         const float2 fmi = a.fm32[s];
         const int n = a.icnt[s];
-        for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
-            unsigned e[MD_UNROLL];
+        // FU entries per lane per batch; the next batch's list entries are loaded while
+        // this batch's neighbours are gathered and summed, so only the gather's latency
+        // stays on each batch's path (2 entries: -2.5 % against 4 loaded together, which
+        // with the look-ahead would spill under the register bound)
+        constexpr int FU = 2;
+        unsigned en[FU];
 #pragma unroll
-            for (int u = 0; u < MD_UNROLL; ++u) {
-                const int k = k0 + u * TPA;
-                e[u] = k < n ? ld_stream(&a.inner[(size_t)k * S + s]) : (unsigned)s;
+        for (int u = 0; u < FU; ++u) {
+            const int k = lane + u * TPA;
+            en[u] = k < n ? ld_stream(&a.inner[(size_t)k * S + s]) : (unsigned)s;
+        }
+        for (int k0 = lane; k0 < n; k0 += TPA * FU) {
+            unsigned e[FU];
+#pragma unroll
+            for (int u = 0; u < FU; ++u) {
+                e[u] = en[u];
+                const int k = k0 + (u + FU) * TPA;
+                en[u] = k < n ? ld_stream(&a.inner[(size_t)k * S + s]) : (unsigned)s;
             }
-            float4 pj[MD_UNROLL];
-            float2 fmj[MD_UNROLL];
+            float4 pj[FU];
+            float2 fmj[FU];
 #pragma unroll
-            for (int u = 0; u < MD_UNROLL; ++u) {
+            for (int u = 0; u < FU; ++u) {
                 const unsigned j = e[u] & MD_J_MASK;
                 pj[u] = __ldg(&pp[j]);
                 fmj[u] = __ldg(&a.fm32[j]);
             }
 #pragma unroll
-            for (int u = 0; u < MD_UNROLL; ++u) {
+            for (int u = 0; u < FU; ++u) {
                 float dx, dy, dz;
                 disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
