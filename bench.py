@@ -146,30 +146,35 @@ def job_value(n_cr_per_rank: int, world: int, steps: int, ms_max: float) -> floa
 
 
 def algorithmic_bytes(kernel: str, kmean: float, kin: float, kskin: float, precision: str) -> float:
-    """Bytes per Cr atom that the kernel must move in a step (int32 lists, neighbour data
-    counted once): K = Verlet-list length, K_in = pairs within rc, K_skin = inner-list
-    length (pairs within rc + inner skin)."""
+    """Bytes per Cr atom the method must move in one launch of the kernel (int32 lists,
+    neighbour data counted once, assuming reuse in cell order), K_in = pairs within rc (the
+    paper's inner list, Sec. 2.6), K = Verlet-list length:
+      mixed k_density  cnt 4 + list 4K_in + own position 16 + (F', M') out 8     = 4K_in + 28
+      mixed k_force    cnt 4 + list 4K_in + position 16 + (F', M') 8 + force out 16 = 4K_in + 44,
+                       plus the integrator fused in its epilogue: x, v FP64 in and out 96,
+                       the FP32 position out 16, the fixed flag 1                  = 4K_in + 157
+    The FP64 form walks the Verlet list with FP64 coordinates: k_density 4K + 44,
+    k_force 4K + 121 (coordinates 24, (F', M') 16, force 24, v 48, flags 5)."""
     if precision == "mixed":
         if kernel == "density":
-            # a step that keeps the inner list: icnt 4 + inner 4K_skin + float4 position 16 +
-            # (F', M') out 8 (the list rebuilds, every few steps, are extra)
-            return 4 * kskin + 28
-        # icnt 4 + inner list 4K_skin + position 16 + (F', M') 8 + F out 24 + v(t+dt/2) in 24 +
-        # v out 24 + fixed 1 + cntc 4, and the next step's drift made in the epilogue: x in 24,
-        # x, v(t+3dt/2) out 48, cell-relative position out 16, the positions at the two list
-        # builds in 32, cell 4
-        return 4 * kskin + 229
+            return 4 * kin + 28
+        return 4 * kin + 44 + 113
     if kernel == "density":
-        return 4 * kmean + 44          # cnt + list + 3 FP64 coordinates 24 + (F', M') out 16
-    return 4 * kmean + 121             # cnt + list + coordinates 24 + (F', M') 16 + F 24 + v 48 + fixed + cntc
+        return 4 * kmean + 44
+    return 4 * kmean + 121
 
 
-def verlet1_bytes(precision: str) -> int:
-    """k_verlet1 per atom: x, v, F in (72), x, v(t+dt/2) out (48), cell 4, fixed 1; mixed adds
-    the positions at the two list builds in (32) and pos4 out (16), FP64 reads x_build (24).
-    In mixed precision it runs only on steps that rebuild the lists (the force epilogue makes
-    the drift otherwise)."""
-    return 125 + (48 if precision == "mixed" else 24)
+def moved_bytes(kernel: str, kin: float, kskin: float) -> float:
+    """Bytes per Cr atom this implementation's mixed kernels actually stream: the inner
+    list they walk (K_skin entries within rc + inner skin), and in k_force the separate
+    v(t + dt/2) array, the FP64 force store and the positions at the two list builds that
+    the fused displacement tests read."""
+    if kernel == "density":
+        return 4 * kskin + 28
+    # icnt 4 + inner list 4K_skin + position 16 + (F', M') 8 + F out 24 + v(t+dt/2) in 24 +
+    # v out 24 + fixed 1 + cntc 4, and the next step's drift: x in 24, x and v(t+3dt/2) out 48,
+    # position out 16, the positions at the two list builds in 32, cell 4
+    return 4 * kskin + 229
 
 
 def inner_mean(sim, rep, radii, sample: int = 20000, seed: int = 0):
@@ -255,8 +260,25 @@ def run_gpu(args):
     t_max = max_over_ranks(ms, dist)
     value = job_value(n_cr, ws, args.steps, t_max)
 
-    # ---- per-kernel device time (direct launches with CUDA events around each phase)
+    # ---- per-kernel device time (direct launches with CUDA events around each phase);
+    # profiled until at least one list rebuild has been timed (for the amortised rate)
     prof = sim.step_profiled(args.profile_steps)
+    while prof["rebuilds"] == 0 and prof["steps"] < 8 * args.profile_steps:
+        more = sim.step_profiled(args.profile_steps)
+        prof = {k: prof[k] + more[k] for k in prof}
+    # rebuild rate of the displacement rule, over an untimed stretch of steps
+    r0 = sim.energy(0)["rebuilds"]
+    sim.step(args.rate_steps)
+    rate = (sim.energy(0)["rebuilds"] - r0) / args.rate_steps
+    # one rebuild costs the list build plus the k_verlet1 that redoes the step's drift
+    ms_rebuild = ((prof["rebuild"] + prof["verlet1"]) / prof["rebuilds"]) if prof["rebuilds"] else None
+    value_amortised = None
+    if ms_rebuild is not None:
+        t_amort = t_max + (rate * args.steps - rebuilds) * ms_rebuild
+        value_amortised = {"value": job_value(n_cr, ws, args.steps, t_amort), "unit": UNIT,
+                           "rebuilds_per_step": rate, "ms_per_rebuild": ms_rebuild,
+                           "how": "timed steps + (rebuild rate x steps - rebuilds in the timed region) "
+                                  "x measured rebuild time"}
     _, cnt, _ = sim.neighbors(0, 0, kmax=1)
     kmean = float(cnt.mean())
     inner_skin = args.inner_skin if args.inner_skin > 0 else (0.0 if args.inner_skin < 0 else 0.1)
@@ -267,7 +289,7 @@ def run_gpu(args):
     bytes_per_launch = algorithmic_bytes(dom, kmean, kin, kskin, args.precision) * n_cr
     achieved = bytes_per_launch / (phases[dom] * 1e-3) / 1e9
     traffic = dram_traffic(args.workload, args.precision, dom)
-    # the whole step: every per-step kernel's algorithmic bytes (rebuilds excluded) over the
+    # the whole step: the per-step kernels' algorithmic bytes (rebuilds excluded) over the
     # measured time per step
     every_step_v1 = args.precision != "mixed"
     step_bytes = (algorithmic_bytes("density", kmean, kin, kskin, args.precision)
@@ -321,7 +343,6 @@ def run_gpu(args):
             variants["fp64"] = {"value": n_cr * k64 / (a0.elapsed_time(a1) * 1e-3), "steps": k64, "skin_A": 0.3,
                                 "ms_per_step": a0.elapsed_time(a1) / k64,
                                 # the bound of this form: the CUDA cores' FP64 FMA rate, measured here
-                                # (the FP64 pipe share of its kernels is in profiles/fp64_kernels_1M.md)
                                 "fp64_fma_peak_tflops": md.md_probe_fp64_fma() * 1e-12}
             s64.close()
         if args.workload != "batched":
@@ -364,8 +385,10 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                      "algorithmic_bytes_per_atom": algorithmic_bytes(dom, kmean, kin, kskin, args.precision),
+                     "moved_bytes_per_atom": (moved_bytes(dom, kin, kskin) if args.precision == "mixed"
+                                              else algorithmic_bytes(dom, kmean, kin, kskin, args.precision)),
                      "mean_list_length": kmean, "mean_pairs_within_rc": kin, "mean_inner_length": kskin,
-                     "launch_ms": phases[dom]},
+                     "launch_ms": phases[dom], "launches_timed": prof["steps"]},
         "phases_ms_per_step": phases,
         "clocks": clk.summary(),
         "e2e": e2e,
@@ -373,6 +396,7 @@ def run_gpu(args):
         # per list build 14 kernels, and in mixed precision k_verlet1; one k_reduce
         "gpu_launches": int(4 * args.steps + (15 if args.precision == "mixed" else 14) * rebuilds + 1),
         "value_incl_c": (n_cr + n_c) * ws * args.steps / (t_max * 1e-3),
+        "value_amortised": value_amortised,
         "step_roofline": step_roofline,
         "variants": variants,
     }
@@ -394,25 +418,34 @@ PAPER_TABLE2_S_PER_STEP = {10: 0.0077, 20: 0.0567, 40: 0.4110}
 
 def paper_cubes() -> dict:
     """The paper's timing workload on this GPU: cubes of n^3 unit cells with free faces
-    (2331 / 17261 / 132921 atoms), the r* = 8.262 A parameter set, mixed and FP64."""
+    (2331 / 17261 / 132921 atoms), the r* = 8.262 A parameter set, mixed and FP64, with two
+    list schemes: a thin Verlet skin (1.0 A) over Hermite tables, and the paper's own
+    (Sec. 2.6: outer list of radius 1.7 r*, skin 0.7 r*, inner list of radius r* rebuilt
+    every step; analytic forms, Sec. 2.4)."""
     import torch
     import md_inputs as mi
     from paper_1507_07068_gb300 import md
     prs = md.load_params(os.path.join(ROOT, "paper_1507_07068_gb300", "cr_c_params_rstar.json"))
-    out = {"potential": "r* = 8.262 A (cr_c_params_rstar.json)", "skin_A": 1.0}
+    rstar = prs["rc"]
+    schemes = {"": dict(skin=1.0),
+               " paper-lists": dict(skin=0.7 * rstar, inner_skin=-1.0, tabulated=0)}
+    out = {"potential": "r* = 8.262 A (cr_c_params_rstar.json)", "skin_A": 1.0,
+           "paper-lists": "outer list 1.7 r* (skin 0.7 r* = %.3f A), inner list r* every step, analytic forms"
+                          % (0.7 * rstar)}
     for n, t_paper in PAPER_TABLE2_S_PER_STEP.items():
         rep = mi.paper_cube(n)
-        for prec, k in (("mixed", 200), ("fp64", 20)):
-            sim = md.MD([rep], prs, precision=prec, skin=1.0)
-            sim.step(5)
-            torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
-            a.record(); sim.step(k); b.record(); torch.cuda.synchronize()
-            ms = a.elapsed_time(b) / k
-            out[f"{n}^3 {prec}"] = {"n_cr": rep.n_cr, "steps": k, "ms_per_step": ms,
-                                    "value": rep.n_cr / (ms * 1e-3), "paper_s_per_step": t_paper,
-                                    "speedup_vs_paper": t_paper / (ms * 1e-3)}
-            sim.close()
+        for tag, kw in schemes.items():
+            for prec, k in (("mixed", 200), ("fp64", 20)):
+                sim = md.MD([rep], prs, precision=prec, **kw)
+                sim.step(5)
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+                a.record(); sim.step(k); b.record(); torch.cuda.synchronize()
+                ms = a.elapsed_time(b) / k
+                out[f"{n}^3 {prec}{tag}"] = {"n_cr": rep.n_cr, "steps": k, "ms_per_step": ms,
+                                             "value": rep.n_cr / (ms * 1e-3), "paper_s_per_step": t_paper,
+                                             "speedup_vs_paper": t_paper / (ms * 1e-3)}
+                sim.close()
     return out
 
 
@@ -513,7 +546,9 @@ def main():
                     help="skip the variant timing the paper's Table 2 workload (r* = 8.262 A cubes)")
     ap.add_argument("--no-graph", action="store_true",
                     help="direct launches instead of graph replay (for launch-list profiling)")
-    ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--profile-steps", type=int, default=50)
+    ap.add_argument("--rate-steps", type=int, default=400,
+                    help="untimed steps over which the list-rebuild rate is counted")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--fp64-steps", type=int, default=40)
     ap.add_argument("--batched-steps", type=int, default=200)

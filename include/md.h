@@ -240,7 +240,9 @@ int md_get_virial(md_t *h, int32_t replica, double *out6n);
  * displacement test for the new indenter path.  Errors: MD_ERR_ARG, MD_ERR_CUDA. */
 int md_set_indenter_velocity(md_t *h, int32_t replica, double v_ind);
 
-/* Test hook.  which = 0: Cr-Cr list, which = 1: Cr-C list, as built at the last rebuild.
+/* Test hook (no counterpart in the paper: it exposes the Verlet lists of Sec. 2.6 so that
+ * they can be compared set for set with an independent build).  which = 0: Cr-Cr list,
+ * which = 1: Cr-C list, as built at the last rebuild.
  * cell_xyz (3*n_cr, may be NULL): cell coordinates of each atom in the Cr cell grid;
  * cnt (n_cr): list lengths (capped at the capacity); nbr (n_cr*kmax, may be NULL): entries
  * in caller ids (film ids for which = 0, indenter ids for which = 1), row i holding atom
@@ -248,9 +250,10 @@ int md_set_indenter_velocity(md_t *h, int32_t replica, double v_ind);
 int md_get_neighbors(md_t *h, int32_t replica, int32_t which, int32_t *cell_xyz, int32_t *cnt,
                      int32_t *nbr, int32_t kmax);
 
-/* Counts of one handle: out[0] = replicas, out[1] = film atoms, out[2] = indenter atoms,
- * out[3] = atom slots (incl. tile padding), out[4] = cells, out[5] = kmax, out[6] = kcmax,
- * out[7] = largest Cr-Cr list length seen at the last rebuild, out[8] = largest Cr-C. */
+/* Utility (no counterpart in the paper): sizes of one handle.  out[0] = replicas,
+ * out[1] = film atoms, out[2] = indenter atoms, out[3] = atom slots (incl. tile padding),
+ * out[4] = cells, out[5] = kmax, out[6] = kcmax, out[7] = largest Cr-Cr list length seen at
+ * the last rebuild, out[8] = largest Cr-C. */
 int md_get_info(md_t *h, int64_t *out9);
 
 /* The last error message of the handle (never NULL; "" when none).  h may be NULL, then
@@ -283,7 +286,9 @@ int md_version(void);
  * scratch address (cudaGetSymbolAddress, checked) and loads the three kernels, then
  * caches the address for that device; if the CUDA runtime has not yet been used on that
  * device, this also creates its context.  Make this first call -- n_cr = 0 does only the
- * set-up -- before any stream capture begins.
+ * set-up -- before any stream capture begins.  The cached address belongs to the context
+ * the set-up ran in: after cudaDeviceReset on that device (which destroys the context and
+ * the array with it) this function must not be called again in the same process.
  *
  * Concurrency: every call on a device uses the same scratch.  Calls whose kernels overlap
  * in time (two streams, or two host threads) race on it and return wrong results; order

@@ -453,10 +453,6 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
             R.w[k] = R.L[k] / n;
             R.iw[k] = 1.0 / R.w[k];
             R.iL[k] = 1.0 / R.L[k];
-            R.w32[k] = (float)R.w[k];
-            R.wc[k] = (double)R.w32[k];
-            R.dL32[k] = (float)(R.L[k] - n * R.wc[k]);
-            R.pad32[k] = (float)(1e-4 + (n + 1) * fabs(R.w[k] - R.wc[k]));
             R.lo32[k] = (float)R.lo[k];
             R.L32[k] = (float)R.L[k];
             R.iL32[k] = (float)(1.0 / R.L[k]);
@@ -516,6 +512,31 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     a.mixed = opt->precision == MD_MIXED;
     a.rebuild_every = opt->rebuild_every;
     a.skin = opt->skin; a.cut = cut; a.cutc = cutc; a.cut2 = cut * cut; a.cutc2 = cutc * cutc;
+    {
+        // unit of the fixed-point cell-relative positions: the largest power of two
+        // u = 2^-k A with (2 w_max + 2 skin + 4 A) / u < 2^30, so that every displacement
+        // within a 27-cell stencil, and any drift before a rebuild, fits in 32 bits with a
+        // margin of two (k = 26, u = 1.5e-8 A, for 5.6 A cells)
+        double wmax = 0.0;
+        for (const RepDev &R : h->rep)
+            for (int k = 0; k < 3; ++k) wmax = std::max(wmax, R.w[k]);
+        int qk = (int)floor(log2(1073741824.0 / (2.0 * wmax + 2.0 * opt->skin + 4.0)));
+        qk = std::min(std::max(qk, 8), 30);
+        const double qu = ldexp(1.0, -qk);
+        a.qu = (float)qu;
+        a.qinv = ldexp(1.0, qk);
+        // cells of width wc = Wq u (w rounded to the unit), centres lo + (c + 1/2) wc; a pair
+        // through a periodic face adds DLq = (L - nc wc) / u rounded (an error below u/2)
+        for (RepDev &R : h->rep)
+            for (int k = 0; k < 3; ++k) {
+                R.Wq[k] = (int32_t)llround(R.w[k] / qu);
+                R.wc[k] = R.Wq[k] * qu;
+                R.w32[k] = (float)R.wc[k];
+                R.DLq[k] = (int32_t)llround((R.L[k] - R.nc[k] * R.wc[k]) / qu);
+                R.dL32[k] = (float)(R.DLq[k] * qu);
+                R.pad32[k] = (float)(1e-4 + (R.nc[k] + 1) * fabs(R.w[k] - R.wc[k]));
+            }
+    }
     {
         // inner list: entries within rc + d (FP32 test); rebuilt once an atom has moved
         // (FP32 estimate, error < 1e-6 A) more than (d - 1e-4) / 2 since its last build, so

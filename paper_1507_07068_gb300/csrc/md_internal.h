@@ -6,8 +6,9 @@
 //     per-CTA partials); slots past a replica's last atom are padding (never binned,
 //     never listed, never integrated);
 //   - per-atom SoA arrays: x[3][S], v[3][S], F[3][S], x_build[3][S] (FP64),
-//     pos4[S] (float4: position relative to the atom's cell centre in FP32, and the
-//     atom's cell coordinates packed in .w), fm (F'(rho), M'(P) per atom: double2 in FP64
+//     pos4[S] (int4: position relative to the atom's cell centre in 32-bit fixed point of
+//     unit 2^-k A, and the atom's cell coordinates packed in .w; a pair's displacement is
+//     an exact integer sum, rounded once when converted to FP32), fm (F'(rho), M'(P) per atom: double2 in FP64
 //     mode, float2 in mixed mode), cellc[S] (packed cell coordinates), orig[S] (caller id),
 //     fixed[S] (uint8);
 //   - Verlet lists in SoA form nbr[k * S + i] (slot of the k-th neighbour of slot i), so a
@@ -53,7 +54,13 @@ struct alignas(32) Cf64 {
 struct PotF32 {
     float rmin_s_f, inv_hf, rmin_s_m, inv_hm, lf0, beta, f_rc, df_rc, rc;
     float inv_re, d, b0, b1, b2, b3;
-    float c0, c1, c2, c3;   // (k + 2) b_k / r_e: dPhi/dr = t (c0 + c1 t + c2 t^2 + c3 t^3)
+    // Eq. A4 in FP32, about t = tc instead of the double root (t = r/r_e - d, s = t - tc):
+    // Phi = t^2 (b0 + b1 s + b2 s^2 + b3 s^3), dPhi/dr = t (c0 + c1 s + c2 s^2 + c3 s^3).
+    // About the double root the cubic's terms cancel ~60-fold at the first neighbour shell;
+    // about tc (near the first two shells) they do not.  s = r inv_re - (d + tc), with the
+    // FP32 rounding of 1/r_e and d + tc carried in inv_re_lo, dc_lo.
+    float c0, c1, c2, c3;
+    float tc, dc, dc_lo;
     float D_o, half_ax, inv_yeq, m_rc, dm_rc, rc_m;
     float F_o, n, inv_rho_e, alpha, inv_P_e, rc2;
     int32_t tabulated, nf, nm;
@@ -61,7 +68,7 @@ struct PotF32 {
     const float4 *tfp;   // f and Phi coefficients interleaved: [2k] = f, [2k + 1] = Phi
     // direct FP32 forms of the pair loops: f = f_e (r_e^2 / r^2)^ipow when beta = 2 ipow
     // (ipow = 0: exp2/log2 form); r / r_e - d with the FP32 rounding of 1/r_e and d carried
-    float f_e, re2, inv_re_lo, d_lo;
+    float f_e, re2, inv_re_lo;
     int32_t ipow;
 };
 
@@ -93,13 +100,15 @@ struct RepDev {
     double lo[3], hi[3], L[3], w[3];  // Cr cell grid; L = hi - lo; w = L / nc (binning)
     double iw[3], iL[3];              // 1 / w, 1 / L (fast path of the exact quotient floors)
     int32_t per[3], nc[3];
-    // FP32 cell-relative positions are taken about the centres lo + (c + 1/2) w32 (w32 =
-    // w rounded to FP32), so two cells' centres differ by an exact multiple of w32, plus
-    // dL32 = L - nc w32 when the pair crosses a periodic boundary
+    // Fixed-point cell-relative positions (unit u = 2^-k A, DevArgs::qu) are taken about the
+    // centres lo + (c + 1/2) wc, wc = Wq u (w rounded to the unit), so two cells' centres
+    // differ by an exact multiple Wq of the unit, plus DLq = (L - nc wc) / u (rounded) when
+    // a pair crosses a periodic boundary.  w32, dL32: the same in FP32 (prefilters only).
+    int32_t Wq[3], DLq[3];
     float w32[3], dL32[3];
-    double wc[3];                     // (double) w32
-    // in the w32 frame a cell's box is off by at most c |w - w32| (c < nc): the margin that
-    // k_nbr adds to the half-width of a stencil cell's box
+    double wc[3];                     // Wq u
+    // in the wc frame a cell's box is off by at most c |w - wc| (c < nc): the margin that
+    // k_nbr adds to the half-width of a stencil cell's box (with 1e-4 A for FP32 rounding)
     float pad32[3];
     int32_t cell_off, n_cells;
     int32_t slot_off, n_atoms, n_slots;  // first slot (TILE aligned), real atoms, slots incl. padding
@@ -115,7 +124,7 @@ struct RepDev {
     // dynamics
     double v_ind, dt, mass, acc_per_f;   // acc_per_f = MD_ACC / mass
     double hk;                           // dt acc_per_f / 2, the half-kick factor
-    int32_t cen_off[3];                  // per-axis cell centres lo + (c + 1/2) w32 in DevArgs::cen
+    int32_t cen_off[3];                  // per-axis cell centres lo + (c + 1/2) wc in DevArgs::cen
     double z_surface0, zc_min0;
 };
 
@@ -169,6 +178,8 @@ struct DevArgs {
     int32_t mixed;
     int32_t rebuild_every;
     double skin, cut2, cutc2, cut, cutc;
+    float qu;                    // unit of the fixed-point positions, 2^-k A
+    double qinv;                 // 2^k
     const RepDev *rep;
     RepState *rs;
     RepEnergy *en;
@@ -181,15 +192,15 @@ struct DevArgs {
     // positions the pair kernels use (outside a step both indices name the state).  FP64
     // mode keeps one buffer (both pointers equal).
     double *xs[2];               // [3][S] each
-    float4 *p4[2];
+    int4 *p4[2];
     double *v, *F, *xb;          // [3][S]: velocity and force at the state's time, x at the build
     double *vh;                  // [3][S]: v(t + dt/2) of the current step
     double2 *fm64;
     float2 *fm32;
     int32_t *inner, *icnt;       // mixed precision: the inner list, entries of the Verlet list
                                  // within rc + MD_INNER_SKIN when it was last rebuilt
-    float4 *pin;                 // mixed: pos4 of each atom when the inner list was rebuilt
-    float4 *pb;                  // mixed: pos4 of each atom when the Verlet list was rebuilt
+    int4 *pin;                   // mixed: pos4 of each atom when the inner list was rebuilt
+    int4 *pb;                    // mixed: pos4 of each atom when the Verlet list was rebuilt
     float rin2, ithr2;           // (rc + MD_INNER_SKIN)^2; max |p - p_in|^2 before a rebuild
     int32_t *cellc, *orig;
     uint8_t *fixed;

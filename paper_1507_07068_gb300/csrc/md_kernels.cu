@@ -102,15 +102,10 @@ void fill_table(int n, double r0, double r1, Fn g, std::vector<Cf64> &out)
 
 }  // namespace
 
-int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs32, char *err, size_t errlen)
+// The analytic forms of md_params in FP64 (Eqs. A2-A5, shifted-force constants, Eq. A4 in
+// its Taylor form about the double root): the fields that md_build_pot and md_pot_forms share.
+static void fill_forms(const md_params *p, PotDev *P, HostPot &H)
 {
-    memset(P, 0, sizeof(*P));
-    if (!(p->r_e > 0 && p->f_e > 0 && p->rho_e > 0 && p->P_e > 0 && p->y_eq > 0 && p->rc > 0 &&
-          p->rc_morse > 0 && p->r_min > 0 && p->r_min < p->rc && p->r_min < p->rc_morse && p->h > 0)) {
-        snprintf(err, errlen, "md_params: r_e, f_e, rho_e, P_e, y_eq, rc, rc_morse, h must be > 0 and r_min < both cut-offs");
-        return MD_ERR_ARG;
-    }
-    HostPot H;
     H.p = *p;
     // Taylor coefficients of the cubic of Eq. A4 about x = d
     const long double a0 = p->a[0], a1 = p->a[1], a2 = p->a[2], a3 = p->a[3], d = p->d;
@@ -131,7 +126,20 @@ int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs
     P->D_o = p->D_o; P->half_ax = 0.5 * p->alpha_x; P->inv_yeq = 1.0 / p->y_eq;
     P->rc = p->rc; P->rc_m = p->rc_morse; P->rc2 = p->rc * p->rc; P->rcm2 = p->rc_morse * p->rc_morse;
     P->f_rc = (double)H.f_rc; P->df_rc = (double)H.df_rc; P->m_rc = (double)H.m_rc; P->dm_rc = (double)H.dm_rc;
-    P->shifted = p->shifted; P->tabulated = p->tabulated;
+    P->shifted = p->shifted;
+}
+
+int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs32, char *err, size_t errlen)
+{
+    memset(P, 0, sizeof(*P));
+    if (!(p->r_e > 0 && p->f_e > 0 && p->rho_e > 0 && p->P_e > 0 && p->y_eq > 0 && p->rc > 0 &&
+          p->rc_morse > 0 && p->r_min > 0 && p->r_min < p->rc && p->r_min < p->rc_morse && p->h > 0)) {
+        snprintf(err, errlen, "md_params: r_e, f_e, rho_e, P_e, y_eq, rc, rc_morse, h must be > 0 and r_min < both cut-offs");
+        return MD_ERR_ARG;
+    }
+    HostPot H;
+    fill_forms(p, P, H);
+    P->tabulated = p->tabulated;
     P->r_min = p->r_min;
     int nf = (int)ceil((p->rc - p->r_min) / p->h - 1e-9);
     int nm = (int)ceil((p->rc_morse - p->r_min) / p->h - 1e-9);
@@ -179,9 +187,31 @@ int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs
     q.inv_hm = (float)P->inv_hm; q.rmin_s_m = (float)(P->r_min * P->inv_hm);
     q.lf0 = (float)P->lf0; q.beta = (float)P->beta; q.f_rc = (float)P->f_rc; q.df_rc = (float)P->df_rc;
     q.rc = (float)P->rc; q.inv_re = (float)(1.0 / P->r_e); q.d = (float)P->d;
-    q.b0 = (float)P->b[0]; q.b1 = (float)P->b[1]; q.b2 = (float)P->b[2]; q.b3 = (float)P->b[3];
-    q.c0 = (float)(2.0 * P->b[0] / P->r_e); q.c1 = (float)(3.0 * P->b[1] / P->r_e);
-    q.c2 = (float)(4.0 * P->b[2] / P->r_e); q.c3 = (float)(5.0 * P->b[3] / P->r_e);
+    {
+        // Eq. A4 about t = tc: tc is t at r = 0.95 r_e (between BCC's first two neighbour
+        // shells for the forms here) rounded to a multiple of 1/64, exact in FP32.  The cubics
+        // B(t) = sum e_k t^k (Phi = t^2 B) and C(t) = sum (k + 2) e_k t^k / r_e (dPhi/dr = t C)
+        // are re-expanded in s = t - tc in extended precision and rounded once.
+        const long double tc = rintl(64.0L * (0.95L - (long double)p->d)) / 64.0L;
+        const long double re = p->r_e;
+        long double B[4], Cc[4];
+        for (int k = 0; k < 4; ++k) { B[k] = H.e[k]; Cc[k] = (k + 2) * H.e[k] / re; }
+        auto shift = [&](const long double (&c)[4], float (&o)[4]) {
+            o[0] = (float)(((c[3] * tc + c[2]) * tc + c[1]) * tc + c[0]);
+            o[1] = (float)((3.0L * c[3] * tc + 2.0L * c[2]) * tc + c[1]);
+            o[2] = (float)(3.0L * c[3] * tc + c[2]);
+            o[3] = (float)c[3];
+        };
+        float bb[4], cc[4];
+        shift(B, bb);
+        shift(Cc, cc);
+        q.b0 = bb[0]; q.b1 = bb[1]; q.b2 = bb[2]; q.b3 = bb[3];
+        q.c0 = cc[0]; q.c1 = cc[1]; q.c2 = cc[2]; q.c3 = cc[3];
+        q.tc = (float)tc;
+        const long double dc = (long double)p->d + tc;
+        q.dc = (float)dc;
+        q.dc_lo = (float)(dc - (long double)q.dc);
+    }
     q.D_o = (float)P->D_o; q.half_ax = (float)P->half_ax; q.inv_yeq = (float)P->inv_yeq;
     q.m_rc = (float)P->m_rc; q.dm_rc = (float)P->dm_rc; q.rc_m = (float)P->rc_m;
     q.F_o = (float)P->F_o; q.n = (float)P->n; q.inv_rho_e = (float)(1.0 / P->rho_e); q.alpha = (float)P->alpha;
@@ -190,8 +220,7 @@ int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs
     q.tfp = *d_tabs32 + 2 * nf + nm;
     q.f_e = (float)p->f_e;
     q.re2 = (float)(p->r_e * p->r_e);
-    q.inv_re_lo = (float)(1.0 / p->r_e - (double)q.inv_re);
-    q.d_lo = (float)(p->d - (double)q.d);
+    q.inv_re_lo = (float)(1.0L / (long double)p->r_e - (long double)q.inv_re);
     const double half_beta = 0.5 * p->beta;
     q.ipow = (half_beta == floor(half_beta) && half_beta >= 1.0 && half_beta <= 8.0) ? (int)half_beta : 0;
     return MD_OK;
@@ -208,6 +237,9 @@ __device__ __forceinline__ int pack_cell(int c0, int c1, int c2)
 __device__ __forceinline__ int cell_x(int p) { return p & ((1 << MD_CELL_BITS) - 1); }
 __device__ __forceinline__ int cell_y(int p) { return (p >> MD_CELL_BITS) & ((1 << MD_CELL_BITS) - 1); }
 __device__ __forceinline__ int cell_z(int p) { return (p >> (2 * MD_CELL_BITS)) & ((1 << MD_CELL_BITS) - 1); }
+
+// a fixed-point length (units of qu = 2^-k A) in A, FP32: one rounding (the scaling is exact)
+__device__ __forceinline__ float qf(int q, float qu) { return __int2float_rn(q) * qu; }
 
 // ---- exact FP64 geometry of the list build and the skin test: every operation is a
 // separately rounded IEEE operation (no FMA contraction), so cell keys and neighbour
@@ -352,8 +384,9 @@ __device__ __forceinline__ T warp_sum(T v)
 }
 
 // CTA sum of up to 4 per-thread values; thread 0 writes part[t * stride + blk] (FP64).
-// Values are summed within a warp in their own type (FP32 in mixed mode: a warp holds
-// at most 32 per-atom energies), then across warps in FP64.
+// Values are summed within a warp in their own type, then across warps in FP64 (every
+// energy and load sum passes FP64 values: the mixed-precision kernels widen each atom's
+// FP32 energy before any sum over atoms).
 template <int NV, class T>
 __device__ __forceinline__ void cta_partials(T (&v)[NV], double *part, int stride, int blk)
 {
@@ -486,9 +519,9 @@ __global__ void k_bin(DevArgs a)
     const int b = buf_cur(a);
     double *x = a.xs[b];
     if (*(volatile int32_t *)&a.st->pos4_ok) {
-        const float4 p = a.p4[b][s];
-        const int pc = __float_as_int(p.w);
-        const float pr[3] = {p.x, p.y, p.z};
+        const int4 p = a.p4[b][s];
+        const int pc = p.w;
+        const float pr[3] = {qf(p.x, a.qu), qf(p.y, a.qu), qf(p.z, a.qu)};
         const int cc[3] = {cell_x(pc), cell_y(pc), cell_z(pc)};
         int wrap[3];
         bool ok = true;
@@ -647,16 +680,19 @@ __global__ void k_gather(DevArgs a)
     a.cellc[s] = pack_cell(c0, c1, c2);
 }
 
-// FP32 position of slot s about its cell centre lo + (c + 1/2) w32 (see RepDev)
-__device__ __forceinline__ float4 rel_pos3(const DevArgs &a, const RepDev &R, int pc, double x0, double x1, double x2)
+// Fixed-point position of slot s about its cell centre lo + (c + 1/2) wc (see RepDev):
+// round((x - centre) / u), u = 2^-k A.  x - centre is exact to ~1e-14 A in FP64 and the
+// scaling by 2^k is exact, so the only rounding is to the unit (<= u/2).
+__device__ __forceinline__ int4 rel_pos3(const DevArgs &a, const RepDev &R, int pc, double x0, double x1, double x2)
 {
     const double c0 = __ldg(&a.cen[R.cen_off[0] + cell_x(pc)]);
     const double c1 = __ldg(&a.cen[R.cen_off[1] + cell_y(pc)]);
     const double c2 = __ldg(&a.cen[R.cen_off[2] + cell_z(pc)]);
-    return make_float4((float)(x0 - c0), (float)(x1 - c1), (float)(x2 - c2), __int_as_float(pc));
+    return make_int4(__double2int_rn((x0 - c0) * a.qinv), __double2int_rn((x1 - c1) * a.qinv),
+                     __double2int_rn((x2 - c2) * a.qinv), pc);
 }
 
-__device__ __forceinline__ float4 rel_pos(const DevArgs &a, const RepDev &R, const double *x, int s)
+__device__ __forceinline__ int4 rel_pos(const DevArgs &a, const RepDev &R, const double *x, int s)
 {
     size_t S = a.S;
     return rel_pos3(a, R, a.cellc[s], x[s], x[S + s], x[2 * S + s]);
@@ -684,17 +720,17 @@ __global__ void k_copyback(DevArgs a)
     }
     a.orig[s] = a.sorig[s];
     a.fixed[s] = a.sfixed[s];
-    const float4 p = rel_pos(a, R, x, s);
+    const int4 p = rel_pos(a, R, x, s);
     a.p4[b][s] = p;   // also used by the FP32 prefilter of k_nbr
     if (a.mixed) a.pb[s] = p;
     if (s == 0) a.st->pos4_ok = 1;
 }
 
 // full Cr-Cr Verlet list: every slot j != i in the 27-cell stencil with |x_j - x_i|^2 <
-// (rc + skin)^2 decided in FP64.  A candidate whose FP32 cell-relative distance is farther
-// than 1e-5 (relative) from the cut-off is decided by the FP32 value (its error is below
-// 2e-6 relative for atoms inside their cells); the rest take the exact FP64 test, so the
-// set equals the all-FP64 set bit for bit.
+// (rc + skin)^2 decided in FP64.  A candidate whose FP32 distance (the exact fixed-point
+// difference rounded once: error below 1e-6 relative with the unit rounding of both
+// positions) is farther than 1e-5 (relative) from the cut-off is decided by that value;
+// the rest take the exact FP64 test, so the set equals the all-FP64 set bit for bit.
 //
 // A lost atom (MDE_LOST from k_bin: outside a non-periodic domain or not finite) ends the
 // step with MD_ERR_LOST_ATOM; the lists are then left empty rather than built around
@@ -712,49 +748,49 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
     size_t S = a.S;
     const int bc = buf_cur(a);
     const double *x = a.xs[bc];
-    const float4 *pos4 = a.p4[bc];
-    const float4 pi = pos4[s];
-    int pc = __float_as_int(pi.w);
+    const int4 *pos4 = a.p4[bc];
+    const int4 pi = pos4[s];
+    int pc = pi.w;
     int c0 = cell_x(pc), c1 = cell_y(pc), c2 = cell_z(pc);
     const float cut2 = (float)a.cut2;
     const float lo2 = cut2 * (1.0f - 1e-5f), hi2 = cut2 * (1.0f + 1e-5f);
-    const float wx = R.w32[0], wy = R.w32[1], wz = R.w32[2];
-    const float hx = fmaf(0.5f, wx, R.pad32[0]), hy = fmaf(0.5f, wy, R.pad32[1]), hz = fmaf(0.5f, wz, R.pad32[2]);
+    const float qu = a.qu;
+    const float hx = fmaf(0.5f, R.w32[0], R.pad32[0]), hy = fmaf(0.5f, R.w32[1], R.pad32[1]),
+                hz = fmaf(0.5f, R.w32[2], R.pad32[2]);
     int m = 0;
     for (int dz = -1; dz <= 1; ++dz) {
         int q2 = c2 + dz;
         if (q2 < 0 || q2 >= R.nc[2]) { if (!R.per[2]) continue; q2 = (q2 + R.nc[2]) % R.nc[2]; }
-        const float oz = fmaf((float)(c2 + dz != q2) * dz, R.dL32[2], dz * wz);
-        const float gz = fmaxf(fabsf(oz - pi.z) - hz, 0.0f);
+        // centre offset of the stencil cell in units: d Wq, plus d DLq through a periodic face
+        const int tz = dz * R.Wq[2] + (c2 + dz != q2 ? dz * R.DLq[2] : 0) - pi.z;
+        const float gz = fmaxf(fabsf(qf(tz, qu)) - hz, 0.0f);
         for (int dy = -1; dy <= 1; ++dy) {
             int q1 = c1 + dy;
             if (q1 < 0 || q1 >= R.nc[1]) { if (!R.per[1]) continue; q1 = (q1 + R.nc[1]) % R.nc[1]; }
-            const float oy = fmaf((float)(c1 + dy != q1) * dy, R.dL32[1], dy * wy);
-            const float gy = fmaxf(fabsf(oy - pi.y) - hy, 0.0f);
+            const int ty = dy * R.Wq[1] + (c1 + dy != q1 ? dy * R.DLq[1] : 0) - pi.y;
+            const float gy = fmaxf(fabsf(qf(ty, qu)) - hy, 0.0f);
             const float gyz = fmaf(gy, gy, gz * gz);
             for (int dx = -1; dx <= 1; ++dx) {
                 int q0 = c0 + dx;
                 if (q0 < 0 || q0 >= R.nc[0]) { if (!R.per[0]) continue; q0 = (q0 + R.nc[0]) % R.nc[0]; }
-                // centre offset of the stencil cell: d w32, plus d dL32 through a periodic face
-                const float ox = fmaf((float)(c0 + dx != q0) * dx, R.dL32[0], dx * wx);
-                const float gx = fmaxf(fabsf(ox - pi.x) - hx, 0.0f);
+                const int tx = dx * R.Wq[0] + (c0 + dx != q0 ? dx * R.DLq[0] : 0) - pi.x;
+                const float gx = fmaxf(fabsf(qf(tx, qu)) - hx, 0.0f);
                 if (fmaf(gx, gx, gyz) > hi2) continue;
                 int key = R.cell_off + (q2 * R.nc[1] + q1) * R.nc[0] + q0;
                 int b = a.cell_start[key], e = b + a.cell_count[key];
                 const unsigned dir = (dx < 0 ? 1u : 0u) | (dx > 0 ? 2u : 0u) | (dy < 0 ? 4u : 0u) | (dy > 0 ? 8u : 0u) |
                                      (dz < 0 ? 16u : 0u) | (dz > 0 ? 32u : 0u);
-                const float tx = ox - pi.x, ty = oy - pi.y, tz = oz - pi.z;
                 for (int t0 = b; t0 < e; t0 += 4) {
                   // four candidate positions are loaded before any test or list store
-                  float4 pjv[4];
+                  int4 pjv[4];
 #pragma unroll
                   for (int u = 0; u < 4; ++u) pjv[u] = __ldg(&pos4[min(t0 + u, e - 1)]);
 #pragma unroll
                   for (int u = 0; u < 4; ++u) {
                     const int t = t0 + u;
                     const bool valid = t < e && t != s;
-                    const float4 pj = pjv[u];
-                    const float fx = pj.x + tx, fy = pj.y + ty, fz = pj.z + tz;
+                    const int4 pj = pjv[u];
+                    const float fx = qf(pj.x + tx, qu), fy = qf(pj.y + ty, qu), fz = qf(pj.z + tz, qu);
                     const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
                     bool in = r2f < lo2;
                     if (valid && !in && !(r2f > hi2)) {
@@ -809,9 +845,9 @@ __global__ void __launch_bounds__(128) k_nbrc(DevArgs a)
     // cell-relative position with an error below 1e-4 A for coordinates below ~1e3 A;
     // the 0.01 A margin keeps every atom the exact test of k_nbrc_near could accept.
     // A non-finite position is queued (and then skipped: k_bin reports it).
-    const float4 p = a.p4[buf_cur(a)][s];
-    const int pc = __float_as_int(p.w);
-    const float pr[3] = {p.x, p.y, p.z};
+    const int4 p = a.p4[buf_cur(a)][s];
+    const int pc = p.w;
+    const float pr[3] = {qf(p.x, a.qu), qf(p.y, a.qu), qf(p.z, a.qu)};
     const int cc[3] = {cell_x(pc), cell_y(pc), cell_z(pc)};
     const float zi32 = (float)a.rs[r].z_cur;
     const float lim = (float)a.cutc + 0.01f;
@@ -927,7 +963,7 @@ __global__ void k_build_done(DevArgs a)
 // Fixed atoms keep x and v (they are copied).  pc: the atom's cell at the last list build.
 __device__ __forceinline__ void drift_atom(const DevArgs &a, const RepDev &R, int s, int pc, float thr,
                                            double x0, double x1, double x2, double v0, double v1, double v2,
-                                           double F0, double F1, double F2, double *xd, float4 *pd,
+                                           double F0, double F1, double F2, double *xd, int4 *pd,
                                            unsigned long long &d2bits, unsigned &ibits)
 {
     const size_t S = a.S;
@@ -940,18 +976,18 @@ __device__ __forceinline__ void drift_atom(const DevArgs &a, const RepDev &R, in
     xd[s] = x0; xd[S + s] = x1; xd[2 * S + s] = x2;
     bool exact = true;
     if (a.mixed) {
-        const float4 p = rel_pos3(a, R, pc, x0, x1, x2);
+        const int4 p = rel_pos3(a, R, pc, x0, x1, x2);
         pd[s] = p;
         // same cell frame as the build's copy pb: a displacement clearly below thr cannot
         // change the rebuild test and its exact FP64 value is not needed
-        const float4 b = a.pb[s];
-        const float bx = p.x - b.x, by = p.y - b.y, bz = p.z - b.z;
+        const int4 b = a.pb[s];
+        const float bx = qf(p.x - b.x, a.qu), by = qf(p.y - b.y, a.qu), bz = qf(p.z - b.z, a.qu);
         const float d2f = fmaf(bx, bx, fmaf(by, by, bz * bz));
         exact = !(thr > 0.0f && d2f < thr * thr);
         // displacement since the inner list was rebuilt (same cell frame: a rebuild of the
         // Verlet list in between invalidates the inner list anyway)
-        const float4 q = a.pin[s];
-        const float ex = p.x - q.x, ey = p.y - q.y, ez = p.z - q.z;
+        const int4 q = a.pin[s];
+        const float ex = qf(p.x - q.x, a.qu), ey = qf(p.y - q.y, a.qu), ez = qf(p.z - q.z, a.qu);
         float dm2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
         if (!(dm2 <= 1e30f)) dm2 = 1e30f;   // not finite: force the rebuild
         ibits = __float_as_uint(dm2);       // dm2 >= 0: bit order = value order
@@ -1072,14 +1108,14 @@ __global__ void __launch_bounds__(256) k_state_scan(DevArgs a, int r, int slot_o
         } else {
             x0 = x[s]; x1 = x[S + s]; x2 = x[2 * S + s];
         }
-        const float4 p = rel_pos3(a, R, a.cellc[s], x0, x1, x2);
+        const int4 p = rel_pos3(a, R, a.cellc[s], x0, x1, x2);
         a.p4[b][s] = p;
         double d2 = norm2_exact(__dsub_rn(x0, a.xb[s]), __dsub_rn(x1, a.xb[S + s]), __dsub_rn(x2, a.xb[2 * S + s]));
         if (d2 != d2) d2 = 1e300;   // NaN position: force a rebuild, which reports it
         d2bits = (unsigned long long)__double_as_longlong(d2);
         if (a.mixed) {
-            const float4 q = a.pin[s];
-            const float ex = p.x - q.x, ey = p.y - q.y, ez = p.z - q.z;
+            const int4 q = a.pin[s];
+            const float ex = qf(p.x - q.x, a.qu), ey = qf(p.y - q.y, a.qu), ez = qf(p.z - q.z, a.qu);
             float dm2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
             if (!(dm2 <= 1e30f)) dm2 = 1e30f;
             ibits = __float_as_uint(dm2);
@@ -1106,24 +1142,28 @@ __global__ void k_state_need(DevArgs a)
 
 // ============================================================================ Task 4, mixed precision
 //
-// Geometry of a pair from FP32 cell-relative positions: x_j - x_i = (p_j - p_i) + offset,
-// the offset being the centre-to-centre vector of the two cells, read from a 64-entry
-// table indexed by the direction bits of the list entry (exact multiples of w32); a pair
-// that crosses a periodic face (atom i in an edge cell, direction bit towards that face)
-// adds -+dL32 on that axis.
+// Geometry of a pair from fixed-point cell-relative positions: x_j - x_i = (p_j - p_i) +
+// offset, in units u, the offset being the centre-to-centre vector of the two cells, read
+// from a 64-entry table indexed by the direction bits of the list entry (multiples of Wq);
+// a pair that crosses a periodic face (atom i in an edge cell, direction bit towards that
+// face) adds -+DLq on that axis.  The integer sum is exact; converted to FP32 (and scaled
+// by u, a power of two) it is the displacement rounded once.  Positions in FP32 about the
+// cell centres would carry three roundings (both positions and the sum), three times the
+// error, and the FP32 pair forces would then miss 1e-5 relative on cold or perfect
+// lattices, where the net forces are small.
 
 struct PairGeom {
     unsigned xmask;          // direction bits that cross a periodic face for this atom
-    float dL0, dL1, dL2;
+    int dL0, dL1, dL2;
 };
 
-__device__ __forceinline__ void fill_offsets(float4 *sm_off, const RepDev &R)
+__device__ __forceinline__ void fill_offsets(int4 *sm_off, const RepDev &R)
 {
     for (int c = threadIdx.x; c < 64; c += blockDim.x) {
-        float ox = (c & 1 ? -R.w32[0] : 0.f) + (c & 2 ? R.w32[0] : 0.f);
-        float oy = (c & 4 ? -R.w32[1] : 0.f) + (c & 8 ? R.w32[1] : 0.f);
-        float oz = (c & 16 ? -R.w32[2] : 0.f) + (c & 32 ? R.w32[2] : 0.f);
-        sm_off[c] = make_float4(ox, oy, oz, 0.f);
+        int ox = (c & 1 ? -R.Wq[0] : 0) + (c & 2 ? R.Wq[0] : 0);
+        int oy = (c & 4 ? -R.Wq[1] : 0) + (c & 8 ? R.Wq[1] : 0);
+        int oz = (c & 16 ? -R.Wq[2] : 0) + (c & 32 ? R.Wq[2] : 0);
+        sm_off[c] = make_int4(ox, oy, oz, 0);
     }
 }
 
@@ -1134,7 +1174,7 @@ __device__ __forceinline__ PairGeom pair_geom(const RepDev &R, int ci)
     G.xmask = (R.per[0] && c0 == 0 ? 1u : 0u) | (R.per[0] && c0 == R.nc[0] - 1 ? 2u : 0u) |
               (R.per[1] && c1 == 0 ? 4u : 0u) | (R.per[1] && c1 == R.nc[1] - 1 ? 8u : 0u) |
               (R.per[2] && c2 == 0 ? 16u : 0u) | (R.per[2] && c2 == R.nc[2] - 1 ? 32u : 0u);
-    G.dL0 = R.dL32[0]; G.dL1 = R.dL32[1]; G.dL2 = R.dL32[2];
+    G.dL0 = R.DLq[0]; G.dL1 = R.DLq[1]; G.dL2 = R.DLq[2];
     return G;
 }
 
@@ -1142,21 +1182,20 @@ __device__ __forceinline__ PairGeom pair_geom(const RepDev &R, int ci)
 // crosses a periodic face and the correction is left out (the caller decides per warp, so
 // the branch between the two forms is uniform)
 template <bool PER>
-__device__ __forceinline__ void disp(const float4 &pi, const float4 &pj, unsigned dir, const float4 *sm_off,
-                                     const PairGeom &G, float &dx, float &dy, float &dz)
+__device__ __forceinline__ void disp(const int4 &pi, const int4 &pj, unsigned dir, const int4 *sm_off,
+                                     const PairGeom &G, float qu, float &dx, float &dy, float &dz)
 {
-    const float4 o = sm_off[dir];
-    dx = (pj.x - pi.x) + o.x;
-    dy = (pj.y - pi.y) + o.y;
-    dz = (pj.z - pi.z) + o.z;
+    const int4 o = sm_off[dir];
+    int ix = pj.x - pi.x + o.x, iy = pj.y - pi.y + o.y, iz = pj.z - pi.z + o.z;
     if (PER) {
         const unsigned c = dir & G.xmask;
-        if (c) {   // through a periodic face: the period is nc w32 + dL
-            dx += (c & 1 ? -G.dL0 : 0.f) + (c & 2 ? G.dL0 : 0.f);
-            dy += (c & 4 ? -G.dL1 : 0.f) + (c & 8 ? G.dL1 : 0.f);
-            dz += (c & 16 ? -G.dL2 : 0.f) + (c & 32 ? G.dL2 : 0.f);
+        if (c) {   // through a periodic face: the period is nc Wq + DLq
+            ix += (c & 1 ? -G.dL0 : 0) + (c & 2 ? G.dL0 : 0);
+            iy += (c & 4 ? -G.dL1 : 0) + (c & 8 ? G.dL1 : 0);
+            iz += (c & 16 ? -G.dL2 : 0) + (c & 32 ? G.dL2 : 0);
         }
     }
+    dx = qf(ix, qu); dy = qf(iy, qu); dz = qf(iz, qu);
 }
 
 template <bool B> struct BoolC { static constexpr bool value = B; };
@@ -1217,8 +1256,8 @@ __device__ __forceinline__ float fa_val(const Pot32 &Q, float r2)
 }
 
 // f, f' and Phi' of a pair, and Phi itself when EN (the energies are wanted).  Phi beyond
-// its double root (t > 0) is zero with its slope; t is clamped to 0 there, where the
-// Taylor form gives exactly 0 for both.
+// its double root (t > 0) is zero with its slope; t is clamped to 0 there, where both
+// forms (t^2 times a cubic in s, t times a cubic in s) give exactly 0.
 template <int IPOW, bool EN>
 __device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, float &f, float &df, float &ph, float &dph)
 {
@@ -1226,9 +1265,10 @@ __device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, flo
     const float fr = f_direct<IPOW>(Q, r2, r);
     f = fr - Q.f_rc - (r - Q.rc) * Q.df_rc;
     df = -Q.beta * fr * rinv - Q.df_rc;
-    const float t = fminf(fmaf(r, Q.inv_re, -Q.d) + fmaf(r, Q.inv_re_lo, -Q.d_lo), 0.0f);
-    ph = EN ? t * t * fmaf(fmaf(fmaf(Q.b3, t, Q.b2), t, Q.b1), t, Q.b0) : 0.0f;
-    dph = t * fmaf(fmaf(fmaf(Q.c3, t, Q.c2), t, Q.c1), t, Q.c0);
+    const float sv = fmaf(r, Q.inv_re, -Q.dc) + fmaf(r, Q.inv_re_lo, -Q.dc_lo);   // t - tc
+    const float t = fminf(sv + Q.tc, 0.0f);
+    ph = EN ? t * t * fmaf(fmaf(fmaf(Q.b3, sv, Q.b2), sv, Q.b1), sv, Q.b0) : 0.0f;
+    dph = t * fmaf(fmaf(fmaf(Q.c3, sv, Q.c2), sv, Q.c1), sv, Q.c0);
 }
 
 // Task 4a (Eqs. A2-A3): rho_i, P_i over the pairs within rc; F'(rho_i), M'(P_i) stored,
@@ -1246,7 +1286,7 @@ __device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, flo
 template <int TPA, int IPOW, bool EN>
 __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
 {
-    __shared__ float4 sm_off[64];
+    __shared__ int4 sm_off[64];
     const int A = blockDim.x / TPA;
     const int g = threadIdx.x / TPA, lane = threadIdx.x % TPA;
     const int s = blockIdx.x * A + g;
@@ -1260,9 +1300,9 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
     const bool rebuild = !a.st->inner_ok || !(__uint_as_float(a.st->imax_bits) <= a.ithr2);
     float rho = 0.f, Ps = 0.f;
     int m = 0;   // inner-list entries of this lane
-    const float4 *pp = a.p4[buf_step(a)];   // positions x(t + dt)
-    const float4 pi = pp[s];
-    const PairGeom G = pair_geom(R, __float_as_int(pi.w));
+    const int4 *pp = a.p4[buf_step(a)];   // positions x(t + dt)
+    const int4 pi = pp[s];
+    const PairGeom G = pair_geom(R, pi.w);
     const bool per = __any_sync(0xffffffffu, real && G.xmask != 0u);
     auto work = [&](auto PERC) {
         constexpr bool PER = decltype(PERC)::value;
@@ -1276,13 +1316,13 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
                     const int k = k0 + u * TPA;
                     e[u] = k < n ? (unsigned)__ldg(&a.nbr[(size_t)k * S + s]) : (unsigned)s;
                 }
-                float4 pj[MD_UNROLL];
+                int4 pj[MD_UNROLL];
 #pragma unroll
                 for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&pp[e[u] & MD_J_MASK]);
 #pragma unroll
                 for (int u = 0; u < MD_UNROLL; ++u) {
                     float dx, dy, dz;
-                    disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
+                    disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, a.qu, dx, dy, dz);
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     if (k0 + u * TPA < n && r2 < a.rin2) {
                         // lane-interleaved rows: each lane owns rows lane, lane + TPA, ...
@@ -1315,13 +1355,13 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
                     const int k = k0 + (u + MD_UNROLL) * TPA;
                     en[u] = k < n ? ld_stream(&a.inner[(size_t)k * S + s]) : (unsigned)s;
                 }
-                float4 pj[MD_UNROLL];
+                int4 pj[MD_UNROLL];
 #pragma unroll
                 for (int u = 0; u < MD_UNROLL; ++u) pj[u] = __ldg(&pp[e[u] & MD_J_MASK]);
 #pragma unroll
                 for (int u = 0; u < MD_UNROLL; ++u) {
                     float dx, dy, dz;
-                    disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
+                    disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, a.qu, dx, dy, dz);
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     // padding entries (the atom itself) and entries now beyond rc drop out
                     const bool in = (e[u] & MD_J_MASK) != (unsigned)s && r2 < Q.rc2;
@@ -1350,7 +1390,7 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
         if (rebuild) a.st->inner_ok_next = 1;   // read by the next k_decide
         a.st->imax_fresh = rebuild;
     }
-    float acc[2] = {0.f, 0.f};
+    double acc[2] = {0.0, 0.0};   // per-atom energies, summed over atoms in FP64
     if (real && lane == 0) {
         float F, Fp, M, Mp;
         Q.embed(rho, F, Fp);
@@ -1372,7 +1412,7 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
 template <int TPA, int IPOW, bool EN>
 __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int integrate)
 {
-    __shared__ float4 sm_off[64];
+    __shared__ int4 sm_off[64];
     const int A = blockDim.x / TPA;
     const int g = threadIdx.x / TPA, lane = threadIdx.x % TPA;
     const int s = blockIdx.x * A + g;
@@ -1398,9 +1438,9 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
         prefetch_l2(a.pb + s0, A * 16u);
         prefetch_l2(a.pin + s0, A * 16u);
     }
-    const float4 *pp = a.p4[bn];
-    const float4 pi = pp[s];
-    const PairGeom G = pair_geom(R, __float_as_int(pi.w));
+    const int4 *pp = a.p4[bn];
+    const int4 pi = pp[s];
+    const PairGeom G = pair_geom(R, pi.w);
     const bool per = __any_sync(0xffffffffu, real && G.xmask != 0u);
     if (TPA == 1) {   // this warp's inner-list rows (32 atoms: 128 B per row) on their way to L2
         const int nmax = __reduce_max_sync(0xffffffffu, real ? a.icnt[s] : 0);
@@ -1431,7 +1471,7 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
                 const int k = k0 + (u + FU) * TPA;
                 en[u] = k < n ? ld_stream(&a.inner[(size_t)k * S + s]) : (unsigned)s;
             }
-            float4 pj[FU];
+            int4 pj[FU];
             float2 fmj[FU];
 #pragma unroll
             for (int u = 0; u < FU; ++u) {
@@ -1442,7 +1482,7 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
 #pragma unroll
             for (int u = 0; u < FU; ++u) {
                 float dx, dy, dz;
-                disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
+                disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, a.qu, dx, dy, dz);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 if ((e[u] & MD_J_MASK) != (unsigned)s) {   // padding is the atom itself
                     // inner-list entries beyond rc (at most rc + inner skin) drop out by a
@@ -1481,7 +1521,7 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
             em += __shfl_xor_sync(0xffffffffu, em, o);
         }
     }
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};   // per-atom energies and load, summed over atoms in FP64
     unsigned long long d2bits = 0ull;
     unsigned ibits = 0u;
     if (real && lane == 0) {
@@ -1504,15 +1544,14 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
             // k_decide that examines those positions, its inner-list test for the k_density
             // that evaluates them.  The next k_decide keeps it unless it rebuilds the lists.
             const double *x = a.xs[bn];
-            drift_atom(a, R, s, __float_as_int(pi.w), integrate == 1 ? a.rs[r].dthr2 : a.rs[r].dthr, x[s], x[S + s],
+            drift_atom(a, R, s, pi.w, integrate == 1 ? a.rs[r].dthr2 : a.rs[r].dthr, x[s], x[S + s],
                        x[2 * S + s], vx, vy, vz, Fx, Fy, Fz, a.xs[bo], a.p4[bo], d2bits, ibits);
         } else {
             vx = a.v[s]; vy = a.v[S + s]; vz = a.v[2 * S + s];
         }
         if (EN) {
-            const float ux = (float)vx, uy = (float)vy, uz = (float)vz;
             acc[0] = ep; acc[1] = em; acc[2] = -mz;
-            acc[3] = (float)(0.5 / MD_ACC) * (float)R.mass * (ux * ux + uy * uy + uz * uz);
+            acc[3] = (0.5 / MD_ACC) * R.mass * (vx * vx + vy * vy + vz * vz);   // kinetic energy, FP64
         }
     }
     if (integrate) cta_max_disp(d2bits, ibits, &a.rs[r].d2b[bo], &a.st->imax_next);
@@ -1716,7 +1755,7 @@ __device__ __forceinline__ void add_vir(T (&w)[6], T c, T dx, T dy, T dz)
 template <int TPA, int IPOW>
 __global__ void __launch_bounds__(256) k_virial_mixed(DevArgs a, PotDev P)
 {
-    __shared__ float4 sm_off[64];
+    __shared__ int4 sm_off[64];
     const int A = blockDim.x / TPA;
     const int g = threadIdx.x / TPA, lane = threadIdx.x % TPA;
     const int s = blockIdx.x * A + g;
@@ -1728,9 +1767,9 @@ __global__ void __launch_bounds__(256) k_virial_mixed(DevArgs a, PotDev P)
     const bool real = (s - R.slot_off) < R.n_atoms;
     const size_t S = a.S;
     const int b = buf_step(a);
-    const float4 *pp = a.p4[b];
-    const float4 pi = pp[s];
-    const PairGeom G = pair_geom(R, __float_as_int(pi.w));
+    const int4 *pp = a.p4[b];
+    const int4 pi = pp[s];
+    const PairGeom G = pair_geom(R, pi.w);
     const bool per = __any_sync(0xffffffffu, real && G.xmask != 0u);
     float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     auto work = [&](auto PERC) {
@@ -1743,7 +1782,7 @@ __global__ void __launch_bounds__(256) k_virial_mixed(DevArgs a, PotDev P)
             const unsigned j = e & MD_J_MASK;
             if (j == (unsigned)s) continue;   // padding
             float dx, dy, dz;
-            disp<PER>(pi, __ldg(&pp[j]), e >> MD_J_BITS, sm_off, G, dx, dy, dz);
+            disp<PER>(pi, __ldg(&pp[j]), e >> MD_J_BITS, sm_off, G, a.qu, dx, dy, dz);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             if (!(r2 < Q.rc2)) continue;
             const float2 fmj = __ldg(&a.fm32[j]);
@@ -2068,7 +2107,7 @@ cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s)
 
 // ============================================================================ md_forces_small
 
-// Analytic part of md_build_pot: the same fields, no tables.
+// The analytic fields of md_build_pot (fill_forms), without tables.
 int md_pot_forms(const md_params *p, PotDev *P, char *err, size_t errlen)
 {
     memset(P, 0, sizeof(*P));
@@ -2081,26 +2120,8 @@ int md_pot_forms(const md_params *p, PotDev *P, char *err, size_t errlen)
         return MD_ERR_ARG;
     }
     HostPot H;
-    H.p = *p;
-    const long double a0 = p->a[0], a1 = p->a[1], a2 = p->a[2], a3 = p->a[3], d = p->d;
-    H.e[0] = ((a3 * d + a2) * d + a1) * d + a0;
-    H.e[1] = (3.0L * a3 * d + 2.0L * a2) * d + a1;
-    H.e[2] = 3.0L * a3 * d + a2;
-    H.e[3] = a3;
-    if (p->shifted) {
-        H.f_rc = H.f_raw(p->rc);
-        H.df_rc = H.df_raw(p->rc);
-        H.morse_raw(p->rc_morse, H.m_rc, H.dm_rc);
-    }
-    P->f_e = p->f_e; P->r_e = p->r_e; P->beta = p->beta;
-    P->lf0 = log2(p->f_e) + p->beta * log2(p->r_e);
-    P->F_o = p->F_o; P->n = p->n; P->rho_e = p->rho_e; P->alpha = p->alpha; P->P_e = p->P_e;
-    for (int k = 0; k < 4; ++k) P->b[k] = (double)H.e[k];
-    P->d = p->d;
-    P->D_o = p->D_o; P->half_ax = 0.5 * p->alpha_x; P->inv_yeq = 1.0 / p->y_eq;
-    P->rc = p->rc; P->rc_m = p->rc_morse; P->rc2 = p->rc * p->rc; P->rcm2 = p->rc_morse * p->rc_morse;
-    P->f_rc = (double)H.f_rc; P->df_rc = (double)H.df_rc; P->m_rc = (double)H.m_rc; P->dm_rc = (double)H.dm_rc;
-    P->shifted = p->shifted; P->tabulated = 0;
+    fill_forms(p, P, H);
+    P->tabulated = 0;
     return MD_OK;
 }
 

@@ -84,5 +84,6 @@ def test_autotune_picks_a_valid_configuration(md, params):
     sim = md.MD([rep], params, precision="mixed", tpa=best.tpa, block=best.block, skin=best.skin,
                 rebuild_every=best.rebuild_every)
     o = oracle.forces(oracle.Potential(params), rep.x_cr, rep.box_lo, rep.box_hi, rep.periodic, rep.x_c)
-    assert rel_force_err(sim.forces(0), o["F"]).max() < 2e-4   # perfect lattice: the absolute FP32 floor
+    # the perfect lattice at t = 0: interior forces vanish by symmetry, F_rms is small
+    assert rel_force_err(sim.forces(0), o["F"]).max() <= 1e-5
     sim.step(50)

@@ -186,8 +186,12 @@ def test_launch_shapes_agree(md, params, tpa, block):
         sim.close()
 
 
-def test_trajectory_fp64_fixed_rebuilds(md, params):
-    rep = tiny(amp=0.05, gap=2.5, T=400.0)
+@pytest.mark.parametrize("gap", [1.0, 2.5])
+def test_trajectory_fp64_fixed_rebuilds(md, params, gap):
+    """50 FP64 steps with rebuilds every 7 steps against the oracle's run.  gap 1.0 A puts
+    the indenter's lowest atoms 1.8 A from the film (inside the Cr-C repulsive wall, 857
+    Cr-C pairs within the Morse cut-off); gap 2.5 A near the Morse minimum (321 pairs)."""
+    rep = tiny(amp=0.05, gap=gap, T=400.0)
     sim = md.MD([rep], params, precision="fp64", rebuild_every=7)
     osim = oracle.Sim(oracle.Potential(params), rep, skin=0.3, rebuild_every=7)
     for chunk in (1, 9, 40):
@@ -314,18 +318,19 @@ def test_interleaved_calls_keep_the_trajectory(md, params):
         sim.close()
 
 
-def _uneven_replicas(n=5):
+def _uneven_replicas(n=5, gap=2.0):
     reps = []
     for r, (nxy, nz, R, T) in enumerate([(6, 6, 5.0, 100.0), (9, 7, 6.0, 450.0), (7, 11, 5.5, 250.0),
                                          (11, 6, 8.0, 300.0), (8, 9, 6.5, 500.0)][:n]):
-        rep = mi.make_replica(f"r{r}", nxy, nxy, nz, R, T, seed=100 + r, gap=2.0)
+        rep = mi.make_replica(f"r{r}", nxy, nxy, nz, R, T, seed=100 + r, gap=gap)
         reps.append(jitter(rep, 0.08, r))
     return reps
 
 
+@pytest.mark.parametrize("gap", [1.2, 2.0])
 @pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("mixed", MIXED_TOL)])
-def test_batched_replicas_match_oracle(md, params, precision, tol):
-    reps = _uneven_replicas()
+def test_batched_replicas_match_oracle(md, params, precision, tol, gap):
+    reps = _uneven_replicas(gap=gap)
     sim = md.MD(reps, params, precision=precision)
     info = sim.info()
     assert info["replicas"] == len(reps) and info["n_cr"] == sum(r.n_cr for r in reps)
@@ -336,8 +341,9 @@ def test_batched_replicas_match_oracle(md, params, precision, tol):
         energy_close(sim.energy(r), o, 1e-12 if precision == "fp64" else 1e-5, 1e-10 if precision == "fp64" else 1e-4)
 
 
-def test_batched_trajectory_equals_replicas_alone(md, params):
-    reps = _uneven_replicas(3)
+@pytest.mark.parametrize("gap", [1.2, 2.0])
+def test_batched_trajectory_equals_replicas_alone(md, params, gap):
+    reps = _uneven_replicas(3, gap=gap)
     batch = md.MD(reps, params, precision="fp64", rebuild_every=5)
     batch.step(30)
     for r, rep in enumerate(reps):

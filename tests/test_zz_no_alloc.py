@@ -1,10 +1,12 @@
 """md_forces_small, the entry point that allocates nothing, against the existing path
 (md_init + md_compute_forces in FP64 with the analytic forms) on the same systems, through
-the C ABI; two calls in a row on one stream, each compared with its reference."""
+the C ABI; two calls in a row on one stream, each compared with its reference.  Also
+against the FP64 oracle directly, and the device's free memory across many calls."""
 import numpy as np
 import pytest
 
 import md_inputs as mi
+import oracle
 from gpu_helpers import jitter, rel_force_err, tiny
 
 pytestmark = pytest.mark.gpu
@@ -89,3 +91,38 @@ def test_sizes_beyond_the_scratch_are_rejected(env, params):
         md.md_forces_small(md.make_params(params, tabulated=1), 10, None, 0, None, [0, 0, 0], [50, 50, 50],
                            [0, 0, 0], None, None, 0)
     assert ei.value.code == md.MD_ERR_ARG
+
+
+def test_matches_the_oracle_directly(env, params):
+    """The all-pairs minimum image of md_forces_small (d - L rint(d / L)) against the
+    oracle's own forces and energies for a film with the indenter in reach."""
+    torch, md = env
+    p = md.make_params(params, tabulated=0)
+    rep = tiny(amp=0.12, gap=1.0, seed=21)
+    x, xc, F, E = device_inputs(torch, rep)
+    call(md, torch, p, rep, x, xc, F, E)
+    torch.cuda.synchronize()
+    o = oracle.forces(oracle.Potential(params, tabulated=0), rep.x_cr, rep.box_lo, rep.box_hi, rep.periodic,
+                      rep.x_c + np.array([0.0, 0.0, rep.z_indenter0]))
+    assert rel_force_err(F.cpu().numpy(), o["F"]).max() <= TOL
+    e = E.cpu().numpy()
+    for k, name in enumerate(("embed", "pair", "mterm", "morse")):
+        assert e[k] == pytest.approx(o[name], rel=ETOL, abs=1e-12), name
+
+
+def test_no_device_memory_taken_after_set_up(env, params):
+    """After the per-device set-up, calls leave the device's free memory unchanged (the
+    scratch is the library's static array; nothing is allocated per call)."""
+    torch, md = env
+    p = md.make_params(params, tabulated=0)
+    rep = tiny(amp=0.1, gap=1.5, seed=22)
+    x, xc, F, E = device_inputs(torch, rep)
+    stream = torch.cuda.current_stream().cuda_stream
+    md.md_forces_small(p, 0, None, 0, None, [0, 0, 0], [1, 1, 1], [0, 0, 0], None, None, stream)
+    call(md, torch, p, rep, x, xc, F, E)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(200):
+        call(md, torch, p, rep, x, xc, F, E)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
