@@ -236,6 +236,18 @@ def run_gpu(args):
     n_cr = sum(r.n_cr for r in reps)
     n_c = sum(r.n_c for r in reps)
     stream = torch.cuda.current_stream()
+    tuned = None
+    if args.autotune if args.autotune is not None else args.workload == "8M":
+        # the launch shape, Verlet skin and rebuild rule chosen by timing candidates on this
+        # workload (each candidate from the same initial state)
+        from paper_1507_07068_gb300.autotune import autotune
+        t = autotune(reps, params, precision=args.precision,
+                     shapes=((1, 64), (1, 128), (1, 256), (2, 128)), skins=(0.8, 1.0, 1.1, 1.2),
+                     steps=60, warmup=5, base_skin=args.skin)
+        args.tpa, args.block, args.skin, args.rebuild_every = t.tpa, t.block, t.skin, t.rebuild_every
+        tuned = {"chosen": {"tpa": t.tpa, "block": t.block, "skin_A": t.skin, "rebuild_every": t.rebuild_every,
+                            "ms_per_step": t.ms_per_step},
+                 "table": [dict(o, ms_per_step=m) for o, m in t.table]}
     sim = md.MD(reps, params, precision=args.precision, skin=args.skin, rebuild_every=args.rebuild_every,
                 tpa=args.tpa, block=args.block, use_graph=not args.no_graph, inner_skin=args.inner_skin)
 
@@ -381,7 +393,8 @@ def run_gpu(args):
                    else "displacement rule 2 max|dx| > skin (conditional graph node)",
                    "rebuilds_in_timed_region": rebuilds, "tpa": args.tpa or 1, "block": args.block or 128,
                    "l2": "working set larger than L2 (neighbour list alone %.0f MB)" % (n_cr * kmean * 4 / 1e6),
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "autotuned": tuned},
         "roofline": {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                      "algorithmic_bytes_per_atom": algorithmic_bytes(dom, kmean, kin, kskin, args.precision),
@@ -542,6 +555,9 @@ def main():
     ap.add_argument("--inner-skin", type=float, default=0.0,
                     help="skin of the inner list (0 = library default 0.1 A; < 0 = rebuilt every step)")
     ap.add_argument("--rebuild-every", type=int, default=0)
+    ap.add_argument("--autotune", dest="autotune", action="store_true", default=None,
+                    help="choose tpa, block, skin and the rebuild rule by timing (default: on for the 8M film)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--no-paper-cubes", action="store_true",
                     help="skip the variant timing the paper's Table 2 workload (r* = 8.262 A cubes)")
     ap.add_argument("--no-graph", action="store_true",

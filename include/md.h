@@ -192,9 +192,15 @@ int md_build_neighbors(md_t *h);
  * forces, energies and load (Eq. (1), Eqs. A1-A10).  Uses the current lists. */
 int md_compute_forces(md_t *h);
 
-/* Advance every replica by n >= 0 time steps (Fig. 5: Tasks 1-5 per step).  Device-side
- * errors raised during the n steps (overflow, lost atom, skin violation) are returned
- * when the call ends; the state after such an error is not meaningful. */
+/* Advance every replica by n >= 0 time steps (Fig. 5: Tasks 1-5 per step).
+ * A neighbour list that overflows its capacity (kmax / kcmax) at a rebuild inside the call
+ * is recovered: the library grows the capacity past the count it met, returns every
+ * replica to the state the call started from, rebuilds the lists there and runs the n
+ * steps again (the rebuild count then includes that extra build, and the sums over pairs
+ * follow the new lists' order).  For this it keeps a device copy of positions, velocities
+ * and indenter state when n >= 16 or when the last build filled more than 3/4 of a
+ * capacity; a call without that copy, and the other device-side errors (lost atom, skin
+ * violation), return the error when the call ends, and the state is then not meaningful. */
 int md_step(md_t *h, int64_t n);
 
 /* As md_step, launching every kernel directly with CUDA events around each phase, and

@@ -32,6 +32,36 @@ __global__ void k_state_in(const double *stage, double *d0, double *d1, const De
     for (int k = 0; k < 3; ++k) dst[k * S + s] = stage[3 * (size_t)o + k];
 }
 
+// md_step's checkpoint (recovery from a list overflow): every replica's positions and
+// velocities in caller order (replica r from 3 real_off), from the state buffer
+__global__ void k_ckpt_save(DevArgs a, double *cx, double *cv)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.S) return;
+    const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
+    if (s - R.slot_off >= R.n_atoms) return;
+    const size_t S = a.S, o = 3 * ((size_t)R.real_off + a.orig[s]);
+    const double *x = a.xs[a.st->ph & 1];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { cx[o + k] = x[k * S + s]; cv[o + k] = a.v[k * S + s]; }
+}
+
+// the checkpoint back into the current slot order, positions into both buffers
+__global__ void k_ckpt_restore(DevArgs a, const double *cx, const double *cv)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.S) return;
+    const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
+    if (s - R.slot_off >= R.n_atoms) return;
+    const size_t S = a.S, o = 3 * ((size_t)R.real_off + a.orig[s]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        a.xs[0][k * S + s] = cx[o + k];
+        a.xs[1][k * S + s] = cx[o + k];
+        a.v[k * S + s] = cv[o + k];
+    }
+}
+
 // the per-atom virial of replica r into caller order, 6 per atom
 __global__ void k_vir_out(const double *vir, double *stage, const int32_t *orig, int slot_off, int n, size_t S)
 {
@@ -98,6 +128,12 @@ struct md_handle {
     bool energies_valid = false;   // the energy sums belong to the current state
     std::vector<cudaEvent_t> ev;
     std::string err;
+    // md_step's checkpoint (allocated on first use): positions and velocities of all replicas
+    // in caller order, the per-replica and global device state
+    double *ck_x = nullptr, *ck_v = nullptr;
+    RepState *ck_rs = nullptr;
+    DevStatus *ck_st = nullptr;
+    int32_t last_max_cnt = 0, last_max_cntc = 0;   // list maxima of the last status read
 };
 
 namespace {
@@ -145,6 +181,8 @@ int read_status(md_t *h, DevStatus *st)
     CU(cudaMemcpyAsync(&h->hp->st, h->a.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     *st = h->hp->st;
+    h->last_max_cnt = st->max_cnt;
+    h->last_max_cntc = st->max_cntc;
     return MD_OK;
 }
 
@@ -190,6 +228,45 @@ int rebuild_now(md_t *h)
     return MD_OK;
 }
 
+void destroy_graphs(md_t *h);
+
+// replace a device array by a larger one (the contents are not kept: a list build follows).
+// The step graphs hold the old pointer: they are destroyed here and rebuilt by the caller.
+template <class T>
+int regrow(md_t *h, T **p, size_t n)
+{
+    destroy_graphs(h);
+    auto it = std::find(h->allocs.begin(), h->allocs.end(), (void *)*p);
+    if (it != h->allocs.end()) {
+        CU(cudaStreamSynchronize(h->stream));
+        cudaFree(*p);
+        h->allocs.erase(it);
+    }
+    return dalloc(h, p, n);
+}
+
+// list capacities grown past the counts of an overflowing build; *grew = false when the
+// status shows no overflow to grow for
+int grow_lists(md_t *h, const DevStatus &st, bool *grew)
+{
+    int rc;
+    *grew = false;
+    if ((st.err & MDE_OVERFLOW) && st.max_cnt > h->a.kmax) {
+        const int k = st.max_cnt + 16;
+        if ((rc = regrow(h, &h->a.nbr, (size_t)k * h->a.S))) return rc;
+        if (h->a.mixed && (rc = regrow(h, &h->a.inner, (size_t)k * h->a.S))) return rc;
+        h->a.kmax = k;
+        *grew = true;
+    }
+    if ((st.err & MDE_COVERFLOW) && st.max_cntc > h->a.kcmax) {
+        const int k = st.max_cntc + 32;
+        if ((rc = regrow(h, &h->a.nbrc, (size_t)k * h->a.S))) return rc;
+        h->a.kcmax = k;
+        *grew = true;
+    }
+    return MD_OK;
+}
+
 // grow the list capacities when the last build overflowed (outside md_step only)
 int rebuild_growing(md_t *h)
 {
@@ -199,25 +276,9 @@ int rebuild_growing(md_t *h)
         if ((rc = rebuild_now(h))) return rc;
         DevStatus st{};
         if ((rc = read_status(h, &st))) return rc;
-        bool grow = false;
-        if ((st.err & MDE_OVERFLOW) && st.max_cnt > h->a.kmax) {
-            int k = st.max_cnt + 16;
-            int32_t *p;
-            if ((rc = dalloc(h, &p, (size_t)k * h->a.S))) return rc;
-            h->a.nbr = p;
-            if (h->a.mixed) {
-                if ((rc = dalloc(h, &p, (size_t)k * h->a.S))) return rc;
-                h->a.inner = p;
-            }
-            h->a.kmax = k; grow = true;
-        }
-        if ((st.err & MDE_COVERFLOW) && st.max_cntc > h->a.kcmax) {
-            int k = st.max_cntc + 32;
-            int32_t *p;
-            if ((rc = dalloc(h, &p, (size_t)k * h->a.S))) return rc;
-            h->a.nbrc = p; h->a.kcmax = k; grow = true;
-        }
-        if (!grow) return status_to_code(h, st);
+        bool grew = false;
+        if ((rc = grow_lists(h, st, &grew))) return rc;
+        if (!grew) return status_to_code(h, st);
     }
     return fail(h, MD_ERR_NBR_OVERFLOW, "neighbour capacity kept growing");
 }
@@ -757,13 +818,45 @@ static int ensure_forces(md_t *h)
     return MD_OK;
 }
 
-int md_step(md_t *h, int64_t n)
+// md_step's checkpoint: every replica's positions and velocities in caller order and the
+// device state words, queued on the stream (copies within the device)
+static int save_checkpoint(md_t *h)
 {
-    if (!h) return MD_ERR_ARG;
-    if (n < 0) return fail(h, MD_ERR_ARG, "md_step: n < 0");
-    int rc = ensure_forces(h);
+    if (!h->ck_x) {
+        int rc;
+        if ((rc = dalloc(h, &h->ck_x, 3 * (size_t)h->n_cr)) || (rc = dalloc(h, &h->ck_v, 3 * (size_t)h->n_cr)) ||
+            (rc = dalloc(h, &h->ck_rs, h->n_rep)) || (rc = dalloc(h, &h->ck_st, 1)))
+            return rc;
+    }
+    k_ckpt_save<<<(h->a.S + 255) / 256, 256, 0, h->stream>>>(h->a, h->ck_x, h->ck_v);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(h->ck_rs, h->a.rs, h->n_rep * sizeof(RepState), cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaMemcpyAsync(h->ck_st, h->a.st, sizeof(DevStatus), cudaMemcpyDeviceToDevice, h->stream));
+    return MD_OK;
+}
+
+// after a list overflow inside md_step: capacities grown past the overflowing counts, every
+// replica back at the checkpoint, lists rebuilt there, forces and the step graphs renewed
+static int restore_checkpoint(md_t *h, const DevStatus &st)
+{
+    bool grew = false;
+    int rc = grow_lists(h, st, &grew);
     if (rc) return rc;
-    if ((rc = clear_err(h))) return rc;
+    k_ckpt_restore<<<(h->a.S + 255) / 256, 256, 0, h->stream>>>(h->a, h->ck_x, h->ck_v);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(h->a.rs, h->ck_rs, h->n_rep * sizeof(RepState), cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaMemcpyAsync(h->a.st, h->ck_st, sizeof(DevStatus), cudaMemcpyDeviceToDevice, h->stream));
+    // the FP32 copies of the positions belong to the abandoned steps: the build bins in FP64
+    CU(cudaMemsetAsync(&h->a.st->pos4_ok, 0, sizeof(int32_t), h->stream));
+    if ((rc = rebuild_growing(h))) return rc;
+    if ((rc = forces_now(h, h->stream))) return rc;
+    h->forces_valid = true;
+    return build_graphs(h);
+}
+
+static int run_steps(md_t *h, int64_t n)
+{
+    int rc;
     if (h->opt.use_graph && h->exec1 && n > 0) {
         // steps 0 .. n-2 without the energies, step n-1 with them (k_reduce follows)
         int64_t k = 0;
@@ -784,9 +877,30 @@ int md_step(md_t *h, int64_t n)
         CU(launch_reduce(h->a, h->cfg, h->stream));
         h->energies_valid = true;
     }
-    DevStatus st{};
-    if ((rc = read_status(h, &st))) return rc;
-    return status_to_code(h, st);
+    return MD_OK;
+}
+
+int md_step(md_t *h, int64_t n)
+{
+    if (!h) return MD_ERR_ARG;
+    if (n < 0) return fail(h, MD_ERR_ARG, "md_step: n < 0");
+    for (int attempt = 0;; ++attempt) {
+        int rc = ensure_forces(h);
+        if (rc) return rc;
+        if ((rc = clear_err(h))) return rc;
+        // a copy to come back to if a list build inside the call overflows: for calls long
+        // enough to amortise it, or when the last build filled more than 3/4 of a capacity
+        const bool near = 4 * (int64_t)h->last_max_cnt > 3 * (int64_t)h->a.kmax ||
+                          4 * (int64_t)h->last_max_cntc > 3 * (int64_t)h->a.kcmax;
+        const bool ck = n > 0 && attempt < 4 && (n >= 16 || near);
+        if (ck && (rc = save_checkpoint(h))) return rc;
+        if ((rc = run_steps(h, n))) return rc;
+        DevStatus st{};
+        if ((rc = read_status(h, &st))) return rc;
+        if (!ck || !(st.err & (MDE_OVERFLOW | MDE_COVERFLOW)) || (st.err & ~(MDE_OVERFLOW | MDE_COVERFLOW)))
+            return status_to_code(h, st);
+        if ((rc = restore_checkpoint(h, st))) return rc;   // then the n steps again
+    }
 }
 
 int md_step_profiled(md_t *h, int64_t n, md_phase_times *out)

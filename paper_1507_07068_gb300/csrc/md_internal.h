@@ -54,21 +54,22 @@ struct alignas(32) Cf64 {
 struct PotF32 {
     float rmin_s_f, inv_hf, rmin_s_m, inv_hm, lf0, beta, f_rc, df_rc, rc;
     float inv_re, d, b0, b1, b2, b3;
-    // Eq. A4 in FP32, about t = tc instead of the double root (t = r/r_e - d, s = t - tc):
+    // Eq. A4 in FP32, about t = tc instead of the double root (t = r/r_e - d): with
+    // s = (r - rs) / r_e = t - tc, rs = r_e (d + tc) an FP32 number near 0.95 r_e,
     // Phi = t^2 (b0 + b1 s + b2 s^2 + b3 s^3), dPhi/dr = t (c0 + c1 s + c2 s^2 + c3 s^3).
     // About the double root the cubic's terms cancel ~60-fold at the first neighbour shell;
-    // about tc (near the first two shells) they do not.  s = r inv_re - (d + tc), with the
-    // FP32 rounding of 1/r_e and d + tc carried in inv_re_lo, dc_lo.
+    // about tc (between the first two shells) they do not, and r - rs is exact.
     float c0, c1, c2, c3;
-    float tc, dc, dc_lo;
+    float tc, rs;
     float D_o, half_ax, inv_yeq, m_rc, dm_rc, rc_m;
     float F_o, n, inv_rho_e, alpha, inv_P_e, rc2;
     int32_t tabulated, nf, nm;
     const float4 *tf, *tp, *tm;
     const float4 *tfp;   // f and Phi coefficients interleaved: [2k] = f, [2k + 1] = Phi
-    // direct FP32 forms of the pair loops: f = f_e (r_e^2 / r^2)^ipow when beta = 2 ipow
-    // (ipow = 0: exp2/log2 form); r / r_e - d with the FP32 rounding of 1/r_e and d carried
-    float f_e, re2, inv_re_lo;
+    // direct FP32 forms of the pair loops: f = (re2f / r^2)^ipow when beta = 2 ipow, with
+    // re2f = f_e^(1/ipow) r_e^2 (ipow = 0: exp2/log2 form); the shifted-force terms as
+    // f(r) - f(rc) - (r - rc) f'(rc) = f(r) - cf - r df_rc, cf = f(rc) - rc f'(rc)
+    float re2f, cf;
     int32_t ipow;
 };
 

@@ -188,12 +188,14 @@ int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs
     q.lf0 = (float)P->lf0; q.beta = (float)P->beta; q.f_rc = (float)P->f_rc; q.df_rc = (float)P->df_rc;
     q.rc = (float)P->rc; q.inv_re = (float)(1.0 / P->r_e); q.d = (float)P->d;
     {
-        // Eq. A4 about t = tc: tc is t at r = 0.95 r_e (between BCC's first two neighbour
-        // shells for the forms here) rounded to a multiple of 1/64, exact in FP32.  The cubics
-        // B(t) = sum e_k t^k (Phi = t^2 B) and C(t) = sum (k + 2) e_k t^k / r_e (dPhi/dr = t C)
-        // are re-expanded in s = t - tc in extended precision and rounded once.
-        const long double tc = rintl(64.0L * (0.95L - (long double)p->d)) / 64.0L;
+        // Eq. A4 about t = tc: rs = r_e (d + tc) is the FP32 number nearest 0.95 r_e (between
+        // BCC's first two neighbour shells for the forms here), so that r - rs is exact near
+        // the first shells.  The cubics B(t) = sum e_k t^k (Phi = t^2 B) and
+        // C(t) = sum (k + 2) e_k t^k / r_e (dPhi/dr = t C) are re-expanded in s = t - tc in
+        // extended precision and rounded once.
+        const float rs = (float)(0.95L * (long double)p->r_e);
         const long double re = p->r_e;
+        const long double tc = (long double)rs / re - (long double)p->d;
         long double B[4], Cc[4];
         for (int k = 0; k < 4; ++k) { B[k] = H.e[k]; Cc[k] = (k + 2) * H.e[k] / re; }
         auto shift = [&](const long double (&c)[4], float (&o)[4]) {
@@ -208,9 +210,7 @@ int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs
         q.b0 = bb[0]; q.b1 = bb[1]; q.b2 = bb[2]; q.b3 = bb[3];
         q.c0 = cc[0]; q.c1 = cc[1]; q.c2 = cc[2]; q.c3 = cc[3];
         q.tc = (float)tc;
-        const long double dc = (long double)p->d + tc;
-        q.dc = (float)dc;
-        q.dc_lo = (float)(dc - (long double)q.dc);
+        q.rs = rs;
     }
     q.D_o = (float)P->D_o; q.half_ax = (float)P->half_ax; q.inv_yeq = (float)P->inv_yeq;
     q.m_rc = (float)P->m_rc; q.dm_rc = (float)P->dm_rc; q.rc_m = (float)P->rc_m;
@@ -218,11 +218,10 @@ int md_build_pot(const md_params *p, PotDev *P, Cf64 **d_tabs64, float4 **d_tabs
     q.inv_P_e = (float)(1.0 / P->P_e); q.rc2 = (float)P->rc2;
     q.tabulated = P->tabulated; q.nf = nf; q.nm = nm; q.tf = P->tf32; q.tp = P->tp32; q.tm = P->tm32;
     q.tfp = *d_tabs32 + 2 * nf + nm;
-    q.f_e = (float)p->f_e;
-    q.re2 = (float)(p->r_e * p->r_e);
-    q.inv_re_lo = (float)(1.0L / (long double)p->r_e - (long double)q.inv_re);
     const double half_beta = 0.5 * p->beta;
     q.ipow = (half_beta == floor(half_beta) && half_beta >= 1.0 && half_beta <= 8.0) ? (int)half_beta : 0;
+    q.re2f = (float)(powl((long double)p->f_e, q.ipow > 0 ? 1.0L / q.ipow : 1.0L) * (long double)p->r_e * p->r_e);
+    q.cf = (float)(H.f_rc - (long double)p->rc * H.df_rc);
     return MD_OK;
 }
 
@@ -1181,9 +1180,12 @@ __device__ __forceinline__ PairGeom pair_geom(const RepDev &R, int ci)
 // PER = false: no atom of the warp sits in an edge cell of a periodic axis, so no pair
 // crosses a periodic face and the correction is left out (the caller decides per warp, so
 // the branch between the two forms is uniform)
+// The displacement is returned in units of qu (FP32, one rounding): the callers scale r^2
+// by qu^2 and a force sum by qu once (exact powers of two, so every result is bit for bit
+// what the same arithmetic on displacements in A gives).
 template <bool PER>
 __device__ __forceinline__ void disp(const int4 &pi, const int4 &pj, unsigned dir, const int4 *sm_off,
-                                     const PairGeom &G, float qu, float &dx, float &dy, float &dz)
+                                     const PairGeom &G, float &dx, float &dy, float &dz)
 {
     const int4 o = sm_off[dir];
     int ix = pj.x - pi.x + o.x, iy = pj.y - pi.y + o.y, iz = pj.z - pi.z + o.z;
@@ -1195,7 +1197,7 @@ __device__ __forceinline__ void disp(const int4 &pi, const int4 &pj, unsigned di
             iz += (c & 16 ? -G.dL2 : 0) + (c & 32 ? G.dL2 : 0);
         }
     }
-    dx = qf(ix, qu); dy = qf(iy, qu); dz = qf(iz, qu);
+    dx = __int2float_rn(ix); dy = __int2float_rn(iy); dz = __int2float_rn(iz);
 }
 
 template <bool B> struct BoolC { static constexpr bool value = B; };
@@ -1218,17 +1220,13 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
 // The pair loops of the mixed path evaluate the forms of Eqs. A2 and A4 directly in FP32
 // (no table gather: at FP32 resolution a Hermite table adds nothing but 32 bytes of memory
 // traffic per pair; its deviation from the forms is below 1e-11).  f: for an even integer
-// beta the power is (r_e^2/r^2)^(beta/2) by multiplication; Phi: Taylor form about the
-// double root, with t = r/r_e - d formed with the rounding of 1/r_e and d compensated.
-// r_e^2 / r^2 from one reciprocal refined by a Newton step (about 1 ulp, no IEEE divide).
-// IPOW > 0: beta = 2 IPOW known at compile time; IPOW = 0: from Q.ipow (or exp2/log2).
+// beta the power (f_e^(2/beta) r_e^2 / r^2)^(beta/2) by multiplication; Phi: about t = tc
+// (PotF32).  IPOW > 0: beta = 2 IPOW known at compile time; IPOW = 0: from Q.ipow, else
+// the exp2/log2 form.
 template <int IPOW>
-__device__ __forceinline__ float f_direct(const Pot32 &Q, float r2, float r)
+__device__ __forceinline__ float f_pow(const Pot32 &Q, float q, float r)
 {
     if (IPOW > 0 || Q.ipow > 0) {
-        const float rcp = __fdividef(1.0f, r2);
-        float q = Q.re2 * rcp;
-        q = fmaf(rcp, fmaf(-q, r2, Q.re2), q);
         float fr = q;
         if (IPOW > 0) {
 #pragma unroll
@@ -1236,7 +1234,7 @@ __device__ __forceinline__ float f_direct(const Pot32 &Q, float r2, float r)
         } else {
             for (int k = 1; k < Q.ipow; ++k) fr *= q;
         }
-        return fr * Q.f_e;
+        return fr;
     }
     return exp2f(Q.lf0 - Q.beta * log2f(r));
 }
@@ -1248,24 +1246,34 @@ __device__ __forceinline__ float rsqrt_nr(float r2)
     return y * fmaf(-0.5f * r2 * y, y, 1.5f);
 }
 
+// f(r) of the density pass.  q = re2f / r^2 from one reciprocal refined by a Newton step
+// (about 1 ulp: the densities' rounding feeds F'(rho) of every neighbour); r itself enters
+// only the shifted-force term r f'(rc) (f'(rc) is ~4 % of f' at the first shell), where the
+// unrefined square root's 2 ulp are negligible -- except in the exp2/log2 form of f.
 template <int IPOW>
 __device__ __forceinline__ float fa_val(const Pot32 &Q, float r2)
 {
-    const float r = r2 * rsqrt_nr(r2);
-    return f_direct<IPOW>(Q, r2, r) - Q.f_rc - (r - Q.rc) * Q.df_rc;
+    const bool gen = IPOW == 0 && Q.ipow == 0;
+    const float r = r2 * (gen ? rsqrt_nr(r2) : rsqrtf(r2));
+    const float rcp = __fdividef(1.0f, r2);
+    float q = Q.re2f * rcp;
+    q = fmaf(rcp, fmaf(-q, r2, Q.re2f), q);
+    return fmaf(-r, Q.df_rc, f_pow<IPOW>(Q, q, r) - Q.cf);
 }
 
-// f, f' and Phi' of a pair, and Phi itself when EN (the energies are wanted).  Phi beyond
-// its double root (t > 0) is zero with its slope; t is clamped to 0 there, where both
-// forms (t^2 times a cubic in s, t times a cubic in s) give exactly 0.
+// f, f' and Phi' of a pair (force pass), and Phi itself when EN (the energies are wanted),
+// from r2 and the refined 1/r (the force's direction factor): r = r2 / r, q = re2f / r^2.
+// Phi beyond its double root (t > 0) is zero with its slope; t is clamped to 0 there, where
+// both forms (t^2 times a cubic in s, t times a cubic in s) give exactly 0.
 template <int IPOW, bool EN>
 __device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, float &f, float &df, float &ph, float &dph)
 {
     const float r = r2 * rinv;
-    const float fr = f_direct<IPOW>(Q, r2, r);
-    f = fr - Q.f_rc - (r - Q.rc) * Q.df_rc;
-    df = -Q.beta * fr * rinv - Q.df_rc;
-    const float sv = fmaf(r, Q.inv_re, -Q.dc) + fmaf(r, Q.inv_re_lo, -Q.dc_lo);   // t - tc
+    const float fr = f_pow<IPOW>(Q, Q.re2f * (rinv * rinv), r);
+    f = fmaf(-r, Q.df_rc, fr - Q.cf);
+    const float beta = IPOW > 0 ? 2.0f * IPOW : Q.beta;
+    df = fmaf(-beta * fr, rinv, -Q.df_rc);
+    const float sv = (r - Q.rs) * Q.inv_re;   // t - tc
     const float t = fminf(sv + Q.tc, 0.0f);
     ph = EN ? t * t * fmaf(fmaf(fmaf(Q.b3, sv, Q.b2), sv, Q.b1), sv, Q.b0) : 0.0f;
     dph = t * fmaf(fmaf(fmaf(Q.c3, sv, Q.c2), sv, Q.c1), sv, Q.c0);
@@ -1303,6 +1311,7 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
     const int4 *pp = a.p4[buf_step(a)];   // positions x(t + dt)
     const int4 pi = pp[s];
     const PairGeom G = pair_geom(R, pi.w);
+    const float qu2 = a.qu * a.qu;   // r^2 from displacements in units of qu
     const bool per = __any_sync(0xffffffffu, real && G.xmask != 0u);
     auto work = [&](auto PERC) {
         constexpr bool PER = decltype(PERC)::value;
@@ -1322,8 +1331,8 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
 #pragma unroll
                 for (int u = 0; u < MD_UNROLL; ++u) {
                     float dx, dy, dz;
-                    disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, a.qu, dx, dy, dz);
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * qu2;
                     if (k0 + u * TPA < n && r2 < a.rin2) {
                         // lane-interleaved rows: each lane owns rows lane, lane + TPA, ...
                         a.inner[(size_t)(m * TPA + lane) * S + s] = (int32_t)e[u];
@@ -1361,11 +1370,11 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
 #pragma unroll
                 for (int u = 0; u < MD_UNROLL; ++u) {
                     float dx, dy, dz;
-                    disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, a.qu, dx, dy, dz);
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * qu2;
                     // padding entries (the atom itself) and entries now beyond rc drop out
                     const bool in = (e[u] & MD_J_MASK) != (unsigned)s && r2 < Q.rc2;
-                    float f = fa_val<IPOW>(Q, in ? r2 : Q.re2);
+                    float f = fa_val<IPOW>(Q, in ? r2 : Q.rc2);
                     f = in ? f : 0.0f;
                     rho += f;
                     Ps = fmaf(f, f, Ps);
@@ -1441,6 +1450,7 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
     const int4 *pp = a.p4[bn];
     const int4 pi = pp[s];
     const PairGeom G = pair_geom(R, pi.w);
+    const float qu2 = a.qu * a.qu;   // r^2 from displacements in units of qu
     const bool per = __any_sync(0xffffffffu, real && G.xmask != 0u);
     if (TPA == 1) {   // this warp's inner-list rows (32 atoms: 128 B per row) on their way to L2
         const int nmax = __reduce_max_sync(0xffffffffu, real ? a.icnt[s] : 0);
@@ -1482,8 +1492,8 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
 #pragma unroll
             for (int u = 0; u < FU; ++u) {
                 float dx, dy, dz;
-                disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, a.qu, dx, dy, dz);
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * qu2;
                 if ((e[u] & MD_J_MASK) != (unsigned)s) {   // padding is the atom itself
                     // inner-list entries beyond rc (at most rc + inner skin) drop out by a
                     // select: their terms are finite
@@ -1503,6 +1513,7 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
         }
     };
     if (per) work(BoolC<true>{}); else work(BoolC<false>{});
+    gx *= a.qu; gy *= a.qu; gz *= a.qu;   // the pair sums were taken over displacements in units of qu
     // Cr-C (Morse): summed by k_morse_mixed for the atoms with Cr-C neighbours
     if (real && lane == 0 && a.cntc[s] > 0) {
         const float4 fmo = a.fmorse[s];
@@ -1782,7 +1793,8 @@ __global__ void __launch_bounds__(256) k_virial_mixed(DevArgs a, PotDev P)
             const unsigned j = e & MD_J_MASK;
             if (j == (unsigned)s) continue;   // padding
             float dx, dy, dz;
-            disp<PER>(pi, __ldg(&pp[j]), e >> MD_J_BITS, sm_off, G, a.qu, dx, dy, dz);
+            disp<PER>(pi, __ldg(&pp[j]), e >> MD_J_BITS, sm_off, G, dx, dy, dz);
+            dx *= a.qu; dy *= a.qu; dz *= a.qu;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             if (!(r2 < Q.rc2)) continue;
             const float2 fmj = __ldg(&a.fm32[j]);
