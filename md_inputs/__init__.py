@@ -252,3 +252,13 @@ def small_cluster(n_side: int = 3, a: float = A_CR, jitter: float = 0.05, seed: 
                    fixed=np.zeros(len(x), np.uint8), x_c=np.zeros((0, 3)), box_lo=lo, box_hi=hi,
                    periodic=np.zeros(3, np.int32), z_indenter0=0.0, v_indenter=0.0, dt=1.0,
                    mass_cr=MASS_CR, temperature=0.0, z_surface0=float(x[:, 2].max()))
+
+
+def paper_indentation_film(T: float = 10.0, seed: int = 1507 + 5) -> Replica:
+    """The paper's nano-indentation system (Sec. 2.5, Sec. 4.3): a Cr film of 19 x 19 x 14 BCC
+    unit cells with free lateral faces (11054 atoms), the bottom layer of unit cells (two
+    atomic planes) fixed, velocities at 10 K, and a diamond hemisphere of radius 9.78 A
+    (the paper's 394 C; the lattice registration is not printed) 3 A above the top plane,
+    moving at 10 m/s."""
+    return make_replica("p11k", 19, 19, 14, 9.78, T, seed=seed, n_fixed_planes=2, gap=3.0,
+                        v_ind_ms=10.0, free_lateral=True)

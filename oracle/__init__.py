@@ -95,6 +95,8 @@ def lib():
         L.or_sim_set_v_ind.argtypes = [C.c_void_p, C.c_double]
         L.or_sim_virial.restype = C.c_int
         L.or_sim_virial.argtypes = [C.c_void_p, dp]
+        L.or_forces_given.restype = C.c_int
+        L.or_forces_given.argtypes = [C.c_void_p, C.c_int32, dp, dp, dp, ip, C.c_int32, dp, up, dp, dp, dp, dp, dp]
         L.or_virial.restype = C.c_int
         L.or_virial.argtypes = [C.c_void_p, C.c_int32, dp, dp, dp, ip, C.c_int32, dp, C.c_int32, dp, dp, dp]
         L.or_sim_step.restype = C.c_int
@@ -224,6 +226,24 @@ def forces(pot: Potential, x, lo, hi, periodic, xc=None, method: int = 1, want_a
     if want_atoms:
         out.update(rho=rho, P=P, e_atom=ea)
     return out
+
+
+def forces_given(pot: Potential, x, lo, hi, periodic, xc=None, given=None, fm_in=None):
+    """The two passes of Task 4 with an exchange between them (the paper's F', M'
+    Allgatherv, Sec. 3.3.2): returns F, fm (F'(rho_i), M'(P_i) from this call's own first
+    pass, (n, 2)), the per-atom energies and the energy sums; atoms with given[i] != 0 enter
+    the second pass with fm_in[i] instead of their own first-pass values."""
+    x = _arr(x).reshape(-1, 3)
+    xc = np.zeros((0, 3)) if xc is None else _arr(xc).reshape(-1, 3)
+    n = len(x)
+    g = np.zeros(n, np.uint8) if given is None else _arr(given, np.uint8)
+    fin = np.zeros((n, 2)) if fm_in is None else _arr(fm_in).reshape(n, 2)
+    F = np.zeros((n, 3)); ep = np.zeros(5); fm = np.zeros((n, 2)); ea = np.zeros(n)
+    err = lib().or_forces_given(pot.h, n, x, _arr(lo), _arr(hi), _arr(periodic, np.int32), len(xc),
+                                xc if len(xc) else np.zeros(3), g, fin, fm, F, ep, ea)
+    if err:
+        raise RuntimeError(f"or_forces_given: {err}")
+    return dict(F=F, fm=fm, e_atom=ea, embed=ep[0], pair=ep[1], mterm=ep[2], morse=ep[3], load=ep[4])
 
 
 def virial(pot: Potential, x, lo, hi, periodic, xc=None, method: int = 1):

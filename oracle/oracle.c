@@ -584,7 +584,7 @@ static void add_virial(double *w, double c, const double *d)
 static int eval_forces(const or_pot *P, int32_t n, const double *x, const or_box *b,
                        const or_list *nl, int32_t nc, const double *xc, const or_list *cl,
                        double *F, double *rho_out, double *P_out, double *eatom_out, or_epot *E,
-                       double *W)
+                       double *W, const uint8_t *given, const double *fm_in, double *fm_out)
 {
     const or_params *p = &P->p;
     double rc2 = p->rc * p->rc, rcm2 = p->rc_m * p->rc_m;
@@ -614,6 +614,10 @@ static int eval_forces(const or_pot *P, int32_t n, const double *x, const or_box
         embed(p, rho, &Fv, &Fd);
         mterm(p, Ps, &Mv, &Md);
         Fp[i] = Fd; Mp[i] = Md; e_emb[i] = Fv; e_m[i] = Mv;
+        if (fm_out) { fm_out[2 * i] = Fd; fm_out[2 * i + 1] = Md; }
+        /* F'(rho_i), M'(P_i) that arrived from elsewhere (the exchange between the two
+         * passes, Sec. 3.3.2) replace the local ones */
+        if (given && given[i]) { Fp[i] = fm_in[2 * i]; Mp[i] = fm_in[2 * i + 1]; }
         if (rho_out) rho_out[i] = rho;
         if (P_out) P_out[i] = Ps;
     }
@@ -676,7 +680,31 @@ int or_forces(const or_pot *P, int32_t n, const double *x, const double *lo, con
     int err = build_list(n, x, &b, P->p.rc, method, &nl);
     if (!err && nc > 0) err = build_clist(n, x, nc, xc, &b, P->p.rc_m, &cl);
     or_epot E = {0, 0, 0, 0, 0};
-    if (!err) err = eval_forces(P, n, x, &b, &nl, nc, xc, nc > 0 ? &cl : NULL, F, rho, Pden, eatom, &E, NULL);
+    if (!err) err = eval_forces(P, n, x, &b, &nl, nc, xc, nc > 0 ? &cl : NULL, F, rho, Pden, eatom, &E, NULL,
+                             NULL, NULL, NULL);
+    list_free(&nl); list_free(&cl);
+    if (err) return err;
+    epot[0] = E.embed; epot[1] = E.pair; epot[2] = E.mterm; epot[3] = E.morse; epot[4] = E.load;
+    return 0;
+}
+
+/* as or_forces, with the two passes of Task 4 open to an exchange between them (the
+ * paper's F', M' Allgatherv, Sec. 3.3.2): fm_out (2n, may be NULL) receives F'(rho_i),
+ * M'(P_i) of every atom from pass 1; for atoms with given[i] != 0, pass 2 uses
+ * fm_in[2i], fm_in[2i + 1] instead (values computed where those atoms' whole
+ * neighbourhoods are known).  eatom: per-atom energies (embedding + M of the atom's own
+ * pass-1 values, half its pair terms, its Morse terms). */
+int or_forces_given(const or_pot *P, int32_t n, const double *x, const double *lo, const double *hi,
+                    const int32_t *per, int32_t nc, const double *xc, const uint8_t *given,
+                    const double *fm_in, double *fm_out, double *F, double *epot, double *eatom)
+{
+    or_box b; or_list nl = {0}, cl = {0};
+    box_set(&b, lo, hi, per);
+    int err = build_list(n, x, &b, P->p.rc, 1, &nl);
+    if (!err && nc > 0) err = build_clist(n, x, nc, xc, &b, P->p.rc_m, &cl);
+    or_epot E = {0, 0, 0, 0, 0};
+    if (!err) err = eval_forces(P, n, x, &b, &nl, nc, xc, nc > 0 ? &cl : NULL, F, NULL, NULL, eatom, &E, NULL,
+                                given, fm_in, fm_out);
     list_free(&nl); list_free(&cl);
     if (err) return err;
     epot[0] = E.embed; epot[1] = E.pair; epot[2] = E.mterm; epot[3] = E.morse; epot[4] = E.load;
@@ -693,7 +721,8 @@ int or_virial(const or_pot *P, int32_t n, const double *x, const double *lo, con
     int err = build_list(n, x, &b, P->p.rc, method, &nl);
     if (!err && nc > 0) err = build_clist(n, x, nc, xc, &b, P->p.rc_m, &cl);
     or_epot E = {0, 0, 0, 0, 0};
-    if (!err) err = eval_forces(P, n, x, &b, &nl, nc, xc, nc > 0 ? &cl : NULL, F, NULL, NULL, NULL, &E, W);
+    if (!err) err = eval_forces(P, n, x, &b, &nl, nc, xc, nc > 0 ? &cl : NULL, F, NULL, NULL, NULL, &E, W,
+                             NULL, NULL, NULL);
     list_free(&nl); list_free(&cl);
     if (err) return err;
     epot[0] = E.embed; epot[1] = E.pair; epot[2] = E.mterm; epot[3] = E.morse; epot[4] = E.load;
@@ -748,7 +777,7 @@ static int sim_forces(or_sim *S)
 {
     sim_place_indenter(S);
     return eval_forces(S->P, S->n, S->x, &S->b, &S->nl, S->nc, S->xc, S->nc > 0 ? &S->cl : NULL,
-                       S->F, NULL, NULL, NULL, &S->E, NULL);
+                       S->F, NULL, NULL, NULL, &S->E, NULL, NULL, NULL, NULL);
 }
 
 static void sim_kinetic(or_sim *S)
@@ -856,7 +885,7 @@ int or_sim_virial(or_sim *S, double *W)
 {
     sim_place_indenter(S);
     return eval_forces(S->P, S->n, S->x, &S->b, &S->nl, S->nc, S->xc, S->nc > 0 ? &S->cl : NULL,
-                       S->F, NULL, NULL, NULL, &S->E, W);
+                       S->F, NULL, NULL, NULL, &S->E, W, NULL, NULL, NULL);
 }
 
 /* the indenter's velocity from the next step on (Task 2; the loading and unloading legs

@@ -14,6 +14,7 @@ starts at minus the initial gap.
 from __future__ import annotations
 
 import math
+import os
 from typing import Optional
 
 import numpy as np
@@ -134,7 +135,10 @@ def main(argv=None) -> int:
     from paper_1507_07068_gb300 import md
 
     ap = argparse.ArgumentParser(description=main.__doc__)
-    ap.add_argument("--workload", default="64k")
+    ap.add_argument("--workload", default="p11k",
+                    help="p11k: the paper's 11k system (Sec. 2.5), or a preset film (tiny, 64k, 1M, 8M)")
+    ap.add_argument("--params", default="",
+                    help="parameter JSON (default: cr_c_params_indent.json for p11k, else cr_c_params.json)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--relax", type=int, default=10000, help="steps with the indenter at rest")
     ap.add_argument("--depth", type=float, default=3.08, help="maximum depth (A)")
@@ -145,11 +149,17 @@ def main(argv=None) -> int:
                     help="Cr-C list capacity (a deep indent puts many C atoms in reach of one Cr atom)")
     ap.add_argument("--curve", default="", help="write the samples to this .npz file")
     args = ap.parse_args(argv)
-    if args.workload not in mi.PRESETS:
-        raise SystemExit(f"--workload: one of {sorted(mi.PRESETS)}")
-    rep = mi.make_workload(args.workload).replicas[0]
-    R = float(mi.PRESETS[args.workload][3])   # the hemisphere's radius (A)
-    sim = md.MD([rep], md.load_params(), precision=args.precision, skin=args.skin, kcmax=args.kcmax)
+    if args.workload == "p11k":
+        rep, R = mi.paper_indentation_film(), 9.78
+        pfile = args.params or os.path.join(os.path.dirname(os.path.abspath(__file__)), "cr_c_params_indent.json")
+    elif args.workload in mi.PRESETS:
+        rep = mi.make_workload(args.workload).replicas[0]
+        R = float(mi.PRESETS[args.workload][3])   # the hemisphere's radius (A)
+        pfile = args.params or None
+    else:
+        raise SystemExit(f"--workload: p11k or one of {sorted(mi.PRESETS)}")
+    params = md.load_params(pfile) if pfile else md.load_params()
+    sim = md.MD([rep], params, precision=args.precision, skin=args.skin, kcmax=args.kcmax)
     out = run(sim, 0, relax_steps=args.relax, depth_max=args.depth, speed=args.speed_ms * 1e-5,
               sample_every=args.sample_every)
     sim.close()
@@ -157,6 +167,7 @@ def main(argv=None) -> int:
         np.savez(args.curve, **{k: v for k, v in out.items() if k != "i_unload"}, i_unload=out["i_unload"])
     iu = out["i_unload"]
     res = {"workload": args.workload, "n_cr": int(rep.n_cr), "n_c": int(rep.n_c), "precision": args.precision,
+           "params": os.path.basename(pfile) if pfile else "cr_c_params.json",
            "steps": int(out["step"][-1]), "max_load": float(out["load"].max()), "min_load": float(out["load"].min()),
            "depth_at_max_load": float(out["depth"][int(np.argmax(out["load"]))])}
     if R > 0 and out["load"][:iu].max() <= 0:

@@ -242,3 +242,29 @@ def test_cr_c_list_in_narrow_periodic_box_matches_plain_minimum_image():
     # some pairs are reached only through the periodic image
     direct = rep.x_c[None, :, :2] - rep.x_cr[:, None, :2]
     assert np.any((r2 < cut * cut) & (np.abs(direct).max(-1) > 0.5 * L[0]))
+
+
+def test_forces_given_passes_equal_the_single_evaluation(params):
+    """The two passes of Task 4 with an exchange between them (oracle.forces_given): fed
+    back its own first-pass F'(rho), M'(P) for every atom, the second pass gives the forces
+    and energies of oracle.forces; a changed F' of one atom changes only the forces of the
+    atoms within rc of it."""
+    import md_inputs as mi
+    rep = mi.make_replica("given", 6, 6, 5, 5.0, 300.0, seed=4, gap=1.5)
+    x = rep.x_cr + np.random.default_rng(2).uniform(-0.1, 0.1, rep.x_cr.shape)
+    pot = oracle.Potential(params)
+    ref = oracle.forces(pot, x, rep.box_lo, rep.box_hi, rep.periodic, rep.x_c)
+    a = oracle.forces_given(pot, x, rep.box_lo, rep.box_hi, rep.periodic, rep.x_c)
+    b = oracle.forces_given(pot, x, rep.box_lo, rep.box_hi, rep.periodic, rep.x_c,
+                            given=np.ones(len(x), np.uint8), fm_in=a["fm"])
+    assert np.array_equal(a["F"], ref["F"]) and np.array_equal(b["F"], ref["F"])
+    assert a["pair"] == ref["pair"] and a["embed"] == ref["embed"]
+    assert a["e_atom"].sum() == pytest.approx(ref["potential"], rel=1e-12)
+    k = 17
+    fm = a["fm"].copy(); fm[k, 0] += 0.05
+    g = np.zeros(len(x), np.uint8); g[k] = 1
+    c = oracle.forces_given(pot, x, rep.box_lo, rep.box_hi, rep.periodic, rep.x_c, given=g, fm_in=fm)
+    changed = np.nonzero(np.abs(c["F"] - ref["F"]).max(1) > 0)[0]
+    off, idx = oracle.neighbors(x, rep.box_lo, rep.box_hi, rep.periodic, params["rc"])
+    assert set(changed.tolist()) <= set(idx[off[k]:off[k + 1]].tolist()) | {k}
+    assert len(changed) > 5
