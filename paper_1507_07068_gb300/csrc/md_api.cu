@@ -897,8 +897,10 @@ int md_step(md_t *h, int64_t n)
         if ((rc = run_steps(h, n))) return rc;
         DevStatus st{};
         if ((rc = read_status(h, &st))) return rc;
-        if (!ck || !(st.err & (MDE_OVERFLOW | MDE_COVERFLOW)) || (st.err & ~(MDE_OVERFLOW | MDE_COVERFLOW)))
-            return status_to_code(h, st);
+        // after an overflowing build the lists miss pairs, so whatever else the rest of the
+        // call raised (a lost atom, a skin violation) may be its consequence: go back and
+        // redo it; an error of its own comes back in the redo and is reported then
+        if (!ck || !(st.err & (MDE_OVERFLOW | MDE_COVERFLOW))) return status_to_code(h, st);
         if ((rc = restore_checkpoint(h, st))) return rc;   // then the n steps again
     }
 }
