@@ -126,6 +126,10 @@ typedef struct md_system {
  *                   inner_skin / 2 since its last build; 0 = default 0.1 A; < 0 = rebuilt
  *                   every step with radius rc, as in the paper.  Forces do not depend on
  *                   it: both loops take exactly the pairs within rc, in Verlet-list order.
+ *   debug_checks  : nonzero = every list build (in md_step too) is followed by the checks
+ *                   of md_check_lists at the list radius; a violation ends the call with
+ *                   MD_ERR_STATE and the counts in md_last_error (a debug mode: the check
+ *                   costs about as much as the build)
  */
 typedef struct md_options {
     const md_params *pot;
@@ -136,6 +140,7 @@ typedef struct md_options {
     int32_t tpa, block;
     int32_t use_graph;
     double inner_skin;
+    int32_t debug_checks;
 } md_options;
 
 /* Energies of one replica after the last force evaluation (eV); FP64 sums. */
@@ -255,6 +260,20 @@ int md_set_indenter_velocity(md_t *h, int32_t replica, double v_ind);
  * i's first min(cnt[i], kmax) entries in unspecified order. */
 int md_get_neighbors(md_t *h, int32_t replica, int32_t which, int32_t *cell_xyz, int32_t *cnt,
                      int32_t *nbr, int32_t kmax);
+
+/* Debug check of the neighbour lists of the last build (no counterpart in the paper; it
+ * stands in for a memory checker by testing, on the device, every invariant the pair
+ * kernels rely on when they index memory with list entries).  radius <= 0 means the list
+ * radius rc + skin.  out8 (caller-owned, 8 counts over all replicas):
+ *   [0] entries outside the atom's replica or naming the atom itself, [1] lengths above the
+ *   capacity, [2] direction codes that do not match the two atoms' cells, [3] listed pairs
+ *   at or beyond `radius` at the build positions (exact FP64), [4] pairs within `radius`
+ *   there that are missing, [5] pairs listed one way only, [6] Cr-C entries outside the
+ *   replica's indenter or beyond rc_morse + skin, [7] inner-list entries (MD_MIXED) that are
+ *   not in the Verlet list.
+ * All zero for lists as built.  With radius < rc + skin, [3] counts the listed pairs between
+ * radius and the list radius.  Synchronises the stream.  Errors: MD_ERR_ARG, MD_ERR_CUDA. */
+int md_check_lists(md_t *h, double radius, int64_t *out8);
 
 /* Utility (no counterpart in the paper): sizes of one handle.  out[0] = replicas,
  * out[1] = film atoms, out[2] = indenter atoms, out[3] = atom slots (incl. tile padding),

@@ -12,7 +12,7 @@
 
 #include "md_internal.h"
 
-#define MD_ABI_VERSION 6
+#define MD_ABI_VERSION 7
 
 namespace {
 
@@ -193,6 +193,10 @@ int status_to_code(md_t *h, const DevStatus &st)
     if (st.err & MDE_COVERFLOW) return fail(h, MD_ERR_NBR_OVERFLOW, "Cr-C neighbour list overflow: %d > kcmax %d", st.max_cntc, h->a.kcmax);
     if (st.err & MDE_SKIN) return fail(h, MD_ERR_SKIN_VIOLATION, "an atom moved more than skin/2 between fixed-interval rebuilds");
     if (st.err & MDE_SCHED) return fail(h, MD_ERR_STATE, "internal: a step found no drift from the last force kernel");
+    if (st.err & MDE_LISTCHECK)
+        return fail(h, MD_ERR_STATE, "list check after a build: %llu out of range, %llu over capacity, %llu wrong "
+                    "direction, %llu beyond the radius, %llu missing, %llu one-way, %llu bad Cr-C, %llu inner not in Verlet",
+                    st.chk[0], st.chk[1], st.chk[2], st.chk[3], st.chk[4], st.chk[5], st.chk[6], st.chk[7]);
     return MD_OK;
 }
 
@@ -572,6 +576,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     a.kcmax = opt->kcmax > 0 ? opt->kcmax : 160;
     a.mixed = opt->precision == MD_MIXED;
     a.rebuild_every = opt->rebuild_every;
+    a.debug = opt->debug_checks != 0;
     a.skin = opt->skin; a.cut = cut; a.cutc = cutc; a.cut2 = cut * cut; a.cutc2 = cutc * cutc;
     {
         // unit of the fixed-point cell-relative positions: the largest power of two
@@ -1147,6 +1152,18 @@ int md_get_neighbors(md_t *h, int32_t r, int32_t which, int32_t *cell_xyz, int32
         }
     }
     return MD_OK;
+}
+
+int md_check_lists(md_t *h, double radius, int64_t *out8)
+{
+    if (!h || !out8) return MD_ERR_ARG;
+    CU(launch_check_lists(h->a, radius, h->stream));
+    DevStatus st{};
+    int rc = read_status(h, &st);
+    if (rc) return rc;
+    for (int t = 0; t < MD_NCHK; ++t) out8[t] = (int64_t)st.chk[t];
+    // the violation bit belongs to this call, not to the steps: clear it again
+    return clear_err(h);
 }
 
 int md_get_info(md_t *h, int64_t *out9)

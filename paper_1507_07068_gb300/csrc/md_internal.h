@@ -36,7 +36,10 @@
 
 // error bits raised by kernels (device word, read by the host after md_step)
 // (MDE_SCHED: a step launched without k_verlet1 found no drift ready - a host bookkeeping error)
-enum { MDE_OVERFLOW = 1, MDE_LOST = 2, MDE_SKIN = 4, MDE_COVERFLOW = 8, MDE_SCHED = 16 };
+// (MDE_LISTCHECK: the debug check after a list build found a violation, see k_check_lists)
+enum { MDE_OVERFLOW = 1, MDE_LOST = 2, MDE_SKIN = 4, MDE_COVERFLOW = 8, MDE_SCHED = 16, MDE_LISTCHECK = 32 };
+// kinds of violation counted by k_check_lists (DevStatus::chk)
+#define MD_NCHK 8
 // what k_decide is launched for: an explicit list build (no step), a step whose Task 3 the
 // last step's force epilogue made (k_verlet1 runs only if the lists are rebuilt), or a step
 // that runs k_verlet1
@@ -168,6 +171,7 @@ struct DevStatus {
     // k_decide on, the positions the pair kernels evaluate); the state a step started from
     // is in buffer ph_cur & 1.  k_decide advances ph; md_set_state keeps it.
     int64_t ph, ph_cur;
+    unsigned long long chk[MD_NCHK];   // list-check violations by kind (md_check_lists)
 };
 
 // everything the kernels need, by value
@@ -178,6 +182,7 @@ struct DevArgs {
     int32_t kmax, kcmax;
     int32_t mixed;
     int32_t rebuild_every;
+    int32_t debug;               // nonzero: every list build is followed by k_check_lists
     double skin, cut2, cutc2, cut, cutc;
     float qu;                    // unit of the fixed-point positions, 2^-k A
     double qinv;                 // 2^k
@@ -243,6 +248,9 @@ cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c
 // must follow a launch with energies = 1); the FP64 one always writes them
 cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int energies,
                          cudaStream_t s);
+// the debug check of the lists of the last build: counters DevStatus::chk cleared, then
+// every atom's lists checked against `radius` (<= 0: the list radius rc + skin)
+cudaError_t launch_check_lists(const DevArgs &a, double radius, cudaStream_t s);
 // the Morse sums alone (mixed precision), and the force kernel with or without them first
 cudaError_t launch_morse(const DevArgs &a, const PotDev &p, cudaStream_t s);
 cudaError_t launch_force_split(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int energies,

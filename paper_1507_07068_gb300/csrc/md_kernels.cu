@@ -952,6 +952,118 @@ __global__ void k_build_done(DevArgs a)
     }
 }
 
+// ============================================================================ list check
+
+// The debug check of the lists of the last build (no counterpart in the paper: it stands
+// in for a memory checker, by testing every invariant the pair kernels rely on when they
+// index memory with list entries).  One thread per atom, counts by kind into st->chk:
+//   0 an entry outside the atom's replica or naming the atom itself, 1 a length above the
+//   capacity, 2 a direction code that does not match the two atoms' cells, 3 a listed pair
+//   at or beyond `radius` at the build positions (exact FP64), 4 a pair within `radius`
+//   there that is missing, 5 a pair listed one way only, 6 a Cr-C entry outside the
+//   replica's indenter or beyond rc_m + skin at the build, 7 an inner-list entry that is
+//   not in the Verlet list (checked when the inner list belongs to the current build).
+// Any violation also raises MDE_LISTCHECK.
+__global__ void __launch_bounds__(128) k_check_lists(DevArgs a, double radius)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.S) return;
+    const RepDev &R = a.rep[a.tile_rep[s / MD_TILE]];
+    if (s - R.slot_off >= R.n_atoms) return;
+    const size_t S = a.S;
+    const double r2max = radius * radius;
+    unsigned long long bad[MD_NCHK] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int n = a.cnt[s];
+    if (n < 0 || n > a.kmax) bad[1]++;
+    const int m = min(max(n, 0), a.kmax);
+    const int ci = a.cellc[s];
+    const int cc[3] = {cell_x(ci), cell_y(ci), cell_z(ci)};
+    auto dist2 = [&](int j) {
+        const double dx = mi_exact(__dsub_rn(a.xb[j], a.xb[s]), R.per[0], R.L[0]);
+        const double dy = mi_exact(__dsub_rn(a.xb[S + j], a.xb[S + s]), R.per[1], R.L[1]);
+        const double dz = mi_exact(__dsub_rn(a.xb[2 * S + j], a.xb[2 * S + s]), R.per[2], R.L[2]);
+        return norm2_exact(dx, dy, dz);
+    };
+    auto listed = [&](int i, unsigned j) {   // j (low bits) in the Verlet row of i
+        const int ni = min(max(a.cnt[i], 0), a.kmax);
+        for (int k = 0; k < ni; ++k)
+            if (((unsigned)a.nbr[(size_t)k * S + i] & MD_J_MASK) == j) return true;
+        return false;
+    };
+    for (int k = 0; k < m; ++k) {
+        const unsigned e = (unsigned)a.nbr[(size_t)k * S + s];
+        const int j = (int)(e & MD_J_MASK);
+        if (j < R.slot_off || j - R.slot_off >= R.n_atoms || j == s) { bad[0]++; continue; }
+        const int cj = a.cellc[j];
+        const int dj[3] = {cell_x(cj) - cc[0], cell_y(cj) - cc[1], cell_z(cj) - cc[2]};
+        unsigned dir = 0u;
+        bool ok = true;
+        for (int q = 0; q < 3; ++q) {
+            int d = dj[q];
+            if (R.per[q] && d > 1) d -= R.nc[q];
+            if (R.per[q] && d < -1) d += R.nc[q];
+            if (d < -1 || d > 1) ok = false;
+            dir |= (d < 0 ? 1u : 0u) << (2 * q);
+            dir |= (d > 0 ? 2u : 0u) << (2 * q);
+        }
+        if (!ok || dir != (e >> MD_J_BITS)) bad[2]++;
+        if (!(dist2(j) < r2max)) bad[3]++;
+        if (!listed(j, (unsigned)s)) bad[5]++;
+    }
+    // completeness: every atom of the stencil cells within radius of s at the build
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int q[3] = {cc[0] + dx, cc[1] + dy, cc[2] + dz};
+                bool skip = false;
+                for (int t = 0; t < 3; ++t) {
+                    if (q[t] < 0 || q[t] >= R.nc[t]) {
+                        if (!R.per[t]) skip = true;
+                        q[t] = (q[t] + R.nc[t]) % R.nc[t];
+                    }
+                }
+                if (skip) continue;   // (a periodic axis has >= 3 cells: no cell is visited twice)
+                const int key = R.cell_off + (q[2] * R.nc[1] + q[1]) * R.nc[0] + q[0];
+                const int b = a.cell_start[key], e = b + a.cell_count[key];
+                for (int t = b; t < e; ++t)
+                    if (t != s && dist2(t) < r2max && !listed(s, (unsigned)t)) bad[4]++;
+            }
+    // Cr-C list, at the indenter's displacement of the build
+    const int nc = a.cntc[s];
+    if (nc < 0 || nc > a.kcmax) bad[1]++;
+    const double zb = a.rs[a.tile_rep[s / MD_TILE]].z_build;
+    for (int k = 0; k < min(max(nc, 0), a.kcmax); ++k) {
+        const int c = a.nbrc[(size_t)k * S + s];
+        if (c < R.c_off || c - R.c_off >= R.n_c) { bad[6]++; continue; }
+        const size_t C = a.C;
+        const double dx = mi_exact(__dsub_rn(a.xc0[c], a.xb[s]), R.per[0], R.L[0]);
+        const double dy = mi_exact(__dsub_rn(a.xc0[C + c], a.xb[S + s]), R.per[1], R.L[1]);
+        const double dz = mi_exact(__dsub_rn(__dadd_rn(a.xc0[2 * C + c], zb), a.xb[2 * S + s]), R.per[2], R.L[2]);
+        if (!(norm2_exact(dx, dy, dz) < a.cutc2)) bad[6]++;
+    }
+    // inner list (mixed precision), when it belongs to this build
+    if (a.mixed && (a.st->inner_ok || a.st->inner_ok_next)) {
+        const int ni = a.icnt[s];
+        if (ni < 0 || ni > a.kmax) bad[1]++;
+        for (int k = 0; k < min(max(ni, 0), a.kmax); ++k) {
+            const unsigned e = (unsigned)a.inner[(size_t)k * S + s];
+            if ((e & MD_J_MASK) == (unsigned)s) continue;   // padding of a lane group
+            bool found = false;
+            for (int kk = 0; kk < m && !found; ++kk) found = (unsigned)a.nbr[(size_t)kk * S + s] == e;
+            if (!found) bad[7]++;
+        }
+    }
+    bool any = false;
+    for (int t = 0; t < MD_NCHK; ++t)
+        if (bad[t]) { atomicAdd(&a.st->chk[t], bad[t]); any = true; }
+    if (any) atomicOr(&a.st->err, MDE_LISTCHECK);
+}
+
+__global__ void k_zero_chk(DevArgs a)
+{
+    if (threadIdx.x < MD_NCHK) a.st->chk[threadIdx.x] = 0ull;
+}
+
 // ============================================================================ Tasks 2 + 3
 
 // Task 3 of one atom (Eqs. A11-A12: half kick, drift) from its state (x, v, F) at time t:
@@ -1992,6 +2104,17 @@ cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s)
     k_nbrc<<<nblk(a.S, 128), 128, 0, s>>>(a);
     k_nbrc_near<<<MD_NEAR_BLOCKS, 256, 0, s>>>(a);
     k_build_done<<<1, 256, 0, s>>>(a);
+    if (a.debug) {
+        k_zero_chk<<<1, 32, 0, s>>>(a);
+        k_check_lists<<<nblk(a.S, 128), 128, 0, s>>>(a, a.cut);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_lists(const DevArgs &a, double radius, cudaStream_t s)
+{
+    k_zero_chk<<<1, 32, 0, s>>>(a);
+    k_check_lists<<<nblk(a.S, 128), 128, 0, s>>>(a, radius > 0.0 ? radius : a.cut);
     return cudaGetLastError();
 }
 

@@ -50,7 +50,7 @@ class md_options(C.Structure):
     _fields_ = [("pot", C.POINTER(md_params)), ("precision", C.c_int32), ("skin", C.c_double),
                 ("rebuild_every", C.c_int32), ("kmax", C.c_int32), ("kcmax", C.c_int32),
                 ("tpa", C.c_int32), ("block", C.c_int32), ("use_graph", C.c_int32),
-                ("inner_skin", C.c_double)]
+                ("inner_skin", C.c_double), ("debug_checks", C.c_int32)]
 
 
 class md_energy(C.Structure):
@@ -80,7 +80,7 @@ _lib = None
 EXPORTS = ["md_init", "md_build_neighbors", "md_compute_forces", "md_step", "md_step_profiled",
            "md_get_energy", "md_get_forces", "md_get_indenter_load", "md_get_state", "md_set_state",
            "md_get_neighbors", "md_get_info", "md_last_error", "md_free", "md_version", "md_forces_small",
-           "md_set_indenter_velocity", "md_get_virial", "md_probe_fp64_fma"]
+           "md_set_indenter_velocity", "md_get_virial", "md_probe_fp64_fma", "md_check_lists"]
 
 
 def lib(build: bool = True):
@@ -109,6 +109,7 @@ def lib(build: bool = True):
     L.md_probe_fp64_fma.argtypes = [vp, vp]
     L.md_get_neighbors.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp, C.c_int32]
     L.md_get_info.argtypes = [vp, vp]
+    L.md_check_lists.argtypes = [vp, C.c_double, vp]
     L.md_last_error.argtypes = [vp]
     L.md_last_error.restype = C.c_char_p
     L.md_free.argtypes = [vp]
@@ -254,6 +255,16 @@ def md_get_info(h) -> dict:
     return dict(zip(keys, (int(v) for v in out)))
 
 
+CHECK_KINDS = ("out_of_range", "over_capacity", "wrong_direction", "beyond_radius", "missing", "one_way",
+               "bad_cr_c", "inner_not_in_verlet")
+
+
+def md_check_lists(h, radius: float = 0.0) -> dict:
+    out = np.zeros(8, np.int64)
+    _check(h, lib().md_check_lists(h, float(radius), _ptr(out)))
+    return dict(zip(CHECK_KINDS, (int(v) for v in out)))
+
+
 def md_free(h):
     if h:
         lib().md_free(h)
@@ -311,7 +322,7 @@ class MD:
     def __init__(self, replicas, params: Optional[dict] = None, precision: str = "mixed", skin: float = 0.3,
                  rebuild_every: int = 0, kmax: int = 0, kcmax: int = 0, tpa: int = 0, block: int = 0,
                  use_graph: bool = True, stream: Optional[int] = None, inner_skin: float = 0.0,
-                 **pot_override):
+                 debug_checks: bool = False, **pot_override):
         self.replicas = list(replicas)
         self.n = [r.n_cr for r in self.replicas]
         self._params = make_params(params or load_params(), **pot_override)
@@ -326,6 +337,7 @@ class MD:
         opt.kmax = int(kmax); opt.kcmax = int(kcmax); opt.tpa = int(tpa); opt.block = int(block)
         opt.use_graph = 1 if use_graph else 0
         opt.inner_skin = float(inner_skin)
+        opt.debug_checks = 1 if debug_checks else 0
         self._opt = opt
         self.stream = current_stream() if stream is None else int(stream)
         self.h = md_init(systems, opt, self.stream)
@@ -388,3 +400,6 @@ class MD:
 
     def info(self) -> dict:
         return md_get_info(self.h)
+
+    def check_lists(self, radius: float = 0.0) -> dict:
+        return md_check_lists(self.h, radius)

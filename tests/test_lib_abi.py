@@ -47,7 +47,7 @@ def test_binding_covers_the_header():
 
 def test_version_and_error_without_gpu(libmd):
     libmd.md_version.restype = C.c_int
-    assert libmd.md_version() == 6
+    assert libmd.md_version() == 7
     libmd.md_last_error.restype = C.c_char_p
     libmd.md_last_error.argtypes = [C.c_void_p]
     assert libmd.md_last_error(None) is not None
