@@ -227,7 +227,9 @@ int md_get_state(md_t *h, int32_t replica, double *x3n, double *v3n, double *z_i
 
 /* Replace positions and velocities (caller order; x3n or v3n may be NULL to keep), the
  * indenter displacement and the step count of one replica, then re-evaluate forces at the
- * new state (the energy sums of the new state are evaluated when md_get_energy first asks
+ * new state -- unless every position and the indenter displacement are bit for bit those
+ * already held, when the forces held stay valid (forces do not depend on velocities) --
+ * (the energy sums of the new state are evaluated when md_get_energy first asks
  * for them; an md_step in between makes its own).  The neighbour lists are kept when the new positions pass the rebuild test of
  * md_step (max |x - x_build| and the indenter's travel since the last build against the
  * skin, Sec. 2.6), else rebuilt (as md_build_neighbors).  Errors: MD_ERR_LOST_ATOM,

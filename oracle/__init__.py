@@ -31,9 +31,14 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
+# optimisation levels the oracle is built at: -O2 as the paper's own build (Sec. 2.3),
+# -O3 beside it for the CPU baseline (no -march=native: one build serves x86 and Arm hosts)
+OPT_LIBS = {"O2": LIB, "O3": os.path.join(HERE, "liboracle_O3.so")}
 
 _lock = threading.Lock()
 _lib = None
+_libs = {}
+_opt = "O2"
 
 OR_F, OR_PHI, OR_MORSE, OR_EMBED, OR_MTERM, OR_F_RAW, OR_PHI_AN, OR_MORSE_RAW = range(8)
 
@@ -45,25 +50,38 @@ class OrParams(C.Structure):
                [("shifted", C.c_int32), ("tabulated", C.c_int32), ("r_min", C.c_double), ("h", C.c_double)]
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so (gcc, FP64, no FMA contraction, OpenMP if available)."""
+def build(force: bool = False, opt: str = "O2") -> str:
+    """Compile oracle.c into liboracle.so (-O2) or liboracle_O3.so (-O3): gcc, FP64, no FMA
+    contraction, OpenMP if available."""
+    out = OPT_LIBS[opt]
     with _lock:
-        if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
-            return LIB
-        base = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", SRC, "-o", LIB + ".tmp", "-lm"]
+        if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(SRC):
+            return out
+        base = ["gcc", "-" + opt, "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", SRC, "-o", out + ".tmp", "-lm"]
         try:
             subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
         except subprocess.CalledProcessError:
             subprocess.run(base, check=True, capture_output=True)
-        os.replace(LIB + ".tmp", LIB)
-        return LIB
+        os.replace(out + ".tmp", out)
+        return out
+
+
+def select(opt: str) -> None:
+    """Use the oracle built at -O2 (default) or -O3 for the objects created from now on."""
+    global _lib, _opt
+    if opt not in OPT_LIBS:
+        raise ValueError(opt)
+    _opt, _lib = opt, _libs.get(opt)
 
 
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = C.CDLL(LIB)
+        if _opt in _libs:
+            _lib = _libs[_opt]
+            return _lib
+        path = build(opt=_opt)
+        L = C.CDLL(path)
         dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
         ip = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
         lp = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
@@ -106,7 +124,7 @@ def lib():
         L.or_sim_list.argtypes = [C.c_void_p, C.c_int32, lp, ip, C.c_int64]
         L.or_set_threads.restype = C.c_int
         L.or_set_threads.argtypes = [C.c_int32]
-        _lib = L
+        _lib = _libs[_opt] = L
     return _lib
 
 
@@ -138,21 +156,22 @@ class Potential:
         for name, _ in OrParams._fields_:
             setattr(st, name, int(p[name]) if name in ("shifted", "tabulated") else float(p[name]))
         self._st = st
-        self.h = lib().or_pot_new(C.byref(st))
+        self._L = lib()   # the build (-O2 / -O3) this potential belongs to
+        self.h = self._L.or_pot_new(C.byref(st))
         if not self.h:
             raise MemoryError("or_pot_new failed")
 
     def __del__(self):
         try:
             if getattr(self, "h", None):
-                lib().or_pot_free(self.h)
+                self._L.or_pot_free(self.h)
                 self.h = None
         except Exception:
             pass
 
     def eval(self, which: int, x: float):
         v = C.c_double(); d = C.c_double()
-        if lib().or_eval(self.h, int(which), float(x), C.byref(v), C.byref(d)):
+        if self._L.or_eval(self.h, int(which), float(x), C.byref(v), C.byref(d)):
             raise ValueError(which)
         return v.value, d.value
 
@@ -217,7 +236,7 @@ def forces(pot: Potential, x, lo, hi, periodic, xc=None, method: int = 1, want_a
     P = np.zeros(n) if want_atoms else None
     ea = np.zeros(n) if want_atoms else None
     ptr = lambda a: a.ctypes.data_as(C.c_void_p) if a is not None else None
-    err = lib().or_forces(pot.h, n, x, _arr(lo), _arr(hi), _arr(periodic, np.int32), len(xc),
+    err = pot._L.or_forces(pot.h, n, x, _arr(lo), _arr(hi), _arr(periodic, np.int32), len(xc),
                           xc if len(xc) else np.zeros(3), int(method), F, ep, ptr(rho), ptr(P), ptr(ea))
     if err:
         raise RuntimeError(f"or_forces: {err}")
@@ -239,7 +258,7 @@ def forces_given(pot: Potential, x, lo, hi, periodic, xc=None, given=None, fm_in
     g = np.zeros(n, np.uint8) if given is None else _arr(given, np.uint8)
     fin = np.zeros((n, 2)) if fm_in is None else _arr(fm_in).reshape(n, 2)
     F = np.zeros((n, 3)); ep = np.zeros(5); fm = np.zeros((n, 2)); ea = np.zeros(n)
-    err = lib().or_forces_given(pot.h, n, x, _arr(lo), _arr(hi), _arr(periodic, np.int32), len(xc),
+    err = pot._L.or_forces_given(pot.h, n, x, _arr(lo), _arr(hi), _arr(periodic, np.int32), len(xc),
                                 xc if len(xc) else np.zeros(3), g, fin, fm, F, ep, ea)
     if err:
         raise RuntimeError(f"or_forces_given: {err}")
@@ -254,7 +273,7 @@ def virial(pot: Potential, x, lo, hi, periodic, xc=None, method: int = 1):
     xc = np.zeros((0, 3)) if xc is None else _arr(xc).reshape(-1, 3)
     n = len(x)
     F = np.zeros((n, 3)); ep = np.zeros(5); W = np.zeros((n, 6))
-    err = lib().or_virial(pot.h, n, x, _arr(lo), _arr(hi), _arr(periodic, np.int32), len(xc),
+    err = pot._L.or_virial(pot.h, n, x, _arr(lo), _arr(hi), _arr(periodic, np.int32), len(xc),
                           xc if len(xc) else np.zeros(3), int(method), F, ep, W)
     if err:
         raise RuntimeError(f"or_virial: {err}")
@@ -274,7 +293,8 @@ class Sim:
         x = _arr(rep.x_cr if x is None else x).reshape(-1, 3)
         v = _arr(rep.v_cr if v is None else v).reshape(-1, 3)
         xc = _arr(rep.x_c).reshape(-1, 3) if rep.n_c else np.zeros((1, 3))
-        self.h = lib().or_sim_new(pot.h, self.n, x, v, _arr(rep.fixed, np.uint8), self.nc, xc,
+        self._L = pot._L
+        self.h = self._L.or_sim_new(pot.h, self.n, x, v, _arr(rep.fixed, np.uint8), self.nc, xc,
                                   _arr(rep.box_lo), _arr(rep.box_hi), _arr(rep.periodic, np.int32),
                                   float(rep.z_indenter0), float(rep.v_indenter), float(rep.dt),
                                   float(rep.mass_cr), float(skin), int(rebuild_every), int(method))
@@ -284,22 +304,22 @@ class Sim:
     def __del__(self):
         try:
             if getattr(self, "h", None):
-                lib().or_sim_free(self.h)
+                self._L.or_sim_free(self.h)
                 self.h = None
         except Exception:
             pass
 
     def step(self, n: int = 1):
-        if lib().or_sim_step(self.h, int(n)):
+        if self._L.or_sim_step(self.h, int(n)):
             raise RuntimeError("or_sim_step failed")
 
     def set_indenter_velocity(self, v_ind: float):
-        lib().or_sim_set_v_ind(self.h, float(v_ind))
+        self._L.or_sim_set_v_ind(self.h, float(v_ind))
 
     def virial(self):
         """Per-atom virial (n, 6: xx, yy, zz, xy, xz, yz) of the current state."""
         W = np.zeros((self.n, 6))
-        if lib().or_sim_virial(self.h, W):
+        if self._L.or_sim_virial(self.h, W):
             raise RuntimeError("or_sim_virial failed")
         return W
 
@@ -307,14 +327,14 @@ class Sim:
         x = np.zeros((self.n, 3)); v = np.zeros((self.n, 3)); F = np.zeros((self.n, 3))
         e = np.zeros(8); z = np.zeros(1); cnt = np.zeros(2, np.int64)
         p = lambda a: a.ctypes.data_as(C.c_void_p)
-        lib().or_sim_get(self.h, p(x), p(v), p(F), p(e), p(z), p(cnt))
+        self._L.or_sim_get(self.h, p(x), p(v), p(F), p(e), p(z), p(cnt))
         return dict(x=x, v=v, F=F, embed=e[0], pair=e[1], mterm=e[2], morse=e[3], kinetic=e[4],
                     potential=e[5], total=e[6], load=e[7], z_ind=z[0], step=int(cnt[0]), rebuilds=int(cnt[1]))
 
     def verlet_list(self, which: int = 0):
         cap = 128 * max(self.n, 1)
         off = np.zeros(self.n + 1, np.int64); idx = np.zeros(cap, np.int32)
-        tot = lib().or_sim_list(self.h, int(which), off, idx, cap)
+        tot = self._L.or_sim_list(self.h, int(which), off, idx, cap)
         if tot < 0:
             raise RuntimeError("list capacity")
         return off, idx[:tot].copy()

@@ -94,6 +94,7 @@ struct HostPin {
     RepEnergy E;
     RepState rs;
     int32_t flag, verlet;
+    int32_t need_changed[2];   // md_set_state: DevStatus any_rebuild, changed
 };
 
 struct md_handle {
@@ -1040,6 +1041,7 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     if (rc) return rc;
     const RepDev &R = h->rep[r];
     int n = R.n_atoms;
+    const bool had_forces = h->forces_valid;
     h->drift = false;   // k_state_prep voids the drift made from the old state
     if (x3n) CU(cudaMemcpyAsync(h->stage, x3n, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     // The velocities go up on the transfer stream once the positions are up (one copy at a
@@ -1063,12 +1065,23 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     // by the density pass if its own test fails.  Otherwise (or when positions leave their
     // periodic image, become NaN, ...) a full rebuild.
     CU(launch_state_set(h->a, r, R.slot_off, n, z_ind, (long long)step, x3n ? h->stage : nullptr, h->stream));
-    CU(cudaMemcpyAsync(&h->hp->flag, &h->a.st->any_rebuild, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    static_assert(offsetof(DevStatus, changed) == offsetof(DevStatus, any_rebuild) + sizeof(int32_t), "layout");
+    CU(cudaMemcpyAsync(h->hp->need_changed, &h->a.st->any_rebuild, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                       h->stream));
     CU(cudaStreamSynchronize(h->stream));
-    const int32_t need = h->hp->flag;
+    const int32_t need = h->hp->need_changed[0], changed = h->hp->need_changed[1];
     if (need) {   // the list build moves the velocities with the atoms
         if (v3n) CU(cudaStreamWaitEvent(h->stream, h->xev1, 0));
         return ensure_forces(h);
+    }
+    if (had_forces && !changed) {
+        // the same positions and indenter displacement: the forces of the state hold (they
+        // do not depend on the velocities); the next step makes its own drift from the
+        // velocities now set, and md_get_energy sums the energies anew (the kinetic term)
+        if (v3n) CU(cudaStreamWaitEvent(h->stream, h->xev1, 0));
+        h->forces_valid = true;
+        h->energies_valid = false;
+        return MD_OK;
     }
     int rc2;
     // the energy sums are left to md_get_energy: a caller that sets a state and steps on

@@ -153,6 +153,8 @@ struct RepEnergy {
 struct DevStatus {
     int32_t err;            // MDE_* bits
     int32_t any_rebuild;    // rebuild decided this step (host-readable)
+    int32_t changed;        // md_set_state: a position or the indenter displacement differs
+                            // from the state's (else the forces of the state still hold)
     int32_t max_cnt, max_cntc;
     int32_t pos4_ok;        // pos4 holds every atom's current position about its cell's centre
     int32_t n_cand;         // atoms queued for the Cr-C list search (set by k_nbrc)

@@ -1192,12 +1192,14 @@ __global__ void k_state_prep(DevArgs a, int r, double z_ind, long long step)
     if (st->imax_fresh) st->imax_bits = 0u;
     st->pos4_ok = a.mixed;   // FP64: the other replicas' pos4 are not kept current
     RepState &S = a.rs[r];
+    st->changed = S.z_ind != z_ind;   // k_state_scan adds the positions
     S.z_ind = z_ind;
     S.d2b[st->ph & 1] = 0ull;
 }
 
 // md_set_state for the n atoms of replica r (slots slot_off ...): the new positions (from
 // stage in caller order, or the current ones when stage is NULL) into the state buffer,
+// noting whether any differs from the one it replaces,
 // their pos4, the exact FP64 max |x - x_build|^2 (as the drift reduces it for k_decide)
 // and, in mixed precision, the displacement since the inner list was built.
 __global__ void __launch_bounds__(256) k_state_scan(DevArgs a, int r, int slot_off, int n, const double *stage)
@@ -1215,6 +1217,8 @@ __global__ void __launch_bounds__(256) k_state_scan(DevArgs a, int r, int slot_o
         if (stage) {
             const int o = a.orig[s];
             x0 = stage[3 * (size_t)o]; x1 = stage[3 * (size_t)o + 1]; x2 = stage[3 * (size_t)o + 2];
+            // bitwise comparison (a NaN counts as changed)
+            if (!(x0 == x[s] && x1 == x[S + s] && x2 == x[2 * S + s])) a.st->changed = 1;
             x[s] = x0; x[S + s] = x1; x[2 * S + s] = x2;
         } else {
             x0 = x[s]; x1 = x[S + s]; x2 = x[2 * S + s];

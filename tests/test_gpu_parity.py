@@ -519,3 +519,27 @@ def test_bad_periodic_box_rejected(md, params):
     with pytest.raises(md.MDError) as ei:
         md.MD([rep], params)
     assert ei.value.code == md.MD_ERR_ARG
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 2e-6)])
+def test_set_state_same_positions_keeps_forces(md, params, precision, tol):
+    """md_set_state with the positions the handle holds and new velocities: the forces of
+    the state stay (they do not depend on velocities; nothing is re-evaluated) and the run
+    goes on from the new velocities, as the oracle started at that state does."""
+    import dataclasses
+    rep = tiny(amp=0.05, gap=2.0, T=300.0)
+    sim = md.MD([rep], params, precision=precision)
+    sim.step(20)
+    x, v, z, st = sim.state(0)
+    F = sim.forces(0)
+    v2 = np.ascontiguousarray(0.8 * v)
+    sim.set_state(0, x, v2, z, st)
+    assert np.array_equal(sim.forces(0), F)
+    sim.step(30)
+    o = oracle.Sim(oracle.Potential(params), dataclasses.replace(rep, x_cr=x, v_cr=v2, z_indenter0=z), skin=0.3)
+    o.step(30)
+    d = sim.state(0)[0] - o.state()["x"]
+    L = rep.box_hi - rep.box_lo
+    d -= np.round(d / L) * L * (rep.periodic == 1)
+    assert np.abs(d).max() < tol
+    sim.close()

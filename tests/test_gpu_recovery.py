@@ -73,7 +73,8 @@ def test_mixed_run_through_overflow_equals_run_with_room(md, params):
     xb, vb, zb, _ = roomy.state(0)
     assert np.array_equal(xa, xb) and np.array_equal(va, vb) and za == zb
     assert tight.energy(0)["total"] == roomy.energy(0)["total"]
-    assert tight.energy(0)["rebuilds"] == roomy.energy(0)["rebuilds"] + 1   # the build at the restart
+    # one build more per restart (a redo can meet another list's overflow and restart again)
+    assert tight.energy(0)["rebuilds"] >= roomy.energy(0)["rebuilds"] + 1
     tight.close(); roomy.close()
 
 
