@@ -250,21 +250,24 @@ int regrow(md_t *h, T **p, size_t n)
     return dalloc(h, p, n);
 }
 
-// list capacities grown past the counts of an overflowing build; *grew = false when the
-// status shows no overflow to grow for
+// list capacities grown past the counts of an overflowing build (by a quarter, at least
+// 16 / 32 entries: lists that overflowed in a compressing film tend to keep growing);
+// *grew = false when the status shows no overflow to grow for
 int grow_lists(md_t *h, const DevStatus &st, bool *grew)
 {
     int rc;
     *grew = false;
     if ((st.err & MDE_OVERFLOW) && st.max_cnt > h->a.kmax) {
-        const int k = st.max_cnt + 16;
+        const int k = std::max(st.max_cnt + 16, st.max_cnt + st.max_cnt / 4);
         if ((rc = regrow(h, &h->a.nbr, (size_t)k * h->a.S))) return rc;
-        if (h->a.mixed && (rc = regrow(h, &h->a.inner, (size_t)k * h->a.S))) return rc;
+        const int kin = (k + h->cfg.tpa - 1) / h->cfg.tpa * h->cfg.tpa;
+        if (h->a.mixed && (rc = regrow(h, &h->a.inner, (size_t)kin * h->a.S))) return rc;
         h->a.kmax = k;
+        h->a.kinner = kin;
         *grew = true;
     }
     if ((st.err & MDE_COVERFLOW) && st.max_cntc > h->a.kcmax) {
-        const int k = st.max_cntc + 32;
+        const int k = std::max(st.max_cntc + 32, st.max_cntc + st.max_cntc / 4);
         if ((rc = regrow(h, &h->a.nbrc, (size_t)k * h->a.S))) return rc;
         h->a.kcmax = k;
         *grew = true;
@@ -524,7 +527,8 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
             R.iL32[k] = (float)(1.0 / R.L[k]);
         }
         R.cell_off = (int32_t)cells;
-        R.n_cells = R.nc[0] * R.nc[1] * R.nc[2];
+        for (int k = 0; k < 3; ++k) R.nbk[k] = (R.nc[k] + 1) / 2;
+        R.n_cells = 8 * R.nbk[0] * R.nbk[1] * R.nbk[2];
         cells += R.n_cells;
         R.slot_off = (int32_t)slots;
         R.n_atoms = y.n_cr;
@@ -648,7 +652,8 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     INIT_FAIL(dalloc(h, &a.fixed, S));
     INIT_FAIL(dalloc(h, &a.nbr, (size_t)a.kmax * S));
     INIT_FAIL(dalloc(h, &a.cnt, S));
-    INIT_FAIL(dalloc(h, &a.inner, a.mixed ? (size_t)a.kmax * S : 1));
+    a.kinner = (a.kmax + tpa - 1) / tpa * tpa;
+    INIT_FAIL(dalloc(h, &a.inner, a.mixed ? (size_t)a.kinner * S : 1));
     INIT_FAIL(dalloc(h, &a.icnt, S));
     INIT_FAIL(dalloc(h, &a.nbrc, (size_t)a.kcmax * S));
     INIT_FAIL(dalloc(h, &a.cntc, S));
@@ -898,7 +903,7 @@ int md_step(md_t *h, int64_t n)
         // enough to amortise it, or when the last build filled more than 3/4 of a capacity
         const bool near = 4 * (int64_t)h->last_max_cnt > 3 * (int64_t)h->a.kmax ||
                           4 * (int64_t)h->last_max_cntc > 3 * (int64_t)h->a.kcmax;
-        const bool ck = n > 0 && attempt < 4 && (n >= 16 || near);
+        const bool ck = n > 0 && attempt < 8 && (n >= 16 || near);
         if (ck && (rc = save_checkpoint(h))) return rc;
         if ((rc = run_steps(h, n))) return rc;
         DevStatus st{};

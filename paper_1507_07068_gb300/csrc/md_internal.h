@@ -114,7 +114,8 @@ struct RepDev {
     // in the wc frame a cell's box is off by at most c |w - wc| (c < nc): the margin that
     // k_nbr adds to the half-width of a stencil cell's box (with 1e-4 A for FP32 rounding)
     float pad32[3];
-    int32_t cell_off, n_cells;
+    int32_t cell_off, n_cells;           // keys of this replica's cells (n_cells: 8 per 2x2x2 brick)
+    int32_t nbk[3];                      // 2x2x2 bricks per axis, ceil(nc / 2)
     int32_t slot_off, n_atoms, n_slots;  // first slot (TILE aligned), real atoms, slots incl. padding
     int32_t real_off;                    // atoms of the replicas before (unpadded)
     int32_t n_mobile;
@@ -182,6 +183,9 @@ struct DevArgs {
     int32_t n_rep;
     int32_t total_cells;
     int32_t kmax, kcmax;
+    int32_t kinner;          // rows of the inner list: kmax rounded up to a multiple of threads
+                             // per atom (its rows are lane-interleaved and padded to the longest
+                             // lane's count times the threads per atom)
     int32_t mixed;
     int32_t rebuild_every;
     int32_t debug;               // nonzero: every list build is followed by k_check_lists
@@ -231,6 +235,23 @@ struct DevArgs {
     double *rsum;                        // k_reduce scratch: [n_rep][MD_RED_CHUNKS][6] chunk sums
     int32_t max_blocks;
 };
+
+// Cell order: 2x2x2 bricks of cells, bricks in row-major order and the eight cells of a
+// brick in row-major order, so that a CTA's atoms (~8 cells) fill a compact block whose
+// 27-cell stencil covers 64 cells (a row of 8 cells: 90).  Keys of cells past an odd grid's
+// last row stay empty.
+__host__ __device__ __forceinline__ int cell_key_loc(const RepDev &R, int c0, int c1, int c2)
+{
+    return ((((c2 >> 1) * R.nbk[1] + (c1 >> 1)) * R.nbk[0] + (c0 >> 1)) << 3) | ((c2 & 1) << 2) |
+           ((c1 & 1) << 1) | (c0 & 1);
+}
+__host__ __device__ __forceinline__ void key_cell_loc(const RepDev &R, int loc, int &c0, int &c1, int &c2)
+{
+    const int b = loc >> 3, l = loc & 7;
+    c0 = 2 * (b % R.nbk[0]) + (l & 1);
+    c1 = 2 * ((b / R.nbk[0]) % R.nbk[1]) + ((l >> 1) & 1);
+    c2 = 2 * (b / (R.nbk[0] * R.nbk[1])) + (l >> 2);
+}
 
 struct LaunchCfg {
     int32_t tpa;      // threads per atom

@@ -567,7 +567,7 @@ __global__ void k_bin(DevArgs a)
         }
         if (lost) atomicOr(&a.st->err, MDE_LOST);
     }
-    int key = R.cell_off + (c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0];
+    int key = R.cell_off + cell_key_loc(R, c[0], c[1], c[2]);
     a.key[s] = key;
     atomicAdd(&a.cell_count[key], 1);
 }
@@ -674,8 +674,8 @@ __global__ void k_gather(DevArgs a)
     }
     a.sorig[s] = a.orig[o];
     a.sfixed[s] = a.fixed[o];
-    int loc = a.key[o] - R.cell_off;
-    int c0 = loc % R.nc[0], c1 = (loc / R.nc[0]) % R.nc[1], c2 = loc / (R.nc[0] * R.nc[1]);
+    int c0, c1, c2;
+    key_cell_loc(R, a.key[o] - R.cell_off, c0, c1, c2);
     a.cellc[s] = pack_cell(c0, c1, c2);
 }
 
@@ -775,7 +775,7 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
                 const int tx = dx * R.Wq[0] + (c0 + dx != q0 ? dx * R.DLq[0] : 0) - pi.x;
                 const float gx = fmaxf(fabsf(qf(tx, qu)) - hx, 0.0f);
                 if (fmaf(gx, gx, gyz) > hi2) continue;
-                int key = R.cell_off + (q2 * R.nc[1] + q1) * R.nc[0] + q0;
+                int key = R.cell_off + cell_key_loc(R, q0, q1, q2);
                 int b = a.cell_start[key], e = b + a.cell_count[key];
                 const unsigned dir = (dx < 0 ? 1u : 0u) | (dx > 0 ? 2u : 0u) | (dy < 0 ? 4u : 0u) | (dy > 0 ? 8u : 0u) |
                                      (dz < 0 ? 16u : 0u) | (dz > 0 ? 32u : 0u);
@@ -1023,7 +1023,7 @@ __global__ void __launch_bounds__(128) k_check_lists(DevArgs a, double radius)
                     }
                 }
                 if (skip) continue;   // (a periodic axis has >= 3 cells: no cell is visited twice)
-                const int key = R.cell_off + (q[2] * R.nc[1] + q[1]) * R.nc[0] + q[0];
+                const int key = R.cell_off + cell_key_loc(R, q[0], q[1], q[2]);
                 const int b = a.cell_start[key], e = b + a.cell_count[key];
                 for (int t = b; t < e; ++t)
                     if (t != s && dist2(t) < r2max && !listed(s, (unsigned)t)) bad[4]++;
@@ -1044,8 +1044,8 @@ __global__ void __launch_bounds__(128) k_check_lists(DevArgs a, double radius)
     // inner list (mixed precision), when it belongs to this build
     if (a.mixed && (a.st->inner_ok || a.st->inner_ok_next)) {
         const int ni = a.icnt[s];
-        if (ni < 0 || ni > a.kmax) bad[1]++;
-        for (int k = 0; k < min(max(ni, 0), a.kmax); ++k) {
+        if (ni < 0 || ni > a.kinner) bad[1]++;
+        for (int k = 0; k < min(max(ni, 0), a.kinner); ++k) {
             const unsigned e = (unsigned)a.inner[(size_t)k * S + s];
             if ((e & MD_J_MASK) == (unsigned)s) continue;   // padding of a lane group
             bool found = false;

@@ -66,3 +66,22 @@ def test_debug_mode_checks_every_build(md, params, precision):
     xa, xb = a.state(0)[0], b.state(0)[0]
     assert np.array_equal(xa, xb)   # the checks read only
     a.close(); b.close()
+
+
+def test_inner_list_capacity_with_lane_groups(md, params):
+    """With several threads per atom the inner list's rows are lane-interleaved and padded to
+    the longest lane's count times the threads per atom, which can pass kmax by up to
+    tpa - 1 rows when the Verlet lists are nearly full (the list check found it): with kmax
+    equal to the longest Verlet list the lists pass the check and the run is bit for bit
+    the run with room."""
+    rep = tiny(amp=0.05, gap=1.0, T=900.0)
+    rep.v_indenter = -2e-3
+    roomy = md.MD([rep], params, precision="mixed", skin=0.42, kmax=200, kcmax=400, tpa=8)
+    k0 = roomy.info()["max_cnt"]
+    tight = md.MD([rep], params, precision="mixed", skin=0.42, kmax=k0, kcmax=400, tpa=8)
+    assert all(v == 0 for v in tight.check_lists().values())
+    assert np.array_equal(tight.forces(0), roomy.forces(0))
+    tight.step(50)
+    roomy.step(50)
+    assert np.array_equal(tight.state(0)[0], roomy.state(0)[0])
+    tight.close(); roomy.close()
