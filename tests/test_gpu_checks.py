@@ -68,7 +68,8 @@ def test_debug_mode_checks_every_build(md, params, precision):
     a.close(); b.close()
 
 
-def test_inner_list_capacity_with_lane_groups(md, params):
+@pytest.mark.parametrize("tpa", [2, 4, 8])
+def test_inner_list_capacity_with_lane_groups(md, params, tpa):
     """With several threads per atom the inner list's rows are lane-interleaved and padded to
     the longest lane's count times the threads per atom, which can pass kmax by up to
     tpa - 1 rows when the Verlet lists are nearly full (the list check found it): with kmax
@@ -76,12 +77,23 @@ def test_inner_list_capacity_with_lane_groups(md, params):
     the run with room."""
     rep = tiny(amp=0.05, gap=1.0, T=900.0)
     rep.v_indenter = -2e-3
-    roomy = md.MD([rep], params, precision="mixed", skin=0.42, kmax=200, kcmax=400, tpa=8)
+    roomy = md.MD([rep], params, precision="mixed", skin=0.42, kmax=200, kcmax=400, tpa=tpa)
     k0 = roomy.info()["max_cnt"]
-    tight = md.MD([rep], params, precision="mixed", skin=0.42, kmax=k0, kcmax=400, tpa=8)
+    tight = md.MD([rep], params, precision="mixed", skin=0.42, kmax=k0, kcmax=400, tpa=tpa)
     assert all(v == 0 for v in tight.check_lists().values())
     assert np.array_equal(tight.forces(0), roomy.forces(0))
     tight.step(50)
     roomy.step(50)
     assert np.array_equal(tight.state(0)[0], roomy.state(0)[0])
+    assert all(v == 0 for v in tight.check_lists().values())
     tight.close(); roomy.close()
+
+
+def test_batched_lists_pass_the_check(md, params):
+    """The 256-replica batch (uneven films, 128-slot tiles) after steps with rebuilds."""
+    w = mi.make_workload("batched")
+    b = md.MD(w.replicas, params, precision="mixed", skin=1.1)
+    b.step(150)
+    assert b.energy(0)["rebuilds"] > 0
+    assert all(v == 0 for v in b.check_lists().values())
+    b.close()

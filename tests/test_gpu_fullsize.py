@@ -69,6 +69,7 @@ def test_fullsize_mixed_forces(md, params, thermal_1m):
     Fm = sim.forces(0)
     ref = oracle.forces(oracle.Potential(params), rep.x_cr, rep.box_lo, rep.box_hi, rep.periodic,
                         rep.x_c + np.array([0.0, 0.0, rep.z_indenter0]))
+    assert all(v == 0 for v in sim.check_lists().values())
     err = rel_force_err(Fm, ref["F"])
     print("1M mixed: max %.2e p99 %.2e median %.2e F_rms %.3f" % (err.max(), np.quantile(err, 0.99),
                                                                    np.median(err), np.sqrt((ref["F"] ** 2).sum(1).mean())))

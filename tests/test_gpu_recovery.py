@@ -75,6 +75,7 @@ def test_mixed_run_through_overflow_equals_run_with_room(md, params):
     assert tight.energy(0)["total"] == roomy.energy(0)["total"]
     # one build more per restart (a redo can meet another list's overflow and restart again)
     assert tight.energy(0)["rebuilds"] >= roomy.energy(0)["rebuilds"] + 1
+    assert all(v == 0 for v in tight.check_lists().values())   # the lists after the restart
     tight.close(); roomy.close()
 
 
