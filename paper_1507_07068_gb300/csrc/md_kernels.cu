@@ -1466,19 +1466,19 @@ __global__ void __launch_bounds__(256, 5) k_density_mixed(DevArgs a, PotDev P)
             const int n = a.icnt[s];
             // the next batch's list entries are loaded while this batch is gathered and
             // summed (as in k_force), so only the gather's latency stays on the path
+            const size_t rstep = (size_t)TPA * S;
+            const int32_t *rowp = a.inner + (size_t)lane * S + s;
             unsigned en[MD_UNROLL];
 #pragma unroll
-            for (int u = 0; u < MD_UNROLL; ++u) {
-                const int k = lane + u * TPA;
-                en[u] = k < n ? ld_stream(&a.inner[(size_t)k * S + s]) : (unsigned)s;
-            }
-            for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL) {
+            for (int u = 0; u < MD_UNROLL; ++u)
+                en[u] = lane + u * TPA < n ? ld_stream(rowp + u * rstep) : (unsigned)s;
+            rowp += MD_UNROLL * rstep;
+            for (int k0 = lane; k0 < n; k0 += TPA * MD_UNROLL, rowp += MD_UNROLL * rstep) {
                 unsigned e[MD_UNROLL];
 #pragma unroll
                 for (int u = 0; u < MD_UNROLL; ++u) {
                     e[u] = en[u];
-                    const int k = k0 + (u + MD_UNROLL) * TPA;
-                    en[u] = k < n ? ld_stream(&a.inner[(size_t)k * S + s]) : (unsigned)s;
+                    en[u] = k0 + (u + MD_UNROLL) * TPA < n ? ld_stream(rowp + u * rstep) : (unsigned)s;
                 }
                 int4 pj[MD_UNROLL];
 #pragma unroll
@@ -1583,19 +1583,19 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
         // stays on each batch's path (2 entries: -2.5 % against 4 loaded together, which
         // with the look-ahead would spill under the register bound)
         constexpr int FU = 2;
+        // row k of this lane at rowp + (k - lane) / TPA * rstep: advanced by increments
+        const size_t rstep = (size_t)TPA * S;
+        const int32_t *rowp = a.inner + (size_t)lane * S + s;
         unsigned en[FU];
 #pragma unroll
-        for (int u = 0; u < FU; ++u) {
-            const int k = lane + u * TPA;
-            en[u] = k < n ? ld_stream(&a.inner[(size_t)k * S + s]) : (unsigned)s;
-        }
-        for (int k0 = lane; k0 < n; k0 += TPA * FU) {
+        for (int u = 0; u < FU; ++u) en[u] = lane + u * TPA < n ? ld_stream(rowp + u * rstep) : (unsigned)s;
+        rowp += FU * rstep;
+        for (int k0 = lane; k0 < n; k0 += TPA * FU, rowp += FU * rstep) {
             unsigned e[FU];
 #pragma unroll
             for (int u = 0; u < FU; ++u) {
                 e[u] = en[u];
-                const int k = k0 + (u + FU) * TPA;
-                en[u] = k < n ? ld_stream(&a.inner[(size_t)k * S + s]) : (unsigned)s;
+                en[u] = k0 + (u + FU) * TPA < n ? ld_stream(rowp + u * rstep) : (unsigned)s;
             }
             int4 pj[FU];
             float2 fmj[FU];
