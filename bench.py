@@ -414,8 +414,10 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "e2e": e2e,
         # per step: k_decide, k_density, k_force, and k_morse_mixed (mixed) or k_verlet1 (FP64);
-        # per list build 14 kernels, and in mixed precision k_verlet1; one k_reduce
-        "gpu_launches": int(4 * args.steps + (15 if args.precision == "mixed" else 14) * rebuilds + 1),
+        # per list build 14 kernels, and in mixed precision k_verlet1; one k_reduce; the
+        # checkpoint md_step keeps for a list overflow (calls of >= 16 steps: k_ckpt_save)
+        "gpu_launches": int(4 * args.steps + (15 if args.precision == "mixed" else 14) * rebuilds + 1
+                            + (1 if args.steps >= 16 else 0)),
         "value_incl_c": (n_cr + n_c) * ws * args.steps / (t_max * 1e-3),
         "value_amortised": value_amortised,
         "step_roofline": step_roofline,
