@@ -331,24 +331,34 @@ def run_gpu(args):
         hv = torch.empty((n0, 3), dtype=torch.float64, pin_memory=True).numpy()
         x, v, z, st = sim.state(0)
         hx[:] = x; hv[:] = v
-        for _ in range(2):
+
+        def exchange():
+            # H2D of this step's inputs, one step, D2H of its result and energies (in place)
+            _, _, en = md.md_step_io(sim.h, 0, hx, hv, z, st, 1, hx, hv)
+            return en["z_indenter"], en["step"]
+
+        def in_turn():
             sim.set_state(0, hx, hv, z, st)
             sim.step(1)
             md.md_get_state(sim.h, 0, n0, hx, hv)
-            z = sim.energy(0)["z_indenter"]; st += 1
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            sim.set_state(0, hx, hv, z, st)        # H2D of this step's inputs
-            sim.step(1)
-            md.md_get_state(sim.h, 0, n0, hx, hv)  # D2H of the step's result
             en = sim.energy(0)
-            z = en["z_indenter"]; st += 1
-        dt_e2e = time.perf_counter() - t0
-        e2e = {"value": n0 * args.e2e_steps / dt_e2e, "unit": UNIT,
+            return en["z_indenter"], en["step"]
+
+        rates = {}
+        for name, fn in (("in_turn", in_turn), ("step_io", exchange)):
+            for _ in range(2):
+                z, st = fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                z, st = fn()
+            rates[name] = n0 * args.e2e_steps / (time.perf_counter() - t0)
+        e2e = {"value": rates["step_io"], "unit": UNIT,
                "h2d_bytes_per_step": int(hx.nbytes + hv.nbytes + 16),
                "d2h_bytes_per_step": int(hx.nbytes + hv.nbytes + md.C.sizeof(md.md_energy)),
-               "path": "md_set_state (H2D) + md_step(1) + md_get_state (D2H) + md_get_energy, replica 0"}
+               "path": "md_step_io(replica 0, n = 1): H2D of x, v; one step; D2H of x, v, energies",
+               "value_calls_in_turn": rates["in_turn"],
+               "calls_in_turn": "md_set_state + md_step(1) + md_get_state + md_get_energy"}
 
     # ---- variants on the same GPU: plain FP64 form on this workload, batched replicas
     variants = {}
@@ -583,7 +593,7 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=50)
     ap.add_argument("--rate-steps", type=int, default=400,
                     help="untimed steps over which the list-rebuild rate is counted")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--fp64-steps", type=int, default=40)
     ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -236,6 +236,20 @@ int md_get_state(md_t *h, int32_t replica, double *x3n, double *v3n, double *z_i
  * MD_ERR_NBR_OVERFLOW, MD_ERR_CUDA. */
 int md_set_state(md_t *h, int32_t replica, const double *x3n, const double *v3n, double z_ind, int64_t step);
 
+/* One exchange of a replica's state with the host around n >= 1 time steps (Fig. 5's time
+ * loop driven from outside, e.g. by a serving layer that holds the state between calls):
+ * md_set_state(replica, x3n, v3n, z_ind, step), md_step(n), then the replica's positions
+ * and velocities into x_out, v_out (3*n_cr doubles each, caller order; they may be x3n and
+ * v3n) and its energies into *e_out -- the results of those calls made in turn (the same
+ * values bit for bit).  The positions after the last step's Task 3 go back to the host
+ * while its density and force passes run (one synchronisation at the end).  Host arrays
+ * in page-locked memory copy fastest; all pointers are required.  A list overflow inside
+ * the steps is recovered as md_step recovers it (the same checkpoint policy; the redo runs
+ * as md_step); handles without graphs make the calls in turn.  Errors: those of
+ * md_set_state and md_step; MD_ERR_ARG for a NULL pointer or n < 1. */
+int md_step_io(md_t *h, int32_t replica, const double *x3n, const double *v3n, double z_ind, int64_t step,
+               int64_t n, double *x_out, double *v_out, md_energy *e_out);
+
 /* Per-atom virial of one replica at the current state, 6 doubles per atom in caller order
  * (xx, yy, zz, xy, xz, yz; eV): the potential part of the per-atom stress times volume
  * (Task 4 can give stresses, Sec. 2.1; their histories are derived along a run, Sec. 3.1).

@@ -122,6 +122,11 @@ struct md_handle {
     // execFE mixed precision's single step that runs k_verlet1, without / with the energies
     cudaGraphExec_t exec1 = nullptr, execU = nullptr, execE = nullptr;
     cudaGraphExec_t execF = nullptr, execFE = nullptr;
+    // md_step_io's last step (captured on first use): execE / execFE with an external event,
+    // xready, recorded once the step's Task 3 has made x(t + dt); [0] after a step or in FP64,
+    // [1] mixed precision's step that runs k_verlet1
+    cudaGraphExec_t execIO[2] = {nullptr, nullptr};
+    cudaEvent_t xready = nullptr;
     bool drift = false;   // mixed: the last force kernel made the next step's Task 3 (mirrors drift_ok)
     HostPin *hp = nullptr;
     int unroll = 1;
@@ -298,7 +303,9 @@ void destroy_graphs(md_t *h)
     if (h->execE) cudaGraphExecDestroy(h->execE);
     if (h->execF) cudaGraphExecDestroy(h->execF);
     if (h->execFE) cudaGraphExecDestroy(h->execFE);
-    h->exec1 = h->execU = h->execE = h->execF = h->execFE = nullptr;
+    for (auto &e : h->execIO)
+        if (e) cudaGraphExecDestroy(e);
+    h->exec1 = h->execU = h->execE = h->execF = h->execFE = h->execIO[0] = h->execIO[1] = nullptr;
 }
 
 // One graph of `nsteps` whole time steps: per step k_decide -> IF(rebuild) [list build] ->
@@ -307,8 +314,10 @@ void destroy_graphs(md_t *h)
 // runs only after a rebuild (inside the IF), except in a first step with first_full set
 // (after md_init, md_set_state, ...).  The energy sums (k_reduce) run once after the last
 // step of an md_step call; with last_energy the graph's last force kernel writes the
-// partials they add.
-int capture(md_t *h, int nsteps, bool first_full, bool last_energy, cudaGraphExec_t *out)
+// partials they add.  xev: recorded (an external event node) in every step once x(t + dt)
+// is final, after Task 3 and any list build.
+int capture(md_t *h, int nsteps, bool first_full, bool last_energy, cudaGraphExec_t *out,
+            cudaEvent_t xev = nullptr)
 {
     cudaGraph_t g = nullptr;
     CU(cudaGraphCreate(&g, 0));
@@ -343,6 +352,7 @@ int capture(md_t *h, int nsteps, bool first_full, bool last_energy, cudaGraphExe
         CU(cudaStreamEndCapture(h->cap, &body));
         CU(cudaStreamBeginCaptureToGraph(h->cap, g, &cn, nullptr, 1, mode));
         if (dm == DEC_FULL) CU(launch_verlet1(h->a, h->cap));
+        if (xev) CU(cudaEventRecordWithFlags(xev, h->cap, cudaEventRecordExternal));
         if (h->a.mixed) {   // the Morse sums need only this step's positions: beside k_density
             CU(cudaEventRecord(h->fork, h->cap));
             CU(cudaStreamWaitEvent(h->cap2, h->fork, 0));
@@ -443,6 +453,7 @@ void md_free(md_t *h)
     if (h->xfer) { cudaStreamSynchronize(h->xfer); cudaStreamDestroy(h->xfer); }
     if (h->xev0) cudaEventDestroy(h->xev0);
     if (h->xev1) cudaEventDestroy(h->xev1);
+    if (h->xready) cudaEventDestroy(h->xready);
     if (h->hp) cudaFreeHost(h->hp);
     delete h;
 }
@@ -768,6 +779,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     CUI(cudaStreamCreateWithFlags(&h->xfer, cudaStreamNonBlocking));
     CUI(cudaEventCreateWithFlags(&h->xev0, cudaEventDisableTiming));
     CUI(cudaEventCreateWithFlags(&h->xev1, cudaEventDisableTiming));
+    CUI(cudaEventCreateWithFlags(&h->xready, cudaEventDisableTiming));
     CUI(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
     CUI(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
     CUI(cudaHostAlloc((void **)&h->hp, sizeof(HostPin), cudaHostAllocDefault));
@@ -865,21 +877,23 @@ static int restore_checkpoint(md_t *h, const DevStatus &st)
     return build_graphs(h);
 }
 
-static int run_steps(md_t *h, int64_t n)
+// io_last (graphs only): the last step is md_step_io's graph, which records h->xready once
+// that step's positions are final
+static int run_steps(md_t *h, int64_t n, bool io_last = false)
 {
     int rc;
     if (h->opt.use_graph && h->exec1 && n > 0) {
         // steps 0 .. n-2 without the energies, step n-1 with them (k_reduce follows)
         int64_t k = 0;
         if (h->a.mixed && !h->drift) {
-            CU(cudaGraphLaunch(n == 1 ? h->execFE : h->execF, h->stream));
+            CU(cudaGraphLaunch(n == 1 ? (io_last ? h->execIO[1] : h->execFE) : h->execF, h->stream));
             k = 1;
         }
         h->drift = h->a.mixed != 0;
         if (h->execU)
             for (; k + h->unroll <= n - 1; k += h->unroll) CU(cudaGraphLaunch(h->execU, h->stream));
         for (; k < n - 1; ++k) CU(cudaGraphLaunch(h->exec1, h->stream));
-        if (k < n) CU(cudaGraphLaunch(h->execE, h->stream));
+        if (k < n) CU(cudaGraphLaunch(io_last ? h->execIO[0] : h->execE, h->stream));
     } else {
         for (int64_t k = 0; k < n; ++k)
             if ((rc = step_direct(h, nullptr, nullptr, k == n - 1))) return rc;
@@ -889,6 +903,13 @@ static int run_steps(md_t *h, int64_t n)
         h->energies_valid = true;
     }
     return MD_OK;
+}
+
+// the last list build filled more than 3/4 of a capacity
+static bool near_capacity(const md_t *h)
+{
+    return 4 * (int64_t)h->last_max_cnt > 3 * (int64_t)h->a.kmax ||
+           4 * (int64_t)h->last_max_cntc > 3 * (int64_t)h->a.kcmax;
 }
 
 int md_step(md_t *h, int64_t n)
@@ -901,9 +922,7 @@ int md_step(md_t *h, int64_t n)
         if ((rc = clear_err(h))) return rc;
         // a copy to come back to if a list build inside the call overflows: for calls long
         // enough to amortise it, or when the last build filled more than 3/4 of a capacity
-        const bool near = 4 * (int64_t)h->last_max_cnt > 3 * (int64_t)h->a.kmax ||
-                          4 * (int64_t)h->last_max_cntc > 3 * (int64_t)h->a.kcmax;
-        const bool ck = n > 0 && attempt < 8 && (n >= 16 || near);
+        const bool ck = n > 0 && attempt < 8 && (n >= 16 || near_capacity(h));
         if (ck && (rc = save_checkpoint(h))) return rc;
         if ((rc = run_steps(h, n))) return rc;
         DevStatus st{};
@@ -953,6 +972,8 @@ int md_step_profiled(md_t *h, int64_t n, md_phase_times *out)
     return status_to_code(h, st);
 }
 
+static void fill_energy(const md_t *h, int32_t r, md_energy *out);
+
 int md_get_energy(md_t *h, int32_t r, md_energy *out)
 {
     int rc = check_replica(h, r);
@@ -966,6 +987,13 @@ int md_get_energy(md_t *h, int32_t r, md_energy *out)
     CU(cudaMemcpyAsync(&h->hp->rs, h->a.rs + r, sizeof(RepState), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaMemcpyAsync(&h->hp->st, h->a.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
+    fill_energy(h, r, out);
+    return MD_OK;
+}
+
+// md_energy of replica r from the sums, replica state and status read into pinned memory
+static void fill_energy(const md_t *h, int32_t r, md_energy *out)
+{
     const RepEnergy E = h->hp->E;
     const RepState rs = h->hp->rs;
     const DevStatus st = h->hp->st;
@@ -980,19 +1008,21 @@ int md_get_energy(md_t *h, int32_t r, md_energy *out)
     out->depth = R.n_c > 0 ? R.z_surface0 - (R.zc_min0 + rs.z_ind) : 0.0;
     out->step = st.step;
     out->rebuilds = st.rebuilds;
-    return MD_OK;
 }
 
 // queue the gather of one per-atom array of replica r into caller order (stage half `half`
-// of the staging buffer) and its copy to out3n; the caller synchronises
-static int fetch_async(md_t *h, int32_t r, const double *s0, const double *s1, double *out3n, int half)
+// of the staging buffer) and its copy to out3n, on stream s (default: the handle's); the
+// caller synchronises
+static int fetch_async(md_t *h, int32_t r, const double *s0, const double *s1, double *out3n, int half,
+                       cudaStream_t s = nullptr)
 {
     const RepDev &R = h->rep[r];
     int n = R.n_atoms;
+    if (!s) s = h->stream;
     double *stage = h->stage + 3 * (size_t)n * half;
-    k_state_out<<<(n + 255) / 256, 256, 0, h->stream>>>(s0, s1, h->a.st, stage, h->a.orig, R.slot_off, n, h->a.S);
+    k_state_out<<<(n + 255) / 256, 256, 0, s>>>(s0, s1, h->a.st, stage, h->a.orig, R.slot_off, n, h->a.S);
     CU(cudaGetLastError());
-    CU(cudaMemcpyAsync(out3n, stage, 3 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(out3n, stage, 3 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
     return MD_OK;
 }
 
@@ -1096,6 +1126,54 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     if ((rc2 = read_status(h, &st))) return rc2;
     if ((rc2 = status_to_code(h, st))) return rc2;
     h->forces_valid = true;
+    return MD_OK;
+}
+
+int md_step_io(md_t *h, int32_t r, const double *x3n, const double *v3n, double z_ind, int64_t step, int64_t n,
+               double *x_out, double *v_out, md_energy *e_out)
+{
+    int rc = check_replica(h, r);
+    if (rc) return rc;
+    if (!x3n || !v3n || !x_out || !v_out || !e_out) return fail(h, MD_ERR_ARG, "md_step_io: null argument");
+    if (n < 1) return fail(h, MD_ERR_ARG, "md_step_io: n < 1");
+    if ((rc = md_set_state(h, r, x3n, v3n, z_ind, step))) return rc;
+    if ((rc = ensure_forces(h))) return rc;
+    // direct launches: the calls in turn
+    if (!h->opt.use_graph || !h->exec1) {
+        if ((rc = md_step(h, n))) return rc;
+        if ((rc = md_get_state(h, r, x_out, v_out, nullptr, nullptr))) return rc;
+        return md_get_energy(h, r, e_out);
+    }
+    const int w = (n == 1 && h->a.mixed && !h->drift) ? 1 : 0;
+    if (!h->execIO[w] && (rc = capture(h, 1, w == 1, true, &h->execIO[w], h->xready))) return rc;
+    if ((rc = clear_err(h))) return rc;
+    // md_step's checkpoint policy; after an overflowing build the checkpoint is restored and
+    // md_step runs the n steps with its recovery
+    const bool ck = n >= 16 || near_capacity(h);
+    if (ck && (rc = save_checkpoint(h))) return rc;
+    if ((rc = run_steps(h, n, true))) return rc;
+    // x(t + n dt) is final once the last step's Task 3 (and list build) is done: its gather
+    // and copy run on the transfer stream beside that step's density and force passes
+    CU(cudaStreamWaitEvent(h->xfer, h->xready, 0));
+    if ((rc = fetch_async(h, r, h->a.xs[0], h->a.xs[1], x_out, 0, h->xfer))) return rc;
+    // v(t + n dt) and the sums after the force pass and k_reduce (queued by run_steps)
+    if ((rc = fetch_async(h, r, h->a.v, h->a.v, v_out, 1))) return rc;
+    CU(cudaMemcpyAsync(&h->hp->E, h->a.en + r, sizeof(RepEnergy), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&h->hp->rs, h->a.rs + r, sizeof(RepState), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&h->hp->st, h->a.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->xfer));
+    CU(cudaStreamSynchronize(h->stream));
+    const DevStatus st = h->hp->st;
+    h->last_max_cnt = st.max_cnt;
+    h->last_max_cntc = st.max_cntc;
+    if (ck && (st.err & (MDE_OVERFLOW | MDE_COVERFLOW))) {
+        if ((rc = restore_checkpoint(h, st))) return rc;
+        if ((rc = md_step(h, n))) return rc;
+        if ((rc = md_get_state(h, r, x_out, v_out, nullptr, nullptr))) return rc;
+        return md_get_energy(h, r, e_out);
+    }
+    if ((rc = status_to_code(h, st))) return rc;
+    fill_energy(h, r, e_out);
     return MD_OK;
 }
 

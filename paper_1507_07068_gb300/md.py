@@ -80,7 +80,7 @@ _lib = None
 EXPORTS = ["md_init", "md_build_neighbors", "md_compute_forces", "md_step", "md_step_profiled",
            "md_get_energy", "md_get_forces", "md_get_indenter_load", "md_get_state", "md_set_state",
            "md_get_neighbors", "md_get_info", "md_last_error", "md_free", "md_version", "md_forces_small",
-           "md_set_indenter_velocity", "md_get_virial", "md_probe_fp64_fma", "md_check_lists"]
+           "md_set_indenter_velocity", "md_get_virial", "md_probe_fp64_fma", "md_check_lists", "md_step_io"]
 
 
 def lib(build: bool = True):
@@ -104,6 +104,7 @@ def lib(build: bool = True):
     L.md_get_indenter_load.argtypes = [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.md_get_state.argtypes = [vp, C.c_int32, vp, vp, vp, vp]
     L.md_set_state.argtypes = [vp, C.c_int32, vp, vp, C.c_double, C.c_int64]
+    L.md_step_io.argtypes = [vp, C.c_int32, vp, vp, C.c_double, C.c_int64, C.c_int64, vp, vp, C.POINTER(md_energy)]
     L.md_set_indenter_velocity.argtypes = [vp, C.c_int32, C.c_double]
     L.md_get_virial.argtypes = [vp, C.c_int32, vp]
     L.md_probe_fp64_fma.argtypes = [vp, vp]
@@ -219,6 +220,21 @@ def md_get_state(h, replica: int, n_cr: int, x: Optional[np.ndarray] = None, v: 
 
 def md_set_state(h, replica: int, x: Optional[np.ndarray], v: Optional[np.ndarray], z_ind: float, step: int):
     _check(h, lib().md_set_state(h, int(replica), _ptr(x), _ptr(v), float(z_ind), int(step)))
+
+
+def md_step_io(h, replica: int, x: np.ndarray, v: np.ndarray, z_ind: float, step: int, n: int = 1,
+               x_out: Optional[np.ndarray] = None, v_out: Optional[np.ndarray] = None):
+    """md_step_io: set replica's state, advance n steps, read its state back; returns
+    (x_out, v_out, energy dict).  x_out, v_out may be x, v."""
+    x_out = np.empty_like(x) if x_out is None else x_out
+    v_out = np.empty_like(v) if v_out is None else v_out
+    for a in (x, v, x_out, v_out):
+        if a.dtype != np.float64 or not a.flags.c_contiguous or a.shape != x.shape:
+            raise ValueError("md_step_io: C-contiguous float64 arrays of one shape (n, 3)")
+    e = md_energy()
+    _check(h, lib().md_step_io(h, int(replica), _ptr(x), _ptr(v), float(z_ind), int(step), int(n),
+                               _ptr(x_out), _ptr(v_out), C.byref(e)))
+    return x_out, v_out, e.as_dict()
 
 
 def md_get_virial(h, replica: int, n_cr: int, out: Optional[np.ndarray] = None):
@@ -385,6 +401,14 @@ class MD:
         x = None if x is None else np.ascontiguousarray(x, np.float64)
         v = None if v is None else np.ascontiguousarray(v, np.float64)
         md_set_state(self.h, r, x, v, z_ind, step)
+
+    def step_io(self, r: int, x, v, z_ind: float, step: int, n: int = 1, x_out=None, v_out=None):
+        """Set replica r's state, advance every replica n steps, return r's (x, v, energies)."""
+        x = np.ascontiguousarray(x, np.float64)
+        v = np.ascontiguousarray(v, np.float64)
+        if x.shape != (self.n[r], 3):
+            raise ValueError(f"step_io: x must be ({self.n[r]}, 3)")
+        return md_step_io(self.h, r, x, v, z_ind, step, n, x_out, v_out)
 
     def virial(self, r: int = 0):
         """Per-atom virial (n, 6: xx, yy, zz, xy, xz, yz; eV) of replica r."""
