@@ -203,8 +203,8 @@ int md_compute_forces(md_t *h);
  * replica to the state the call started from, rebuilds the lists there and runs the n
  * steps again (the rebuild count then includes that extra build, and the sums over pairs
  * follow the new lists' order).  For this it keeps a device copy of positions, velocities
- * and indenter state when n >= 16 or when the last build filled more than 3/4 of a
- * capacity; a call without that copy, and the other device-side errors (lost atom, skin
+ * and indenter state when n >= 16 or when the longest list of the last build came within
+ * 1/8 of its capacity (8 entries at least); a call without that copy, and the other device-side errors (lost atom, skin
  * violation), return the error when the call ends, and the state is then not meaningful. */
 int md_step(md_t *h, int64_t n);
 

@@ -905,11 +905,13 @@ static int run_steps(md_t *h, int64_t n, bool io_last = false)
     return MD_OK;
 }
 
-// the last list build filled more than 3/4 of a capacity
+// the longest list of the last build came within 1/8 of its capacity (8 entries at least):
+// between builds the longest lists of a film grow by a few entries (thermal motion, an
+// indenter's compression), so a build inside a short call overflows only from there
 static bool near_capacity(const md_t *h)
 {
-    return 4 * (int64_t)h->last_max_cnt > 3 * (int64_t)h->a.kmax ||
-           4 * (int64_t)h->last_max_cntc > 3 * (int64_t)h->a.kcmax;
+    const auto near = [](int64_t m, int64_t k) { return m + std::max<int64_t>(8, k / 8) > k; };
+    return near(h->last_max_cnt, h->a.kmax) || near(h->last_max_cntc, h->a.kcmax);
 }
 
 int md_step(md_t *h, int64_t n)
@@ -921,7 +923,7 @@ int md_step(md_t *h, int64_t n)
         if (rc) return rc;
         if ((rc = clear_err(h))) return rc;
         // a copy to come back to if a list build inside the call overflows: for calls long
-        // enough to amortise it, or when the last build filled more than 3/4 of a capacity
+        // enough to amortise it, or when the last build came near a capacity
         const bool ck = n > 0 && attempt < 8 && (n >= 16 || near_capacity(h));
         if (ck && (rc = save_checkpoint(h))) return rc;
         if ((rc = run_steps(h, n))) return rc;
