@@ -234,6 +234,8 @@ struct DevArgs {
     double *part;
     double *rsum;                        // k_reduce scratch: [n_rep][MD_RED_CHUNKS][6] chunk sums
     int32_t max_blocks;
+    int32_t max_rep_slots;               // slots of the largest replica (k_reduce's chunking)
+    int32_t n_sm;                        // SMs of the device (grids of the one-warp-per-atom kernels)
 };
 
 // Cell order: 2x2x2 bricks of cells, bricks in row-major order and the eight cells of a

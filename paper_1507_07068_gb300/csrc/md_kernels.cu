@@ -35,7 +35,6 @@
 #include "md_internal.h"
 
 #define MD_UNROLL 4   // neighbour entries per lane whose loads are issued together
-#define MD_NEAR_BLOCKS 304   // CTAs (8 warps each) of the one-warp-per-atom Cr-C kernels
 #define MD_SORT_MAX 2048     // largest cell k_cellsort orders
 
 // ============================================================================ host:
@@ -876,21 +875,30 @@ __global__ void __launch_bounds__(256) k_nbrc_near(DevArgs a)
         const double *x = a.xs[buf_cur(a)];
         const double xi[3] = {x[s], x[S + s], x[2 * S + s]};
         if (!(isfinite(xi[0]) && isfinite(xi[1]) && isfinite(xi[2]))) continue;   // reported by k_bin
+        // the cells within reach along axis k = lane (lanes 0-2; FP64, with its divisions, is
+        // slow on this part: computed once per axis, not by every lane), then broadcast
+        unsigned long long mk = 0ull;
+        float qk = 0.0f;
+        if (lane < 3) {
+            const int k = lane;
+            double q = (k == 0 ? xi[0] : k == 1 ? xi[1] : xi[2] - z_ind);
+            const double ctr = R.cg_lo[k] + 0.5 * R.cg_n[k] * R.cg_w[k];
+            if (R.per[k]) {
+                q = ctr + mi64(q - ctr, 1, R.L[k]);
+                const double q2 = q > ctr ? q - R.L[k] : q + R.L[k];
+                mk = cell_bits(q2, reach, R.cg_lo[k], R.cg_w[k], R.cg_n[k]);
+            }
+            mk |= cell_bits(q, reach, R.cg_lo[k], R.cg_w[k], R.cg_n[k]);
+            qk = (float)(q - R.cg_lo[k]);
+        }
         unsigned long long mask[3];
         float q32[3];
         bool none = false;
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-            double q = xi[k] - (k == 2 ? z_ind : 0.0);
-            double ctr = R.cg_lo[k] + 0.5 * R.cg_n[k] * R.cg_w[k];
-            mask[k] = 0ull;
-            if (R.per[k]) {
-                q = ctr + mi64(q - ctr, 1, R.L[k]);
-                double q2 = q > ctr ? q - R.L[k] : q + R.L[k];
-                mask[k] = cell_bits(q2, reach, R.cg_lo[k], R.cg_w[k], R.cg_n[k]);
-            }
-            mask[k] |= cell_bits(q, reach, R.cg_lo[k], R.cg_w[k], R.cg_n[k]);
+            mask[k] = __shfl_sync(0xffffffffu, mk, k);
+            q32[k] = __shfl_sync(0xffffffffu, qk, k);
             none |= !mask[k];
-            q32[k] = (float)(q - R.cg_lo[k]);
         }
         if (none) continue;
         // FP32 prefilter (indenter frame, positions below ~100 A: error < 1e-4 A^2 on y^2);
@@ -2011,8 +2019,8 @@ __global__ void __launch_bounds__(256) k_virial_fp64(DevArgs a, PotDev P)
         for (int k = 0; k < 6; ++k) a.vir[k * S + s] = w[k];
 }
 
-// per-replica sums of the CTA partials in a fixed order.  MD_RED_CHUNKS CTAs per replica
-// each sum a contiguous run of the partials (thread t adds blocks t, t + B, ... of all six
+// per-replica sums of the CTA partials in a fixed order.  gridDim.x (<= MD_RED_CHUNKS, fixed
+// for a handle) CTAs per replica each sum a contiguous run of the partials (thread t adds blocks t, t + B, ... of all six
 // terms together; the lanes of a warp by a fixed shuffle tree; thread 0 the warp sums in
 // warp order) into rsum; the CTA that finishes last (a counter per replica, after a fence)
 // adds the chunk sums in chunk order and resets the counter.  Which CTA finishes last does
@@ -2079,6 +2087,17 @@ __global__ void __launch_bounds__(64) k_reduce(DevArgs a, int atoms_per_block)
 
 inline unsigned nblk(long n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// the grid of the one-warp-per-atom Cr-C kernels (their atom count is known only on the
+// device): every CTA the SMs can hold at once, so that the warps' latency-bound walks over
+// the indenter's cells overlap (2 CTAs per SM took 1.07 ms per list build on 256 replicas)
+template <class K>
+static unsigned full_grid(const DevArgs &a, K kernel, int block)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, 0) != cudaSuccess || occ < 1) occ = 1;
+    return (unsigned)(occ * std::max(1, a.n_sm));
+}
+
 }  // namespace
 
 // ============================================================================ launchers
@@ -2106,7 +2125,7 @@ cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s)
     k_copyback<<<nblk(a.S, B), B, 0, s>>>(a);
     k_nbr<<<nblk(a.S, 128), 128, 0, s>>>(a);
     k_nbrc<<<nblk(a.S, 128), 128, 0, s>>>(a);
-    k_nbrc_near<<<MD_NEAR_BLOCKS, 256, 0, s>>>(a);
+    k_nbrc_near<<<full_grid(a, k_nbrc_near, 256), 256, 0, s>>>(a);
     k_build_done<<<1, 256, 0, s>>>(a);
     if (a.debug) {
         k_zero_chk<<<1, 32, 0, s>>>(a);
@@ -2192,7 +2211,7 @@ cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c
 
 cudaError_t launch_morse(const DevArgs &a, const PotDev &p, cudaStream_t s)
 {
-    if (a.mixed) k_morse_mixed<<<MD_NEAR_BLOCKS, 256, 0, s>>>(a, p);
+    if (a.mixed) k_morse_mixed<<<full_grid(a, k_morse_mixed, 256), 256, 0, s>>>(a, p);
     return cudaGetLastError();
 }
 
@@ -2205,7 +2224,7 @@ cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, 
 cudaError_t launch_force_split(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int energies,
                                int with_morse, cudaStream_t s)
 {
-    if (with_morse && a.mixed) k_morse_mixed<<<MD_NEAR_BLOCKS, 256, 0, s>>>(a, p);
+    if (with_morse && a.mixed) k_morse_mixed<<<full_grid(a, k_morse_mixed, 256), 256, 0, s>>>(a, p);
     switch (c.tpa) {
     case 1: force_t<1>(a, p, c.block, integrate, energies, s); break;
     case 2: force_t<2>(a, p, c.block, integrate, energies, s); break;
@@ -2240,7 +2259,12 @@ cudaError_t launch_virial(const DevArgs &a, const PotDev &p, const LaunchCfg &c,
 
 cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
-    k_reduce<<<dim3(MD_RED_CHUNKS, a.n_rep), 64, 0, s>>>(a, c.block / c.tpa);
+    // chunks per replica: one per ~32 CTA partials of the largest replica (1 .. MD_RED_CHUNKS):
+    // 256 small replicas would otherwise launch 32 768 CTAs with a partial or none each
+    const int apb = c.block / c.tpa;
+    const int parts = (a.max_rep_slots + apb - 1) / apb + 1;
+    const int nch = std::min(MD_RED_CHUNKS, std::max(1, (parts + 31) / 32));
+    k_reduce<<<dim3(nch, a.n_rep), 64, 0, s>>>(a, apb);
     return cudaGetLastError();
 }
 
