@@ -107,7 +107,7 @@ struct md_handle {
     md_options opt{};
     md_params pot_h{};
     PotDev pot{};
-    LaunchCfg cfg{1, 128};
+    LaunchCfg cfg{1, 128, 0};
     DevArgs a{};
     std::vector<RepDev> rep;
     std::vector<int32_t> c_orig;          // indenter slot -> caller indenter id (within replica)
@@ -544,7 +544,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
         R.slot_off = (int32_t)slots;
         R.n_atoms = y.n_cr;
         R.n_slots = (y.n_cr + MD_TILE - 1) / MD_TILE * MD_TILE;
-        h->a.max_rep_slots = std::max(h->a.max_rep_slots, R.n_slots);
+        h->cfg.max_rep_slots = std::max(h->cfg.max_rep_slots, R.n_slots);
         R.real_off = (int32_t)real;
         slots += R.n_slots;
         real += y.n_cr;
@@ -687,11 +687,6 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     INIT_FAIL(dalloc(h, &a.sfixed, S));
     INIT_FAIL(dalloc(h, &a.part, 6 * (size_t)a.max_blocks));
     INIT_FAIL(dalloc(h, &a.rsum, 6 * (size_t)MD_RED_CHUNKS * n_replicas));
-    {
-        int dev = 0;
-        CUI(cudaGetDevice(&dev));
-        CUI(cudaDeviceGetAttribute(&a.n_sm, cudaDevAttrMultiProcessorCount, dev));
-    }
     double *d_xc0; int32_t *d_ccs, *d_ccc;
     float4 *d_xc32;
     INIT_FAIL(dalloc(h, &d_xc0, 3 * (size_t)(cslots > 0 ? cslots : 1)));

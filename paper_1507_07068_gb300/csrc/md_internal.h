@@ -234,8 +234,6 @@ struct DevArgs {
     double *part;
     double *rsum;                        // k_reduce scratch: [n_rep][MD_RED_CHUNKS][6] chunk sums
     int32_t max_blocks;
-    int32_t max_rep_slots;               // slots of the largest replica (k_reduce's chunking)
-    int32_t n_sm;                        // SMs of the device (grids of the one-warp-per-atom kernels)
 };
 
 // Cell order: 2x2x2 bricks of cells, bricks in row-major order and the eight cells of a
@@ -256,8 +254,9 @@ __host__ __device__ __forceinline__ void key_cell_loc(const RepDev &R, int loc, 
 }
 
 struct LaunchCfg {
-    int32_t tpa;      // threads per atom
-    int32_t block;    // threads per block
+    int32_t tpa;            // threads per atom
+    int32_t block;          // threads per block
+    int32_t max_rep_slots;  // slots of the largest replica (k_reduce's chunks per replica)
 };
 
 // ---- host-side helpers implemented in md_kernels.cu

@@ -819,14 +819,17 @@ __global__ void __launch_bounds__(128) k_nbr(DevArgs a)
 // Along a periodic axis both images of the film atom that can reach the indenter are
 // searched: the cells of the two reach intervals are merged into one bit set per axis
 // (indenter grids have at most 64 cells per axis), so every cell is visited once.
-__device__ __forceinline__ unsigned long long cell_bits(double q, double reach, double lo, double w, int n)
+//
+// The cells (bits) of an n-cell axis within reach r of offset u from the grid's origin
+// (iw = 1 / cell width; r already widened by the caller's margin; bits a..b, b = 63 wraps
+// to the top bit correctly)
+__device__ __forceinline__ unsigned long long cell_bits32(float u, float r, float iw, int n)
 {
-    double tl = floor((q - reach - lo) / w);
-    double th = floor((q + reach - lo) / w);
-    if (!(th >= 0.0) || !(tl <= (double)(n - 1))) return 0ull;
-    int a = tl < 0.0 ? 0 : (int)tl;
-    int b = th > (double)(n - 1) ? n - 1 : (int)th;
-    return (2ull << b) - (1ull << a);   // bits a..b (b = 63 wraps to the top bit correctly)
+    const float tl = floorf((u - r) * iw), th = floorf((u + r) * iw);
+    if (!(th >= 0.0f) || !(tl <= (float)(n - 1))) return 0ull;
+    const int a = tl < 0.0f ? 0 : (int)tl;
+    const int b = th > (float)(n - 1) ? n - 1 : (int)th;
+    return (2ull << b) - (1ull << a);
 }
 
 __global__ void __launch_bounds__(128) k_nbrc(DevArgs a)
@@ -875,20 +878,25 @@ __global__ void __launch_bounds__(256) k_nbrc_near(DevArgs a)
         const double *x = a.xs[buf_cur(a)];
         const double xi[3] = {x[s], x[S + s], x[2 * S + s]};
         if (!(isfinite(xi[0]) && isfinite(xi[1]) && isfinite(xi[2]))) continue;   // reported by k_bin
-        // the cells within reach along axis k = lane (lanes 0-2; FP64, with its divisions, is
-        // slow on this part: computed once per axis, not by every lane), then broadcast
+        // the cells within reach along axis k = lane (lanes 0-2: the FP64 pipe of this part
+        // takes a warp instruction whatever its active lanes, so once per axis), then
+        // broadcast.  The image choice and the offsets from the grid's origin in FP64; the
+        // cell range in FP32, widened by 0.01 A (FP32 errors here stay below 1e-4 A), so
+        // that it holds every cell of the exact range: a wider range only adds candidates
+        // the exact test rejects
         unsigned long long mk = 0ull;
         float qk = 0.0f;
         if (lane < 3) {
             const int k = lane;
             double q = (k == 0 ? xi[0] : k == 1 ? xi[1] : xi[2] - z_ind);
             const double ctr = R.cg_lo[k] + 0.5 * R.cg_n[k] * R.cg_w[k];
+            const float rf = (float)reach + 0.01f, iwf = 1.0f / (float)R.cg_w[k];
             if (R.per[k]) {
                 q = ctr + mi64(q - ctr, 1, R.L[k]);
                 const double q2 = q > ctr ? q - R.L[k] : q + R.L[k];
-                mk = cell_bits(q2, reach, R.cg_lo[k], R.cg_w[k], R.cg_n[k]);
+                mk = cell_bits32((float)(q2 - R.cg_lo[k]), rf, iwf, R.cg_n[k]);
             }
-            mk |= cell_bits(q, reach, R.cg_lo[k], R.cg_w[k], R.cg_n[k]);
+            mk |= cell_bits32((float)(q - R.cg_lo[k]), rf, iwf, R.cg_n[k]);
             qk = (float)(q - R.cg_lo[k]);
         }
         unsigned long long mask[3];
@@ -2087,16 +2095,27 @@ __global__ void __launch_bounds__(64) k_reduce(DevArgs a, int atoms_per_block)
 
 inline unsigned nblk(long n, int b) { return (unsigned)((n + b - 1) / b); }
 
-// the grid of the one-warp-per-atom Cr-C kernels (their atom count is known only on the
-// device): every CTA the SMs can hold at once, so that the warps' latency-bound walks over
-// the indenter's cells overlap (2 CTAs per SM took 1.07 ms per list build on 256 replicas)
+static int device_sms()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        n = 0;
+    return std::max(1, n);
+}
+
+// grids of the one-warp-per-atom Cr-C kernels (their atom count is known only on the
+// device).  k_nbrc_near: every CTA the SMs hold at once; k_morse_mixed: 2 CTAs per SM, as
+// it runs beside k_density in the step graphs (a full grid there cost the batch of 256
+// replicas 2 % of its step)
 template <class K>
-static unsigned full_grid(const DevArgs &a, K kernel, int block)
+static unsigned full_grid(K kernel, int block)
 {
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, 0) != cudaSuccess || occ < 1) occ = 1;
-    return (unsigned)(occ * std::max(1, a.n_sm));
+    return (unsigned)(occ * device_sms());
 }
+
+static unsigned morse_grid() { return (unsigned)(2 * device_sms()); }
 
 }  // namespace
 
@@ -2125,7 +2144,7 @@ cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s)
     k_copyback<<<nblk(a.S, B), B, 0, s>>>(a);
     k_nbr<<<nblk(a.S, 128), 128, 0, s>>>(a);
     k_nbrc<<<nblk(a.S, 128), 128, 0, s>>>(a);
-    k_nbrc_near<<<full_grid(a, k_nbrc_near, 256), 256, 0, s>>>(a);
+    k_nbrc_near<<<full_grid(k_nbrc_near, 256), 256, 0, s>>>(a);
     k_build_done<<<1, 256, 0, s>>>(a);
     if (a.debug) {
         k_zero_chk<<<1, 32, 0, s>>>(a);
@@ -2211,7 +2230,7 @@ cudaError_t launch_density(const DevArgs &a, const PotDev &p, const LaunchCfg &c
 
 cudaError_t launch_morse(const DevArgs &a, const PotDev &p, cudaStream_t s)
 {
-    if (a.mixed) k_morse_mixed<<<full_grid(a, k_morse_mixed, 256), 256, 0, s>>>(a, p);
+    if (a.mixed) k_morse_mixed<<<morse_grid(), 256, 0, s>>>(a, p);
     return cudaGetLastError();
 }
 
@@ -2224,7 +2243,7 @@ cudaError_t launch_force(const DevArgs &a, const PotDev &p, const LaunchCfg &c, 
 cudaError_t launch_force_split(const DevArgs &a, const PotDev &p, const LaunchCfg &c, int integrate, int energies,
                                int with_morse, cudaStream_t s)
 {
-    if (with_morse && a.mixed) k_morse_mixed<<<full_grid(a, k_morse_mixed, 256), 256, 0, s>>>(a, p);
+    if (with_morse && a.mixed) k_morse_mixed<<<morse_grid(), 256, 0, s>>>(a, p);
     switch (c.tpa) {
     case 1: force_t<1>(a, p, c.block, integrate, energies, s); break;
     case 2: force_t<2>(a, p, c.block, integrate, energies, s); break;
@@ -2262,7 +2281,7 @@ cudaError_t launch_reduce(const DevArgs &a, const LaunchCfg &c, cudaStream_t s)
     // chunks per replica: one per ~32 CTA partials of the largest replica (1 .. MD_RED_CHUNKS):
     // 256 small replicas would otherwise launch 32 768 CTAs with a partial or none each
     const int apb = c.block / c.tpa;
-    const int parts = (a.max_rep_slots + apb - 1) / apb + 1;
+    const int parts = (c.max_rep_slots + apb - 1) / apb + 1;
     const int nch = std::min(MD_RED_CHUNKS, std::max(1, (parts + 31) / 32));
     k_reduce<<<dim3(nch, a.n_rep), 64, 0, s>>>(a, apb);
     return cudaGetLastError();
