@@ -228,7 +228,10 @@ int md_get_state(md_t *h, int32_t replica, double *x3n, double *v3n, double *z_i
 /* Replace positions and velocities (caller order; x3n or v3n may be NULL to keep), the
  * indenter displacement and the step count of one replica, then re-evaluate forces at the
  * new state -- unless every position and the indenter displacement are bit for bit those
- * already held, when the forces held stay valid (forces do not depend on velocities) --
+ * already held, when the forces held stay valid (forces do not depend on velocities), and,
+ * in mixed precision with the velocities bit for bit those held too, so does the next
+ * step's Task 3 that the last force evaluation made (the device checks the velocities as
+ * they arrive; the next step reads the result) --
  * (the energy sums of the new state are evaluated when md_get_energy first asks
  * for them; an md_step in between makes its own).  The neighbour lists are kept when the new positions pass the rebuild test of
  * md_step (max |x - x_build| and the indenter's travel since the last build against the

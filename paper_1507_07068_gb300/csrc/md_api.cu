@@ -19,17 +19,30 @@ namespace {
 thread_local std::string g_init_error;
 
 // device-side state transfer between the caller's AoS order and the slot order; the
-// positions live in one of two buffers (d0, d1), chosen by the buffer counter st->ph
+// positions live in one of two buffers (d0, d1), chosen by the buffer counter st->ph.
+// diff (may be NULL) is set when any value differs bit for bit from the one it replaces.
 __global__ void k_state_in(const double *stage, double *d0, double *d1, const DevStatus *st, const int32_t *orig,
-                           int slot_off, int n, size_t S)
+                           int slot_off, int n, size_t S, int32_t *diff)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double *dst = (st->ph & 1) ? d1 : d0;
     int s = slot_off + i;
     int o = orig[s];
+    bool same = true;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) dst[k * S + s] = stage[3 * (size_t)o + k];
+    for (int k = 0; k < 3; ++k) {
+        const double v = stage[3 * (size_t)o + k];
+        same &= __double_as_longlong(v) == __double_as_longlong(dst[k * S + s]);
+        dst[k * S + s] = v;
+    }
+    if (diff && !same) *diff = 1;
+}
+
+// md_set_state: the drift the last force pass made is kept when no velocity changed
+__global__ void k_keep_drift(int32_t *drift_ok, const int32_t *vdiff)
+{
+    *drift_ok = *vdiff == 0 ? 1 : 0;
 }
 
 // md_step's checkpoint (recovery from a list overflow): every replica's positions and
@@ -95,6 +108,7 @@ struct HostPin {
     RepState rs;
     int32_t flag, verlet;
     int32_t need_changed[2];   // md_set_state: DevStatus any_rebuild, changed
+    int32_t one;               // 1, the source of a device flag set from the host
 };
 
 struct md_handle {
@@ -104,6 +118,7 @@ struct md_handle {
     cudaEvent_t fork = nullptr, join = nullptr;
     cudaStream_t xfer = nullptr;         // md_set_state: the velocities' upload beside the list test
     cudaEvent_t xev0 = nullptr, xev1 = nullptr;
+    int32_t *vdiff = nullptr;            // md_set_state: k_state_in's velocity comparison
     md_options opt{};
     md_params pot_h{};
     PotDev pot{};
@@ -312,7 +327,8 @@ void destroy_graphs(md_t *h)
 // k_verlet1 -> k_density (beside k_morse) -> k_force; k_decide sets the step's conditional.
 // In mixed precision the force kernel drifts the positions for the next step, and k_verlet1
 // runs only after a rebuild (inside the IF), except in a first step with first_full set
-// (after md_init, md_set_state, ...).  The energy sums (k_reduce) run once after the last
+// (after md_build_neighbors, md_set_state, ...): there k_decide (DEC_AUTO) sets a second
+// conditional, IF(rebuild or no drift ready) [k_verlet1], from the device's drift flag.  The energy sums (k_reduce) run once after the last
 // step of an md_step call; with last_energy the graph's last force kernel writes the
 // partials they add.  xev: recorded (an external event node) in every step once x(t + dt)
 // is final, after Task 3 and any list build.
@@ -324,12 +340,13 @@ int capture(md_t *h, int nsteps, bool first_full, bool last_energy, cudaGraphExe
     std::vector<cudaGraphNode_t> deps;
     const cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
     for (int k = 0; k < nsteps; ++k) {
-        const int dm = (h->a.mixed && !(first_full && k == 0)) ? DEC_DRIFT : DEC_FULL;
+        const int dm = !h->a.mixed ? DEC_FULL : (first_full && k == 0) ? DEC_AUTO : DEC_DRIFT;
         const int en = last_energy && k == nsteps - 1;
-        cudaGraphConditionalHandle hc;
+        cudaGraphConditionalHandle hc, hv = 0;
         CU(cudaGraphConditionalHandleCreate(&hc, g, 0, cudaGraphCondAssignDefault));
+        if (dm == DEC_AUTO) CU(cudaGraphConditionalHandleCreate(&hv, g, 0, cudaGraphCondAssignDefault));
         CU(cudaStreamBeginCaptureToGraph(h->cap, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), mode));
-        CU(launch_decide(h->a, dm, 1, hc, h->cap));
+        CU(launch_decide(h->a, dm, 1, hc, h->cap, hv));
         cudaStreamCaptureStatus cs;
         const cudaGraphNode_t *d = nullptr;
         size_t nd = 0;
@@ -350,6 +367,22 @@ int capture(md_t *h, int nsteps, bool first_full, bool last_energy, cudaGraphExe
         CU(launch_rebuild(h->a, h->cap));
         if (dm == DEC_DRIFT) CU(launch_verlet1(h->a, h->cap));   // the drift was made before the build
         CU(cudaStreamEndCapture(h->cap, &body));
+        if (dm == DEC_AUTO) {   // IF(rebuild or no drift ready) [k_verlet1]
+            alignas(cudaGraphNodeParams) unsigned char vpbuf[sizeof(cudaGraphNodeParams)];
+            memset(vpbuf, 0, sizeof vpbuf);
+            cudaGraphNodeParams &vp = *reinterpret_cast<cudaGraphNodeParams *>(vpbuf);
+            vp.type = cudaGraphNodeTypeConditional;
+            vp.conditional.handle = hv;
+            vp.conditional.type = cudaGraphCondTypeIf;
+            vp.conditional.size = 1;
+            cudaGraphNode_t cv;
+            CU(cudaGraphAddNode(&cv, g, &cn, nullptr, 1, &vp));
+            cudaGraph_t vbody = vp.conditional.phGraph_out[0];
+            CU(cudaStreamBeginCaptureToGraph(h->cap, vbody, nullptr, nullptr, 0, mode));
+            CU(launch_verlet1(h->a, h->cap));
+            CU(cudaStreamEndCapture(h->cap, &vbody));
+            cn = cv;
+        }
         CU(cudaStreamBeginCaptureToGraph(h->cap, g, &cn, nullptr, 1, mode));
         if (dm == DEC_FULL) CU(launch_verlet1(h->a, h->cap));
         if (xev) CU(cudaEventRecordWithFlags(xev, h->cap, cudaEventRecordExternal));
@@ -396,7 +429,7 @@ int step_direct(md_t *h, cudaEvent_t *ev, bool *rebuilt, bool energies)
 {
     cudaStream_t s = h->stream;
     if (ev) CU(cudaEventRecord(ev[0], s));
-    CU(launch_decide(h->a, h->drift ? DEC_DRIFT : DEC_FULL, 0, 0, s));
+    CU(launch_decide(h->a, h->drift ? DEC_DRIFT : (h->a.mixed ? DEC_AUTO : DEC_FULL), 0, 0, s));
     if (ev) CU(cudaEventRecord(ev[1], s));
     CU(cudaMemcpyAsync(&h->hp->flag, &h->a.st->any_rebuild, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(&h->hp->verlet, &h->a.st->run_verlet, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -696,6 +729,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     INIT_FAIL(dalloc(h, &d_ccc, ccells > 0 ? ccells : 1));
     a.xc0 = d_xc0; a.ccell_start = d_ccs; a.ccell_count = d_ccc;
     INIT_FAIL(dalloc(h, &h->stage, 6 * max_n));
+    INIT_FAIL(dalloc(h, &h->vdiff, 1));
     double *d_cen;
     INIT_FAIL(dalloc(h, &d_cen, ncen));
     a.cen = d_cen;
@@ -785,6 +819,7 @@ int md_init(const md_system *sys, int32_t n_replicas, const md_options *opt, voi
     CUI(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
     CUI(cudaHostAlloc((void **)&h->hp, sizeof(HostPin), cudaHostAllocDefault));
     *h->hp = HostPin{};
+    h->hp->one = 1;
     h->ev.resize(8);
     for (auto &e : h->ev) CUI(cudaEventCreate(&e));
     h->unroll = 8;
@@ -1080,6 +1115,7 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     const RepDev &R = h->rep[r];
     int n = R.n_atoms;
     const bool had_forces = h->forces_valid;
+    const bool had_drift = h->drift;
     h->drift = false;   // k_state_prep voids the drift made from the old state
     if (x3n) CU(cudaMemcpyAsync(h->stage, x3n, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     // The velocities go up on the transfer stream once the positions are up (one copy at a
@@ -1091,8 +1127,9 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
         double *st2 = h->stage + 3 * (size_t)n;
         CU(cudaStreamWaitEvent(h->xfer, h->xev0, 0));
         CU(cudaMemcpyAsync(st2, v3n, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->xfer));
+        CU(cudaMemsetAsync(h->vdiff, 0, sizeof(int32_t), h->xfer));
         k_state_in<<<(n + 255) / 256, 256, 0, h->xfer>>>(st2, h->a.v, h->a.v, h->a.st, h->a.orig, R.slot_off, n,
-                                                         h->a.S);
+                                                         h->a.S, h->vdiff);
         CU(cudaGetLastError());
         CU(cudaEventRecord(h->xev1, h->xfer));
     }
@@ -1114,9 +1151,25 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     }
     if (had_forces && !changed) {
         // the same positions and indenter displacement: the forces of the state hold (they
-        // do not depend on the velocities); the next step makes its own drift from the
-        // velocities now set, and md_get_energy sums the energies anew (the kinetic term)
+        // do not depend on the velocities), and md_get_energy sums the energies anew (the
+        // kinetic term).  With the same velocities too, bit for bit, the next step's Task 3
+        // that the last force pass made (mixed precision) holds as well: it is what
+        // k_verlet1 would make again from the same x, v and F, so it is kept (k_state_prep
+        // voided it; nothing else of it was touched).  The device sets its flag again when
+        // k_state_in found every velocity the same, without a wait here: the host then
+        // does not know, and the next step's graph (DEC_AUTO) reads the flag.  Otherwise
+        // the next step makes its own drift from the velocities now set.
         if (v3n) CU(cudaStreamWaitEvent(h->stream, h->xev1, 0));
+        if (had_drift) {
+            if (v3n) {
+                k_keep_drift<<<1, 1, 0, h->stream>>>(&h->a.st->drift_ok, h->vdiff);
+                CU(cudaGetLastError());
+            } else {
+                CU(cudaMemcpyAsync(&h->a.st->drift_ok, &h->hp->one, sizeof(int32_t), cudaMemcpyHostToDevice,
+                                   h->stream));
+                h->drift = true;
+            }
+        }
         h->forces_valid = true;
         h->energies_valid = false;
         return MD_OK;
@@ -1209,8 +1262,10 @@ int md_set_indenter_velocity(md_t *h, int32_t r, double v_ind)
     h->rep[r].v_ind = v_ind;
     RepDev *d = const_cast<RepDev *>(h->a.rep) + r;
     CU(cudaMemcpyAsync(&d->v_ind, &h->rep[r].v_ind, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    // the drift made for the next step took its displacement threshold from the old path:
+    // void it on the device too (a first step in DEC_AUTO reads the device's flag)
+    CU(cudaMemsetAsync(&h->a.st->drift_ok, 0, sizeof(int32_t), h->stream));
     CU(cudaStreamSynchronize(h->stream));
-    // the drift made for the next step took its displacement threshold from the old path
     h->drift = false;
     return MD_OK;
 }

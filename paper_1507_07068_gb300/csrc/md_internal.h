@@ -43,7 +43,9 @@ enum { MDE_OVERFLOW = 1, MDE_LOST = 2, MDE_SKIN = 4, MDE_COVERFLOW = 8, MDE_SCHE
 // what k_decide is launched for: an explicit list build (no step), a step whose Task 3 the
 // last step's force epilogue made (k_verlet1 runs only if the lists are rebuilt), or a step
 // that runs k_verlet1
-enum { DEC_BUILD = 0, DEC_DRIFT = 1, DEC_FULL = 2 };
+// DEC_AUTO: k_verlet1 runs when the device's drift flag says no drift is ready or the lists
+// are rebuilt (a second graph conditional, set by k_decide)
+enum { DEC_BUILD = 0, DEC_DRIFT = 1, DEC_FULL = 2, DEC_AUTO = 3 };
 // skin of the inner list (A): rebuilt from the Verlet list when an atom has moved more than
 // half of it since the last rebuild
 #define MD_INNER_SKIN 0.1
@@ -263,7 +265,8 @@ struct LaunchCfg {
 int md_build_pot(const md_params *p, PotDev *out, Cf64 **d_tabs64, float4 **d_tabs32, char *err, size_t errlen);
 
 // ---- launchers (all enqueue on `s`; return cudaError_t of the launch)
-cudaError_t launch_decide(const DevArgs &a, int mode, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_decide(const DevArgs &a, int mode, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s,
+                          cudaGraphConditionalHandle hv = 0);
 cudaError_t launch_rebuild(const DevArgs &a, cudaStream_t s);
 cudaError_t launch_verlet1(const DevArgs &a, cudaStream_t s);
 // energies = 0: the mixed-precision kernel leaves the embedding-energy partials alone

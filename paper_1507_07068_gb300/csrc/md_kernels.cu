@@ -413,11 +413,12 @@ __device__ __forceinline__ void cta_partials(T (&v)[NV], double *part, int strid
 __device__ __forceinline__ int buf_cur(const DevArgs &a) { return (int)(*(volatile long long *)&a.st->ph_cur & 1); }
 __device__ __forceinline__ int buf_step(const DevArgs &a) { return (int)(*(volatile long long *)&a.st->ph & 1); }
 
-// Task 1 of a step (mode DEC_DRIFT or DEC_FULL) or of an explicit list build (DEC_BUILD),
-// and for a step also Task 2: the indenter moves by v dt, and the step count and the buffer
-// counter advance (the pair kernels of this step find their positions in buffer ph & 1).
-// The graph's conditional (use_cond) gets the rebuild decision.
-__global__ void k_decide(DevArgs a, int mode, int use_cond, cudaGraphConditionalHandle h)
+// Task 1 of a step (mode DEC_DRIFT, DEC_FULL or DEC_AUTO) or of an explicit list build
+// (DEC_BUILD), and for a step also Task 2: the indenter moves by v dt, and the step count
+// and the buffer counter advance (the pair kernels of this step find their positions in
+// buffer ph & 1).  The graph's conditional h (use_cond) gets the rebuild decision; in
+// DEC_AUTO, hv gets whether k_verlet1 runs (a rebuild, or no drift ready: drift_ok).
+__global__ void k_decide(DevArgs a, int mode, int use_cond, cudaGraphConditionalHandle h, cudaGraphConditionalHandle hv)
 {
     const int force = mode == DEC_BUILD;
     // the status words first, all at once (this kernel is a chain of dependent memory
@@ -469,7 +470,8 @@ __global__ void k_decide(DevArgs a, int mode, int use_cond, cudaGraphConditional
     }
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
-        const int run_verlet = mode == DEC_FULL || (mode == DEC_DRIFT && any);
+        const int run_verlet = mode == DEC_FULL || ((mode == DEC_DRIFT || mode == DEC_AUTO) && any) ||
+                               (mode == DEC_AUTO && !drift_ok);
         if (mode == DEC_DRIFT && !any && !drift_ok) atomicOr(&a.st->err, MDE_SCHED);
         a.st->ph_cur = T;
         if (!force) { a.st->ph = T + 1; a.st->step += 1; }
@@ -480,7 +482,10 @@ __global__ void k_decide(DevArgs a, int mode, int use_cond, cudaGraphConditional
             for (int r = 0; r < a.n_rep; ++r) a.rs[r].d2b[bs ^ 1] = 0ull;
         a.st->any_rebuild = any;
         a.st->run_verlet = run_verlet;
-        if (use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
+        if (use_cond) {
+            cudaGraphSetConditional(h, any ? 1u : 0u);
+            if (mode == DEC_AUTO) cudaGraphSetConditional(hv, run_verlet ? 1u : 0u);
+        }
     }
 }
 __global__ void k_zero_i32(int32_t *p, int n)
@@ -2121,9 +2126,10 @@ static unsigned morse_grid() { return (unsigned)(2 * device_sms()); }
 
 // ============================================================================ launchers
 
-cudaError_t launch_decide(const DevArgs &a, int mode, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s)
+cudaError_t launch_decide(const DevArgs &a, int mode, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s,
+                          cudaGraphConditionalHandle hv)
 {
-    k_decide<<<1, 256, 0, s>>>(a, mode, use_cond, h);
+    k_decide<<<1, 256, 0, s>>>(a, mode, use_cond, h, hv);
     return cudaGetLastError();
 }
 

@@ -276,11 +276,13 @@ def test_graph_and_direct_launch_bitwise_equal(md, params):
 
 
 def test_interleaved_calls_keep_the_trajectory(md, params):
-    """The mixed-precision force kernel makes the next step's drift; a state set from the
-    host (even unchanged, even with another step count), forces recomputed, or lists
-    rebuilt between steps void it and the next step drifts afresh.  A run interrupted by
-    such calls that do not change the state follows the uninterrupted run bit for bit, with
-    graphs (unrolled and single steps) and with direct launches alike."""
+    """The mixed-precision force kernel makes the next step's drift; forces recomputed or
+    lists rebuilt between steps make it again, and a state set from the host keeps it when
+    positions, velocities and indenter are bit for bit the ones held (even with another
+    step count; the first step then reads the device's drift flag), else the next step
+    drifts afresh.  A run interrupted by such calls that do not change the state follows
+    the uninterrupted run bit for bit, with graphs (unrolled and single steps) and with
+    direct launches alike."""
     rep = tiny(amp=0.05, gap=2.0, T=600.0)
     ref = md.MD([rep], params, precision="mixed")
     ref.step(3 + 1 + 2 + 9 + 4)
