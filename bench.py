@@ -529,9 +529,17 @@ def cpu_baseline(workload: str, params, seconds: float, skin: float = 0.3):
         v3 = oracle_rate(params, rep, n, skin)
     finally:
         oracle.select("O2")
-    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "value_O3": v3,
+    # one thread (-O2), on a sample sized for about seconds / 8 at the all-core rate / cores
+    oracle.set_threads(1)
+    try:
+        rep1, desc1 = oracle_sample_replica(workload, max(int(rate / max(cores, 1) * seconds / 16), 5000))
+        v1 = oracle_rate(params, rep1, 2, skin)
+    finally:
+        oracle.set_threads(cores)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "value_O3": v3, "value_1core": v1,
             "sample": f"{n} FP64 oracle time steps (list build excluded) on {desc}, OpenMP over {cores} threads; "
-                      "value: built -O2 (the paper's flags), value_O3: the same at -O3"}
+                      "value: built -O2 (the paper's flags), value_O3: the same at -O3; "
+                      f"value_1core: -O2 on one thread, 2 steps on {desc1}"}
 
 
 def run_reference(args):
