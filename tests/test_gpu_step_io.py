@@ -144,3 +144,31 @@ def test_step_io_recovers_an_overflow_as_md_step(md, params, precision):
     assert info["kmax"] > k0 or info["kcmax"] > kc0    # an exchange met an overflow
     assert (info["kmax"], info["kcmax"]) == (a.info()["kmax"], a.info()["kcmax"])
     a.close(); b.close()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_one_changed_velocity_remakes_the_drift(md, params, use_graph):
+    """md_set_state with every position and all velocities but one atom's the held ones:
+    the device's comparison must void the drift the last force pass made (it used the old
+    velocity), so the run follows the oracle started at the new state; with the drift kept
+    that atom would move 1.5e-3 A off in the first step alone."""
+    rep = tiny(amp=0.05, gap=2.0, T=300.0)
+    sim = md.MD([rep], params, precision="mixed", skin=0.3, use_graph=use_graph)
+    sim.step(12)
+    x, v, z, st = sim.state(0)
+    v2 = v.copy()
+    k = int(np.argmax(np.abs(v[:, 0])))
+    v2[k] *= 1.5
+    if use_graph:
+        sim.step_io(0, x, v2, z, st, 1)
+    else:   # direct launches: k_decide's DEC_AUTO read back by the host
+        sim.set_state(0, x, v2, z, st)
+        sim.step(1)
+    sim.step(9)
+    o = oracle.Sim(oracle.Potential(params), dataclasses.replace(rep, x_cr=x, v_cr=v2, z_indenter0=z), skin=0.3)
+    o.step(10)
+    d = sim.state(0)[0] - o.state()["x"]
+    L = rep.box_hi - rep.box_lo
+    d -= np.round(d / L) * L * (rep.periodic == 1)
+    assert np.abs(d).max() < 1e-5
+    sim.close()
