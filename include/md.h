@@ -235,7 +235,8 @@ int md_get_state(md_t *h, int32_t replica, double *x3n, double *v3n, double *z_i
  * (the energy sums of the new state are evaluated when md_get_energy first asks
  * for them; an md_step in between makes its own).  The neighbour lists are kept when the new positions pass the rebuild test of
  * md_step (max |x - x_build| and the indenter's travel since the last build against the
- * skin, Sec. 2.6), else rebuilt (as md_build_neighbors).  Errors: MD_ERR_LOST_ATOM,
+ * skin, Sec. 2.6), else rebuilt (as md_build_neighbors).  The call returns once x3n and v3n
+ * have been read (the caller may reuse them).  Errors: MD_ERR_LOST_ATOM,
  * MD_ERR_NBR_OVERFLOW, MD_ERR_CUDA. */
 int md_set_state(md_t *h, int32_t replica, const double *x3n, const double *v3n, double z_ind, int64_t step);
 

@@ -1108,7 +1108,21 @@ int md_get_state(md_t *h, int32_t r, double *x3n, double *v3n, double *z_ind, in
     return MD_OK;
 }
 
-int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, double z_ind, int64_t step)
+// page-locked host memory (the copy engine reads it after the call that queued the copy)
+static bool host_pinned(const void *p)
+{
+    cudaPointerAttributes at;
+    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
+// md_set_state; wait_v: return only once the velocities are read from v3n (the public
+// call: the caller may write v3n when it returns); md_step_io synchronises later itself
+static int set_state_impl(md_t *h, int32_t r, const double *x3n, const double *v3n, double z_ind, int64_t step,
+                          bool wait_v)
 {
     int rc = check_replica(h, r);
     if (rc) return rc;
@@ -1172,6 +1186,9 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
         }
         h->forces_valid = true;
         h->energies_valid = false;
+        // a page-locked v3n is still being read by the copy engine when this returns: the
+        // public call waits for it (a pageable one was copied before cudaMemcpyAsync returned)
+        if (wait_v && v3n && host_pinned(v3n)) CU(cudaStreamSynchronize(h->xfer));
         return MD_OK;
     }
     int rc2;
@@ -1185,6 +1202,11 @@ int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, doubl
     return MD_OK;
 }
 
+int md_set_state(md_t *h, int32_t r, const double *x3n, const double *v3n, double z_ind, int64_t step)
+{
+    return set_state_impl(h, r, x3n, v3n, z_ind, step, true);
+}
+
 int md_step_io(md_t *h, int32_t r, const double *x3n, const double *v3n, double z_ind, int64_t step, int64_t n,
                double *x_out, double *v_out, md_energy *e_out)
 {
@@ -1192,7 +1214,7 @@ int md_step_io(md_t *h, int32_t r, const double *x3n, const double *v3n, double 
     if (rc) return rc;
     if (!x3n || !v3n || !x_out || !v_out || !e_out) return fail(h, MD_ERR_ARG, "md_step_io: null argument");
     if (n < 1) return fail(h, MD_ERR_ARG, "md_step_io: n < 1");
-    if ((rc = md_set_state(h, r, x3n, v3n, z_ind, step))) return rc;
+    if ((rc = set_state_impl(h, r, x3n, v3n, z_ind, step, false))) return rc;
     if ((rc = ensure_forces(h))) return rc;
     // direct launches: the calls in turn
     if (!h->opt.use_graph || !h->exec1) {

@@ -172,3 +172,50 @@ def test_one_changed_velocity_remakes_the_drift(md, params, use_graph):
     d -= np.round(d / L) * L * (rep.periodic == 1)
     assert np.abs(d).max() < 1e-5
     sim.close()
+
+
+def _pinned(a):
+    """A page-locked copy of a (the array and the tensor that owns its memory)."""
+    torch = pytest.importorskip("torch")
+    t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+    p = t.numpy()
+    p[:] = a
+    return p, t
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_page_locked_arrays_move_the_same_bits(md, params, precision):
+    """Page-locked host arrays (copied asynchronously by the copy engines; md_set_state
+    waits until its velocities are read) and pageable ones give the same state, forces and
+    energies bit for bit, through state changes that keep and rebuild the lists, on a
+    replica that is not the first of its batch."""
+    reps = []
+    for r, (nxy, nz, R, T) in enumerate([(6, 6, 5.0, 100.0), (9, 7, 6.0, 600.0)]):
+        reps.append(jitter(mi.make_replica(f"p{r}", nxy, nxy, nz, R, T, seed=70 + r, gap=1.5), 0.05, r))
+    a = md.MD(reps, params, precision=precision, skin=0.3)
+    b = md.MD(reps, params, precision=precision, skin=0.3)
+    a.step(3); b.step(3)
+    x, v, z, st = a.state(1)
+    rng = np.random.default_rng(5)
+    keep = []
+    for it, (dx, n) in enumerate([(0.0, 1), (0.02, 1), (0.0, 4), (0.3, 1), (0.0, 20), (0.0, 1)]):
+        x = np.ascontiguousarray(x + rng.uniform(-dx, dx, x.shape)) if dx else x
+        v = np.ascontiguousarray(v * (1.0 + 0.01 * it))
+        ra = a.step_io(1, x, v, z, st, n)                       # pageable: staged copies
+        xp, t1 = _pinned(x); vp, t2 = _pinned(v)
+        xo, t3 = _pinned(np.zeros_like(x)); vo, t4 = _pinned(np.zeros_like(v))
+        keep += [t1, t2, t3, t4]
+        rb = b.step_io(1, xp, vp, z, st, n, x_out=xo, v_out=vo)  # page-locked: in place
+        same(ra, rb)
+        x, v, z, st = ra[0], ra[1], ra[2]["z_indenter"], ra[2]["step"]
+    assert b.energy(1)["rebuilds"] >= 2
+    # the separate calls with page-locked arrays
+    xp, t1 = _pinned(x); vp, t2 = _pinned(v)
+    a.set_state(1, x, v, z, st); b.set_state(1, xp, vp, z, st)
+    a.step(3); b.step(3)
+    xo, t3 = _pinned(np.zeros_like(x)); vo, t4 = _pinned(np.zeros_like(v)); fo, t5 = _pinned(np.zeros_like(x))
+    md.md_get_state(b.h, 1, len(x), xo, vo)
+    md.md_get_forces(b.h, 1, len(x), fo)
+    xa, va, _, _ = a.state(1)
+    assert np.array_equal(xa, xo) and np.array_equal(va, vo) and np.array_equal(a.forces(1), fo)
+    a.close(); b.close()
