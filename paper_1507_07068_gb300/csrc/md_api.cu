@@ -130,16 +130,17 @@ struct md_handle {
     int64_t n_cr = 0, n_c = 0;
     Cf64 *tab64 = nullptr;
     float4 *tab32 = nullptr;
-    double *stage = nullptr;              // 3 * max replica atoms doubles
+    double *stage = nullptr;              // 6 * max replica atoms doubles (x, then v)
     std::vector<void *> allocs;
     // step graphs: exec1 / execU one / `unroll` steps after a step (mixed: drift made), execE
     // the same single step with the energies (the last step of an md_step call); execF /
-    // execFE mixed precision's single step that runs k_verlet1, without / with the energies
+    // execFE mixed precision's first step when no drift is known to be ready (DEC_AUTO: it
+    // runs k_verlet1 unless the device's flag says one is), without / with the energies
     cudaGraphExec_t exec1 = nullptr, execU = nullptr, execE = nullptr;
     cudaGraphExec_t execF = nullptr, execFE = nullptr;
     // md_step_io's last step (captured on first use): execE / execFE with an external event,
-    // xready, recorded once the step's Task 3 has made x(t + dt); [0] after a step or in FP64,
-    // [1] mixed precision's step that runs k_verlet1
+    // xready, recorded once the step's Task 3 has made x(t + dt); [0] when a drift is known to
+    // be ready or in FP64, [1] mixed precision's first step that reads the drift flag (DEC_AUTO)
     cudaGraphExec_t execIO[2] = {nullptr, nullptr};
     cudaEvent_t xready = nullptr;
     bool drift = false;   // mixed: the last force kernel made the next step's Task 3 (mirrors drift_ok)
@@ -328,10 +329,11 @@ void destroy_graphs(md_t *h)
 // In mixed precision the force kernel drifts the positions for the next step, and k_verlet1
 // runs only after a rebuild (inside the IF), except in a first step with first_full set
 // (after md_build_neighbors, md_set_state, ...): there k_decide (DEC_AUTO) sets a second
-// conditional, IF(rebuild or no drift ready) [k_verlet1], from the device's drift flag.  The energy sums (k_reduce) run once after the last
-// step of an md_step call; with last_energy the graph's last force kernel writes the
-// partials they add.  xev: recorded (an external event node) in every step once x(t + dt)
-// is final, after Task 3 and any list build.
+// conditional, IF(rebuild or no drift ready) [k_verlet1], from the device's drift flag.
+// The energy sums (k_reduce) run once after the last step of an md_step call; with
+// last_energy the graph's last force kernel writes the partials they add.  xev: recorded
+// (an external event node) in every step once x(t + dt) is final, after Task 3 and any
+// list build.
 int capture(md_t *h, int nsteps, bool first_full, bool last_energy, cudaGraphExec_t *out,
             cudaEvent_t xev = nullptr)
 {
