@@ -1416,6 +1416,44 @@ __device__ __forceinline__ void fa_phi(const Pot32 &Q, float r2, float rinv, flo
     dph = t * fmaf(fmaf(fmaf(Q.c3, sv, Q.c2), sv, Q.c1), sv, Q.c0);
 }
 
+// The force pass's pair terms for beta = 6 (f = q^3, q = re2f / r^2) for two pairs at once,
+// in Blackwell's packed FP32x2 arithmetic (__ffma2_rn, __fmul2_rn, __fadd2_rn: each
+// component rounded as the scalar operation; the rsqrt and Phi's clamp per component), as
+// an explicit sequence of separately rounded operations.  In: the two displacements in
+// units of qu and (F'_j, 2 M'_j); out: r^2, coef (the force on i from j over its
+// displacement) and, with EN, Phi/2; the caller selects coef and Phi/2 by r < rc.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+template <bool EN>
+__device__ __forceinline__ void pair_force6x2(const Pot32 &Q, float qu2, float2 fmi, float2 fmj0, float2 fmj1,
+                                              float2 DX, float2 DY, float2 DZ, float2 &R2, float2 &COEF,
+                                              float2 &PH)
+{
+    R2 = __fmul2_rn(__ffma2_rn(DX, DX, __ffma2_rn(DY, DY, __fmul2_rn(DZ, DZ))), f2(qu2));
+    const float2 Y = make_float2(rsqrtf(R2.x), rsqrtf(R2.y));
+    const float2 RINV = __fmul2_rn(Y, __ffma2_rn(__fmul2_rn(__fmul2_rn(R2, f2(-0.5f)), Y), Y, f2(1.5f)));
+    const float2 R = __fmul2_rn(R2, RINV);
+    const float2 QQ = __fmul2_rn(f2(Q.re2f), __fmul2_rn(RINV, RINV));
+    const float2 FR = __fmul2_rn(__fmul2_rn(QQ, QQ), QQ);
+    const float2 F = __ffma2_rn(R, f2(-Q.df_rc), __fadd2_rn(FR, f2(-Q.cf)));
+    const float2 DF = __ffma2_rn(__fmul2_rn(FR, f2(-6.0f)), RINV, f2(-Q.df_rc));
+    const float2 SV = __fmul2_rn(__fadd2_rn(R, f2(-Q.rs)), f2(Q.inv_re));
+    float2 T = __fadd2_rn(SV, f2(Q.tc));
+    T.x = fminf(T.x, 0.0f);
+    T.y = fminf(T.y, 0.0f);
+    const float2 PC = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2(Q.c3), SV, f2(Q.c2)), SV, f2(Q.c1)), SV, f2(Q.c0));
+    const float2 DPH = __fmul2_rn(T, PC);
+    const float2 A = __fadd2_rn(f2(fmi.y), make_float2(fmj0.y, fmj1.y));
+    const float2 B = __fadd2_rn(f2(fmi.x), make_float2(fmj0.x, fmj1.x));
+    COEF = __fmul2_rn(__ffma2_rn(__ffma2_rn(A, F, B), DF, DPH), RINV);
+    if (EN) {
+        const float2 PB = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2(Q.b3), SV, f2(Q.b2)), SV, f2(Q.b1)), SV, f2(Q.b0));
+        PH = __fmul2_rn(__fmul2_rn(__fmul2_rn(T, T), PB), f2(0.5f));
+    } else {
+        PH = make_float2(0.0f, 0.0f);
+    }
+}
+
 // Task 4a (Eqs. A2-A3): rho_i, P_i over the pairs within rc; F'(rho_i), M'(P_i) stored,
 // and with EN F(rho_i), M(P_i) into the CTA's energy partials.  MD_UNROLL entries per lane
 // are loaded (list entry, then position) before any is used.
@@ -1626,25 +1664,52 @@ __global__ void __launch_bounds__(256, 5) k_force_mixed(DevArgs a, PotDev P, int
                 pj[u] = __ldg(&pp[j]);
                 fmj[u] = __ldg(&a.fm32[j]);
             }
+            // beta = 6: the batch's two pairs in packed FP32x2 arithmetic (a warp-uniform
+            // path: an atom's last batch with one entry only computes its padding too)
+            if (IPOW == 3 && FU == 2) {
+                // a padding entry (the atom itself: r = 0, non-finite terms) is dropped by the
+                // selects below, which never multiply it
+                const bool real0 = (e[0] & MD_J_MASK) != (unsigned)s, real1 = (e[FU - 1] & MD_J_MASK) != (unsigned)s;
+                float dx0, dy0, dz0, dx1, dy1, dz1;
+                disp<PER>(pi, pj[0], e[0] >> MD_J_BITS, sm_off, G, dx0, dy0, dz0);
+                disp<PER>(pi, pj[FU - 1], e[FU - 1] >> MD_J_BITS, sm_off, G, dx1, dy1, dz1);
+                float2 R2, COEF, PH;
+                pair_force6x2<EN>(Q, qu2, fmi, fmj[0], fmj[FU - 1], make_float2(dx0, dx1), make_float2(dy0, dy1),
+                                  make_float2(dz0, dz1), R2, COEF, PH);
+                const bool in0 = real0 && R2.x < Q.rc2, in1 = real1 && R2.y < Q.rc2;
+                const float cw0 = in0 ? COEF.x : 0.0f, cw1 = in1 ? COEF.y : 0.0f;
+                gx = fmaf(cw0, dx0, gx);
+                gy = fmaf(cw0, dy0, gy);
+                gz = fmaf(cw0, dz0, gz);
+                gx = fmaf(cw1, dx1, gx);
+                gy = fmaf(cw1, dy1, gy);
+                gz = fmaf(cw1, dz1, gz);
+                if (EN) {
+                    ep += in0 ? PH.x : 0.0f;
+                    ep += in1 ? PH.y : 0.0f;
+                }
+                continue;
+            }
 #pragma unroll
             for (int u = 0; u < FU; ++u) {
                 float dx, dy, dz;
                 disp<PER>(pi, pj[u], e[u] >> MD_J_BITS, sm_off, G, dx, dy, dz);
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * qu2;
                 if ((e[u] & MD_J_MASK) != (unsigned)s) {   // padding is the atom itself
                     // inner-list entries beyond rc (at most rc + inner skin) drop out by a
                     // select: their terms are finite
-                    const bool in = r2 < Q.rc2;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * qu2;
                     const float rinv = rsqrt_nr(r2);
                     float f, df, ph, dph;
                     fa_phi<IPOW, EN>(Q, r2, rinv, f, df, ph, dph);
                     // [(F'_i + F'_j) + 2 (M'_i + M'_j) f] f' + Phi', over r
                     const float coef = fmaf(fmaf(fmi.y + fmj[u].y, f, fmi.x + fmj[u].x), df, dph) * rinv;
+                    ph *= 0.5f;
+                    const bool in = r2 < Q.rc2;
                     const float cw = in ? coef : 0.0f;
                     gx = fmaf(cw, dx, gx);
                     gy = fmaf(cw, dy, gy);
                     gz = fmaf(cw, dz, gz);
-                    if (EN) ep += in ? 0.5f * ph : 0.0f;
+                    if (EN) ep += in ? ph : 0.0f;
                 }
             }
         }
