@@ -168,3 +168,35 @@ def test_fullsize_8m_mixed_forces_and_lists(md, params):
     err = rel_force_err(Fm, ref["F"])
     print("8M mixed: max %.2e p99 %.2e" % (err.max(), np.quantile(err, 0.99)))
     assert err.max() <= 1e-5
+
+
+def test_fullsize_step_io_against_oracle(md, params, thermal_1m):
+    """md_step_io on the whole 1M film from a state the host changed (velocities scaled,
+    so the drift is made afresh), page-locked arrays written in place, 10 steps, mixed
+    precision: positions and velocities against the FP64 oracle started at that state
+    (every atom), energies per atom; the call's result is the calls in turn's bit for bit."""
+    torch = pytest.importorskip("torch")
+    rep, _ = thermal_1m
+    x, v, z = rep.x_cr, np.ascontiguousarray(0.9 * rep.v_cr), rep.z_indenter0
+    hx = torch.empty(x.shape, dtype=torch.float64, pin_memory=True).numpy()
+    hv = torch.empty(v.shape, dtype=torch.float64, pin_memory=True).numpy()
+    a = md.MD([rep], params, precision="mixed", skin=SKIN)
+    b = md.MD([rep], params, precision="mixed", skin=SKIN)
+    hx[:] = x; hv[:] = v
+    _, _, e = a.step_io(0, hx, hv, z, 0, 10, x_out=hx, v_out=hv)
+    b.set_state(0, x, v, z, 0)
+    b.step(10)
+    xb, vb, _, _ = b.state(0)
+    assert np.array_equal(hx, xb) and np.array_equal(hv, vb)
+    oracle.set_threads(0)
+    osim = oracle.Sim(oracle.Potential(params), dataclasses.replace(rep, v_cr=v), skin=SKIN)
+    osim.step(10)
+    o = osim.state()
+    d = hx - o["x"]
+    L = rep.box_hi - rep.box_lo
+    d -= np.round(d / L) * L * (rep.periodic == 1)
+    assert np.abs(d).max() < 1e-5
+    assert np.abs(hv - o["v"]).max() < 1e-5
+    assert abs(e["potential"] - o["potential"]) / rep.n_cr < 1e-5
+    assert e["step"] == 10 and e["z_indenter"] == o["z_ind"]
+    a.close(); b.close()
